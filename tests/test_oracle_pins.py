@@ -1,0 +1,386 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+None of these compares the oracle with itself: each checks it against a
+hand-computed value, a closed form, an invariant, an independent algorithm
+(explicit-flow ALM, linear programming, exhaustive search) or the paper's
+own definitions (path weights W, flow excess d).
+"""
+import numpy as np
+import pytest
+
+import synth
+
+
+def softmax_closed_form(D, k, c):
+    """S = 0 (or spatially constant D): q stays 0, so after k iterations of
+    Algorithm 1 u_L = exp(-k D_L / c) / sum_L' exp(-k D_L' / c)."""
+    z = -k * D.astype(np.float64) / c
+    z -= z.max(axis=0, keepdims=True)
+    e = np.exp(z)
+    return e / e.sum(axis=0, keepdims=True)
+
+
+# ---------------------------------------------------------------- operators
+
+def test_grad_hand_values(orc):
+    u = np.array([[1.0, 4.0, 2.0],
+                  [0.5, 0.0, 7.0]])          # (ny=2, nx=3)
+    g = orc.grad(u)
+    gx = np.array([[3.0, -2.0, 0.0], [-0.5, 7.0, 0.0]])
+    gy = np.array([[-0.5, -4.0, 5.0], [0.0, 0.0, 0.0]])
+    assert np.array_equal(g[0], gx) and np.array_equal(g[1], gy)
+
+
+def test_div_hand_values(orc):
+    qx = np.array([[1.0, 2.0, 9.0]])          # last x entry is ignored
+    qy = np.array([[5.0, 5.0, 5.0]])          # ny = 1: y flow never enters
+    d = orc.div(np.stack([qx, qy]))
+    assert np.array_equal(d, np.array([[1.0, 1.0, -2.0]]))
+
+
+@pytest.mark.parametrize("spatial", [(7, 5), (4, 6, 5), (1, 9), (3, 1, 4)])
+def test_div_is_negative_adjoint_of_grad(orc, spatial):
+    rng = np.random.default_rng(1)
+    u = rng.standard_normal(spatial)
+    q = rng.standard_normal((len(spatial),) + spatial)
+    lhs = np.sum(orc.grad(u) * q)
+    rhs = -np.sum(u * orc.div(q))
+    assert abs(lhs - rhs) <= 1e-12 * (1 + abs(lhs))
+
+
+def test_projection_iso_and_aniso(orc):
+    rng = np.random.default_rng(2)
+    for _ in range(200):
+        y = rng.standard_normal(3) * rng.uniform(0.01, 3)
+        s = rng.uniform(0, 2)
+        p = orc.project(y, s, orc.ISO)
+        r = np.linalg.norm(y)
+        if r <= s:
+            assert np.array_equal(p, y)
+        else:
+            assert abs(np.linalg.norm(p) - s) <= 1e-12 and np.allclose(p * r, y * s)
+        # nearest point of the ball: no sampled ball point is closer
+        pts = rng.standard_normal((64, 3))
+        pts *= (s * rng.random((64, 1)) ** (1 / 3)) / np.maximum(np.linalg.norm(pts, axis=1, keepdims=True), 1e-300)
+        assert np.linalg.norm(y - p) <= np.min(np.linalg.norm(pts - y, axis=1)) + 1e-12
+        pa = orc.project(y, s, orc.ANISO)
+        assert np.array_equal(pa, np.clip(y, -s, s))
+    assert np.array_equal(orc.project([0.3, -0.4], 0.0, orc.ISO), np.zeros(2))
+
+
+# ---------------------------------------------------------------- closed forms
+
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("spatial", [(9, 11), (3, 4, 5)])
+def test_potts_zero_capacity_closed_form(orc, mode, spatial):
+    p = synth.random_problem(3, spatial, nl=4)
+    D = p.D.astype(np.float64)
+    S = np.zeros(spatial)
+    u, q = orc.potts_init(spatial, 4)
+    done = 0
+    for k in (1, 7, 20):
+        orc.potts_iterate(D, u, q, k - done, 0.5, 0.11, S_field=S, grad_source=mode)
+        done = k
+        assert np.abs(u - softmax_closed_form(D, k, 0.5)).max() <= 1e-13
+        assert np.all(q == 0.0)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_potts_constant_data_any_capacity(orc, mode):
+    rng = np.random.default_rng(4)
+    spatial = (6, 5)
+    D = np.broadcast_to(rng.random((3, 1, 1)), (3,) + spatial).copy()
+    S = rng.random(spatial)
+    u, q = orc.potts_init(spatial, 3)
+    orc.potts_iterate(D, u, q, 15, 0.5, 0.11, S_field=S, grad_source=mode)
+    assert np.abs(u - softmax_closed_form(D, 15, 0.5)).max() <= 1e-13
+    assert np.all(q == 0.0)
+
+
+def test_dag_zero_capacity_closed_form(orc):
+    """With q = 0 the excess of an end-label is its own data term (d_S = 0,
+    inner nodes carry no data), so the Potts closed form holds on leaves."""
+    rng = np.random.default_rng(5)
+    nn, edges = synth.random_dag(rng, 3, 5, 2)
+    dag = orc.Dag(nn, edges)
+    spatial = (4, 5, 3)
+    D = rng.random((5,) + spatial)
+    u, q = orc.dag_init(spatial, dag)
+    orc.dag_iterate(dag, D, u, q, 12, 0.5, 0.11, S_field=np.zeros(spatial))
+    assert np.abs(u - softmax_closed_form(D, 12, 0.5)).max() <= 1e-13
+
+
+# ---------------------------------------------------------------- invariants
+
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("norm", [0, 1])
+def test_potts_invariants_every_iteration(orc, mode, norm):
+    p = synth.random_problem(6, (5, 7, 6), nl=4, s_kind="both")
+    D, S, sn = p.D.astype(np.float64), p.S_field.astype(np.float64), p.s_node.astype(np.float64)
+    u, q = orc.potts_init(p.spatial, 4)
+    cap = sn[:, None, None, None] * S[None]
+    for _ in range(25):
+        orc.potts_iterate(D, u, q, 1, 0.5, 0.11, S_field=S, s_node=sn, norm=norm, grad_source=mode)
+        assert np.all(u >= 0) and np.abs(u.sum(0) - 1).max() <= 1e-12
+        mag = np.sqrt((q ** 2).sum(1)) if norm == 0 else np.abs(q).max(1)
+        assert np.all(mag <= cap * (1 + 1e-12) + 1e-300)
+        # zero normal flux at the far boundary of every axis
+        assert np.all(q[:, 0, :, :, -1] == 0) and np.all(q[:, 1, :, -1, :] == 0) and np.all(q[:, 2, -1] == 0)
+        E, P = orc.potts_energy(D, u, q, S_field=S, s_node=sn, norm=norm)
+        assert E - P >= -1e-12 * abs(E)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_dag_invariants_every_iteration(orc, mode):
+    rng = np.random.default_rng(7)
+    nn, edges = synth.random_dag(rng, 3, 6, 2)
+    dag = orc.Dag(nn, edges)
+    spatial = (6, 5)
+    D = rng.random((6,) + spatial)
+    sn = rng.uniform(0.05, 0.5, nn)
+    u, q = orc.dag_init(spatial, dag)
+    for _ in range(20):
+        orc.dag_iterate(dag, D, u, q, 1, 0.5, 0.11, s_node=sn, grad_source=mode)
+        assert np.all(u >= 0) and np.abs(u.sum(0) - 1).max() <= 1e-12
+        assert np.all(np.sqrt((q ** 2).sum(1)) <= sn[:, None, None] * (1 + 1e-12))
+        E, P = orc.dag_energy(dag, D, u, q, s_node=sn)
+        assert E - P >= -1e-12 * abs(E)
+
+
+@pytest.mark.parametrize("norm", [0, 1])
+def test_weak_duality_random_feasible_pairs(orc, norm):
+    """P(q) <= E(u) for ANY simplex u and ANY capacity-feasible q."""
+    rng = np.random.default_rng(8)
+    nn, edges = synth.hmf_tree(2, 3)
+    dag = orc.Dag(nn, edges)
+    spatial = (4, 5, 6)
+    for trial in range(10):
+        D = rng.random((6,) + spatial)
+        u = rng.random((6,) + spatial) ** 3
+        u /= u.sum(0)
+        sn = rng.uniform(0, 0.6, nn)
+        q = rng.standard_normal((nn, 3) + spatial)
+        for A in range(nn):
+            for idx in np.ndindex(spatial):
+                q[(A, slice(None)) + idx] = orc.project(q[(A, slice(None)) + idx], sn[A], norm)
+        E, P = orc.dag_energy(dag, D, u, q, s_node=sn, norm=norm)
+        assert P <= E + 1e-12
+        E2, P2 = orc.potts_energy(D, u, q[:6], s_node=sn[:6], norm=norm)
+        assert P2 <= E2 + 1e-12
+
+
+# ---------------------------------------------------------------- the paper's own definitions
+
+def test_path_weights_definition(orc):
+    # S -> 0 (w 1), S -> 1 (w 1); 0 -> 2 (0.5), 1 -> 2 (0.5), 0 -> 3 (0.5), 1 -> 3 (0.25), 1 -> 4 (0.25)
+    edges = [(-1, 0, 1.0), (-1, 1, 1.0), (0, 2, 0.5), (1, 2, 0.5), (0, 3, 0.5), (1, 3, 0.25), (1, 4, 0.25)]
+    W = orc.Dag(5, edges).path_weights()
+    expect = np.eye(5)
+    expect[0, 2], expect[1, 2], expect[0, 3], expect[1, 3], expect[1, 4] = 0.5, 0.5, 0.5, 0.25, 0.25
+    assert np.array_equal(W, expect)
+    # two-level paths multiply and add
+    edges2 = [(-1, 0, 1.0), (0, 1, 0.5), (0, 2, 0.5), (1, 3, 1.0), (2, 3, 1.0)]
+    W2 = orc.Dag(4, edges2).path_weights()
+    assert W2[0, 3] == 1.0 and W2[1, 3] == 1.0 and W2[0, 1] == 0.5
+
+
+def test_generated_dags_have_unit_source_weight(orc):
+    rng = np.random.default_rng(9)
+    for _ in range(20):
+        nn, edges = synth.random_dag(rng, 4, 10, 2)
+        dag = orc.Dag(nn, edges)
+        W = dag.path_weights()
+        roots = [b for a, b, _ in edges if a == -1]
+        w_s = {b: w for a, b, w in edges if a == -1}
+        for leaf in dag.leaves():
+            assert abs(sum(w_s[r] * W[r, leaf] for r in roots) - 1.0) <= 1e-12
+
+
+def test_dag_excess_equals_path_weight_form(orc):
+    """The top-down pass of Algorithm 2 equals the definition of d_L in
+    Section 3.3 unrolled with the path weights: d_leaf = sum_A W_(A,leaf) e_A,
+    e_A = div q_A (+ D_A on end-labels).  Checked through P(q) = sum min d."""
+    rng = np.random.default_rng(10)
+    nn, edges = synth.random_dag(rng, 3, 5, 2)
+    dag = orc.Dag(nn, edges)
+    W = dag.path_weights()
+    leaves = dag.leaves()
+    spatial = (5, 4, 3)
+    D = rng.random((5,) + spatial)
+    q = 0.3 * rng.standard_normal((nn, 3) + spatial)
+    u = np.full((5,) + spatial, 0.2)
+    _, P = orc.dag_energy(dag, D, u, q)
+    e = np.stack([orc.div(q[A]) for A in range(nn)])
+    for j, leaf in enumerate(leaves):
+        e[leaf] += D[j]
+    d = np.stack([sum(W[A, leaf] * e[A] for A in range(nn)) for leaf in leaves])
+    assert abs(P - d.min(0).sum()) <= 1e-12 * (1 + abs(P))
+
+
+def test_flat_dag_is_potts_bitwise(orc):
+    for mode in (0, 1):
+        p = synth.random_problem(11, (6, 7), nl=4, s_kind="both")
+        D, S, sn = (a.astype(np.float64) for a in (p.D, p.S_field, p.s_node))
+        u1, q1 = orc.potts_init(p.spatial, 4)
+        orc.potts_iterate(D, u1, q1, 30, 0.5, 0.11, S_field=S, s_node=sn, grad_source=mode)
+        dag = orc.Dag.flat(4)
+        u2, q2 = orc.dag_init(p.spatial, dag)
+        orc.dag_iterate(dag, D, u2, q2, 30, 0.5, 0.11, S_field=S, s_node=sn, grad_source=mode)
+        assert np.array_equal(u1, u2) and np.array_equal(q1, q2)
+        assert orc.potts_energy(D, u1, q1, S, sn) == orc.dag_energy(dag, D, u2, q2, S, sn)
+
+
+def test_malformed_dags_rejected(orc):
+    for n, edges in [(2, [(-1, 0, 1.0), (0, 1, 1.0), (1, 0, 1.0)]),      # cycle
+                     (2, [(-1, 0, 1.0)]),                                  # orphan node 1
+                     (2, [(-1, 0, 1.0), (0, 5, 1.0)]),                     # bad index
+                     (1, [(-1, 0, 1.0), (0, 0, 1.0)])]:                   # self loop
+        assert orc.Dag(n, edges).n_leaves() == -1
+
+
+# ---------------------------------------------------------------- optimum pins
+
+def _lp_optimum(D, W, leaves, S_field, s_node, norm_aniso=True):
+    """Relaxed optimum of Eq. dagmf_original (Potts: W = I) with the l1
+    (anisotropic) TV, solved as a linear program by HiGHS.  The difference
+    operators are built here from scratch, independently of the oracle."""
+    from scipy.optimize import linprog
+    from scipy import sparse
+    nl = D.shape[0]
+    spatial = D.shape[1:]
+    n = int(np.prod(spatial))
+    nd = len(spatial)
+    idx = np.arange(n).reshape(spatial)
+    Gs = []
+    for comp in range(nd):
+        ax = nd - 1 - comp                    # component 0 = x = last numpy axis
+        rows, cols, vals = [], [], []
+        for pos in np.ndindex(spatial):
+            if pos[ax] + 1 < spatial[ax]:
+                nxt = list(pos)
+                nxt[ax] += 1
+                i, j = idx[pos], idx[tuple(nxt)]
+                rows += [i, i]
+                cols += [j, i]
+                vals += [1.0, -1.0]
+        Gs.append(sparse.csr_matrix((vals, (rows, cols)), shape=(n, n)))
+    nn = W.shape[0]
+    nu, nt = nl * n, nn * nd * n
+    cost = np.concatenate([D.reshape(-1)])
+    capv = []
+    for A in range(nn):
+        s = s_node[A] if s_node is not None else 1.0
+        f = S_field.reshape(-1) if S_field is not None else np.ones(n)
+        for _ in range(nd):
+            capv.append(s * f)
+    cost = np.concatenate([D.reshape(-1), np.concatenate(capv)])
+    A_ub_blocks = []
+    for A in range(nn):
+        # u_A = sum_leaf W[A, leaf] u_leaf
+        Wrow = sparse.hstack([W[A, leaf] * sparse.identity(n) for leaf in leaves])
+        for comp in range(nd):
+            GA = Gs[comp] @ Wrow
+            sel = sparse.lil_matrix((n, nt))
+            base = (A * nd + comp) * n
+            sel[np.arange(n), base + np.arange(n)] = -1.0
+            A_ub_blocks.append(sparse.hstack([GA, sel.tocsr()]))
+            A_ub_blocks.append(sparse.hstack([-GA, sel.tocsr()]))
+    A_ub = sparse.vstack(A_ub_blocks).tocsr()
+    A_eq = sparse.hstack([sparse.hstack([sparse.identity(n)] * nl), sparse.csr_matrix((n, nt))])
+    res = linprog(cost, A_ub=A_ub, b_ub=np.zeros(A_ub.shape[0]), A_eq=A_eq, b_eq=np.ones(n),
+                  bounds=(0, None), method="highs")
+    assert res.status == 0
+    return res.fun
+
+
+def _converge_potts(orc, D, S, sn, norm, iters=20000, c=1.0, tau=0.25):
+    u, q = orc.potts_init(D.shape[1:], D.shape[0])
+    orc.potts_iterate(D, u, q, iters, c, tau, S_field=S, s_node=sn, norm=norm)
+    return u, q, orc.potts_energy(D, u, q, S_field=S, s_node=sn, norm=norm)
+
+
+@pytest.mark.parametrize("spatial", [(5, 4), (3, 3, 3)])
+def test_potts_converges_to_lp_optimum_aniso(orc, spatial):
+    rng = np.random.default_rng(12)
+    D = rng.random((3,) + spatial)
+    S = 0.4 * rng.random(spatial)
+    tau = 0.25 if len(spatial) == 2 else 0.16
+    u, q, (E, P) = _converge_potts(orc, D, S, None, orc.ANISO, tau=tau)
+    lp = _lp_optimum(D, np.eye(3), [0, 1, 2], S, None)
+    assert abs(E - lp) <= 1e-8 * abs(lp) and abs(P - lp) <= 1e-8 * abs(lp)
+
+
+@pytest.mark.parametrize("kind", ["hmf", "dag"])
+def test_dag_converges_to_lp_optimum_aniso(orc, kind):
+    rng = np.random.default_rng(13)
+    if kind == "hmf":
+        nn, edges = synth.hmf_tree(2, 2)
+    else:
+        nn, edges = synth.random_dag(rng, 2, 4, 2)
+    dag = orc.Dag(nn, edges)
+    leaves = dag.leaves()
+    spatial = (4, 5)
+    D = rng.random((len(leaves),) + spatial)
+    sn = rng.uniform(0.05, 0.5, nn)
+    u, q = orc.dag_init(spatial, dag)
+    orc.dag_iterate(dag, D, u, q, 30000, 1.0, 0.15, s_node=sn, norm=orc.ANISO)
+    E, P = orc.dag_energy(dag, D, u, q, s_node=sn, norm=orc.ANISO)
+    lp = _lp_optimum(D, dag.path_weights(), leaves, None, sn)
+    assert abs(E - lp) <= 1e-7 * abs(lp) and abs(P - lp) <= 1e-7 * abs(lp)
+
+
+def test_potts_iso_matches_explicit_flow_alm(orc):
+    """The pseudo-flow optimum equals the full-flow continuous max-flow
+    optimum (the equivalence chain of Section 3.2)."""
+    rng = np.random.default_rng(14)
+    spatial = (12, 10)
+    D = rng.random((3,) + spatial)
+    S = 0.3 * np.ones(spatial)
+    u, q, (E, P) = _converge_potts(orc, D, S, None, orc.ISO, iters=30000)
+    flow, _ = orc.alm_potts(D, 40000, 0.3, 0.25, S_field=S)
+    assert (E - P) <= 1e-10 * abs(E)
+    assert abs(E - flow) <= 1e-9 * abs(flow)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_two_label_threshold_equals_bruteforce(orc, seed):
+    rng = np.random.default_rng(100 + seed)
+    spatial = (4, 4)
+    D = rng.random((2,) + spatial)
+    sn = np.array([0.15, 0.15]) * rng.uniform(0.5, 2)
+    u, q, (E, P) = _converge_potts(orc, D, None, sn, orc.ANISO, iters=20000)
+    best, second, lab0 = orc.bruteforce_binary(D, s_node=sn, norm=orc.ANISO)
+    thr = (u[0] > 0.5).astype(np.float64)
+    ub = np.stack([thr, 1 - thr])
+    Eb, _ = orc.potts_energy(D, ub, np.zeros((2, 2) + spatial), s_node=sn, norm=orc.ANISO)
+    assert abs(E - best) <= 1e-8 and abs(Eb - best) <= 1e-9
+    if second - best > 1e-6:
+        assert np.array_equal(thr.astype(np.uint8), lab0)
+
+
+def test_two_label_1d_iso_equals_bruteforce(orc):
+    rng = np.random.default_rng(120)
+    spatial = (1, 16)                       # ISO and ANISO coincide on a line
+    D = rng.random((2,) + spatial)
+    sn = np.array([0.1, 0.1])
+    u, q, (E, P) = _converge_potts(orc, D, None, sn, orc.ISO, iters=20000)
+    best, _, _ = orc.bruteforce_binary(D, s_node=sn, norm=orc.ISO)
+    assert abs(E - best) <= 1e-8
+
+
+def test_chain_reduction_to_potts(orc):
+    """A leaf whose only parent is an inner node with that single child:
+    u_inner = u_leaf, so at the optimum the DAG energy equals Potts with the
+    two capacities added on that label (Eq. dagmf_original)."""
+    rng = np.random.default_rng(15)
+    spatial = (6, 6)
+    D = rng.random((3,) + spatial)
+    # nodes: 0 inner (under S), leaves 1, 2, 3; 1 under 0, 2 and 3 under S
+    edges = [(-1, 0, 1.0), (0, 1, 1.0), (-1, 2, 1.0), (-1, 3, 1.0)]
+    dag = orc.Dag(4, edges)
+    sn = np.array([0.2, 0.1, 0.25, 0.15])
+    u, q = orc.dag_init(spatial, dag)
+    orc.dag_iterate(dag, D, u, q, 30000, 1.0, 0.2, s_node=sn)
+    E, P = orc.dag_energy(dag, D, u, q, s_node=sn)
+    _, _, (E2, P2) = _converge_potts(orc, D, None, np.array([0.3, 0.25, 0.15]), orc.ISO, iters=30000)
+    assert abs(E - E2) <= 1e-8 * abs(E2) and (E - P) <= 1e-8 * abs(E)
