@@ -1,0 +1,352 @@
+"""Benchmark: pseudo-flow continuous max-flow, 3-D Potts, 256^3 voxels x 8 labels, FP32.
+
+One step = 10 iterations of the fused pseudo-flow update (label prox +
+flow step, Algorithm 1) plus one FP64 primal/dual energy reduction (the gap
+check that drives the stopping test), on a seeded 8-region sphere phantom.
+Metric: voxel-label updates per second (VLU/s, one VLU = one (voxel, label)
+pair advanced by one iteration).  Inputs (4.9 GB of state per iteration)
+are larger than L2, so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Multi-GPU (under torchrun): every rank solves its own independent volume
+(weak scaling, no collective on the data path).  --impl reference times the
+FP64 CPU oracle on the host cores (rank 0 only).
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+ITERS_PER_STEP = 10
+CONFIGS = {
+    # name: (shape, labels, generator, schedule, storage)
+    "potts3d": ((256, 256, 256), 8, "potts3d", 0, 0),
+    "potts3d_inplace": ((256, 256, 256), 8, "potts3d", 1, 0),
+    "potts3d_bf16": ((256, 256, 256), 8, "potts3d", 0, 1),
+    "hmf": ((192, 192, 192), 12, "hmf", 0, 0),
+    "hmf_bf16": ((192, 192, 192), 12, "hmf", 0, 1),
+}
+KERNEL_SOURCE = os.path.join(ROOT, "paper_1501_07844_gb300", "csrc", "pfm_device.cuh")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic.json")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="pfm", choices=["pfm", "reference"])
+    ap.add_argument("--config", default="potts3d", choices=sorted(CONFIGS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--dims", type=int, default=0, help="cube edge override (profiling of small cases)")
+    return ap.parse_args()
+
+
+def make_problem(cfg, seed, shape=None):
+    import synth
+    shape0, nl, gen, _, _ = CONFIGS[cfg]
+    shape = shape or shape0
+    if gen == "potts3d":
+        return synth.potts3d_problem(seed=seed, nl=nl, shape=shape)
+    return synth.hmf_problem(seed=seed, shape=shape)
+
+
+def algorithmic_bytes_per_iter(prob, storage, schedule):
+    """Minimum bytes one fused iteration must move: read u, D, q; write u, q
+    (d and the normaliser stay on chip), plus the S field once per voxel."""
+    n = int(np.prod(prob.spatial))
+    ts = 4 if storage == 0 else 2
+    ndim = len(prob.spatial)
+    b = n * (prob.n_leaf * (2 * ts + 4) + prob.n_nodes * ndim * 2 * ts)
+    if prob.S_field is not None:
+        b += 4 * n
+    return b
+
+
+def kernel_sha():
+    return hashlib.sha256(open(KERNEL_SOURCE, "rb").read()).hexdigest()[:16]
+
+
+def load_traffic(cfg):
+    """DRAM bytes per launch of the dominant kernel from a committed ncu
+    capture, valid only while the kernel source is unchanged."""
+    try:
+        t = json.load(open(TRAFFIC_FILE))
+    except (OSError, ValueError):
+        return None
+    e = t.get(cfg)
+    if not e or e.get("kernel_source_sha") != kernel_sha():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            time.sleep(0.15)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_oracle_sample(cfg, min_seconds=8.0, max_iters=20, zslab=64, seed=2000):
+    """The FP64 oracle, as it stands, on a z-slab of the same phantom (same
+    x-y extent, labels and parameters): iterations until min_seconds passed."""
+    import oracle
+    import synth
+    shape, nl, gen, _, _ = CONFIGS[cfg]
+    slab = (min(zslab, shape[0]),) + tuple(shape[1:])
+    if gen == "potts3d":
+        p = synth.potts3d_problem(seed=seed, nl=nl, shape=slab)
+    else:
+        p = synth.hmf_problem(seed=seed, shape=slab)
+    D = p.D.astype(np.float64)
+    S = None if p.S_field is None else p.S_field.astype(np.float64)
+    sn = None if p.s_node is None else p.s_node.astype(np.float64)
+    flat = gen == "potts3d"
+    if flat:
+        u, q = oracle.potts_init(p.spatial, p.n_leaf)
+    else:
+        dag = oracle.Dag(p.n_nodes, p.edges)
+        u, q = oracle.dag_init(p.spatial, dag)
+    its, t0 = 0, time.perf_counter()
+    while its < max_iters:
+        if flat:
+            oracle.potts_iterate(D, u, q, 1, p.c, p.tau, S_field=S, s_node=sn)
+        else:
+            oracle.dag_iterate(dag, D, u, q, 1, p.c, p.tau, S_field=S, s_node=sn)
+        its += 1
+        if time.perf_counter() - t0 >= min_seconds and its >= 2:
+            break
+    dt = time.perf_counter() - t0
+    vlu = its * int(np.prod(slab)) * p.n_nodes
+    return {"value": vlu / dt, "unit": "VLU/s", "cores": oracle.threads(), "kind": "oracle",
+            "sample": "%d FP64 iterations of Algorithm %s on a %dx%dx%d slab (%d labels) of the same phantom, %.1f s"
+                      % (its, "1" if flat else "2", slab[0], slab[1], slab[2], p.n_nodes, dt)}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    cfg = args.config
+    shape, nl, _, _, _ = CONFIGS[cfg]
+    samples = []
+    for s in range(args.warmup + args.steps):
+        r = cpu_oracle_sample(cfg, min_seconds=0.0, max_iters=1, zslab=32)
+        if s >= args.warmup:
+            samples.append(r)
+    vals = [r["value"] for r in samples]
+    v = statistics.median(vals)
+    nodes = nl if CONFIGS[cfg][2] == "potts3d" else 15
+    vlu_step = ITERS_PER_STEP * int(np.prod(shape)) * nodes
+    line = {"impl": "reference", "metric": "voxel-label updates/s (%s)" % cfg, "value": v, "unit": "VLU/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * vlu_step / v, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": cfg, "dims": list(shape), "labels": nl},
+            "cpu_baseline": {"value": v, "unit": "VLU/s", "cores": samples[0]["cores"], "kind": "oracle",
+                             "sample": "each step: " + samples[0]["sample"].split(", ")[0]},
+            "e2e": {"value": v, "unit": "VLU/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    import paper_1501_07844_gb300 as pfm
+    assert torch.cuda.is_available(), "bench.py needs a CUDA GPU"
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    cfg = args.config
+    shape, nl, gen, schedule, storage = CONFIGS[cfg]
+    if args.dims:
+        shape = (args.dims,) * 3
+    prob = make_problem(cfg, seed=2000 + rank, shape=shape)
+    D = torch.from_numpy(prob.D).cuda()
+    S = None if prob.S_field is None else torch.from_numpy(prob.S_field).cuda()
+    stream = torch.cuda.current_stream()
+    gp = pfm.Problem(D, S_field=S, s_node=prob.s_node, n_nodes=prob.n_nodes, edges=prob.edges,
+                     c=prob.c, tau=prob.tau, schedule=schedule, storage=storage,
+                     stream=stream.cuda_stream)
+    n = int(np.prod(shape))
+    vlu_step = ITERS_PER_STEP * n * prob.n_nodes
+    alg_bytes = algorithmic_bytes_per_iter(prob, storage, schedule)
+
+    def step():
+        gp.iterate(ITERS_PER_STEP)
+        return gp.energy()
+
+    for _ in range(args.warmup):
+        step()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches0 = gp.launches
+    barrier()
+    with ClockSampler(local) as clk:
+        t_start.record(stream)
+        for k in range(args.steps):
+            ev[k][0].record(stream)
+            gp.iterate(ITERS_PER_STEP)          # the dominant kernel, ITERS_PER_STEP launches
+            ev[k][1].record(stream)
+            gp.energy()                          # FP64 energy / dual (host reads 2 doubles)
+        t_end.record(stream)
+        barrier()
+    launches = gp.launches - launches0
+    elapsed = t_start.elapsed_time(t_end) / 1e3
+    kern_ms = sum(a.elapsed_time(b) for a, b in ev) / (args.steps * ITERS_PER_STEP)  # per iteration
+    if dist is not None:
+        t = torch.tensor([elapsed], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+    value = world * args.steps * vlu_step / elapsed
+
+    # end to end through the C ABI with pinned host buffers: upload D and S,
+    # iterate, energy, read the thresholded labelling back, every step
+    e2e = None
+    if not args.no_e2e:
+        hD = torch.from_numpy(prob.D).pin_memory()
+        hS = None if prob.S_field is None else torch.from_numpy(prob.S_field).pin_memory()
+        hL = torch.empty(prob.spatial, dtype=torch.int32).pin_memory()
+        h2d = hD.numel() * 4 + (0 if hS is None else hS.numel() * 4)
+        d2h = hL.numel() * 4 + 16
+        for _ in range(max(1, args.warmup)):
+            gp.set_data(hD, hS)
+            step()
+            gp.argmax(out=hL)
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            gp.set_data(hD, hS)
+            step()
+            gp.argmax(out=hL)
+        e1.record(stream)
+        barrier()
+        te = e0.elapsed_time(e1) / 1e3
+        if dist is not None:
+            t = torch.tensor([te], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            te = float(t.item())
+        e2e = {"value": world * args.steps * vlu_step / te, "unit": "VLU/s",
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    peak = peaks.get("hbm_gbs")
+    peak_src = "measured" if peak else "fallback"
+    peak = peak or 6800.0
+    achieved = alg_bytes / (kern_ms / 1e3) / 1e9
+    traffic = load_traffic(cfg)
+    kname = "fused_step_kernel" if schedule == 0 else "prox_inplace_kernel+flow_inplace_kernel"
+
+    gp.close()
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_oracle_sample(cfg)
+    line = {
+        "metric": "voxel-label updates/s, 3-D Potts 256^3 x 8 labels" if cfg == "potts3d" else
+                  "voxel-label updates/s (%s)" % cfg,
+        "value": value, "unit": "VLU/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if storage == 0 else "f32 math, bf16 u/q storage",
+        "data": "synthetic (seeded sphere phantom)",
+        "config": {"workload": cfg, "dims": list(shape), "labels": prob.n_leaf, "nodes": prob.n_nodes,
+                   "iters_per_step": ITERS_PER_STEP, "schedule": "fused" if schedule == 0 else "in-place",
+                   "c": prob.c, "tau": prob.tau, "norm": "iso", "grad_source": "normalised",
+                   "l2": "inputs larger than L2 (%.2f GB moved per iteration)" % (alg_bytes / 1e9),
+                   "parallelism": "independent volume per GPU" if world > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_source": peak_src, "traffic": traffic,
+                     "algorithmic_bytes_per_launch": alg_bytes, "kernel_ms_per_launch": kern_ms},
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

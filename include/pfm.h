@@ -1,0 +1,202 @@
+/*
+ * pfm.h -- C ABI of libpfm, a single-GPU (GB300, sm_103a) solver for the
+ * pseudo-flow continuous max-flow method of Baxter, Rajchl, Yuan and Peters,
+ * "A Proximal Bregman Projection Approach to Continuous Max-Flow Problems
+ * Using Entropic Distances" (arXiv 1501.07844).
+ *
+ * What one iteration computes (Algorithm 1 for the Potts model, Algorithm 2
+ * for DAG-structured and hierarchical models, Section 3):
+ *   excess      d_L(x) = D_L(x) + div q_L(x) + sum_{P in L.P} w_(P,L) d_P(x)
+ *               (Potts: d_L = D_L + div q_L)
+ *   label prox  u_L <- u_L exp(-d_L / c) / sum_L' u_L' exp(-d_L' / c)
+ *               over end-labels (Eq. potts_labelupdate, both forms)
+ *   flow step   q_A <- Proj_{|q_A| <= S_A} (q_A - c tau grad g_A),
+ *               g_A = sum_{L end-label} W_(A,L) u_L (Eq. potts_flowupdate and
+ *               the DAG flow update of Section 3.3)
+ * Discretisation (not fixed by the paper): unit grid, forward-difference
+ * gradient that is zero at the last index of each axis, divergence = minus
+ * its adjoint, capacity set the Euclidean ball (PFM_NORM_ISO) or the box
+ * (PFM_NORM_ANISO).  The source S carries no flow and d_S = 0.
+ *
+ * Conventions for every entry point:
+ *   - Spatial arrays are x fastest: index (z*ny + y)*nx + x; a 2-D problem
+ *     has ndim = 2 and dims[2] = 1.
+ *   - Per-label and per-node arrays are label-major: D and u are
+ *     [n_leaf][z][y][x]; flows are [n_nodes][ndim][z][y][x] with component 0
+ *     along x.  End-labels (nodes without children) are numbered in
+ *     ascending node id.
+ *   - "Host or device" pointers are copied with cudaMemcpyDefault (unified
+ *     addressing), so either kind works; pinned host memory is fastest.
+ *   - The library owns every device buffer of a problem.  Inputs are copied
+ *     at the call; the caller may free them afterwards.  Outputs go to
+ *     caller-owned memory.
+ *   - Work is queued on the CUDA stream given at creation (NULL = the legacy
+ *     default stream).  Entry points marked (sync) wait for that stream.
+ *   - No entry point aborts or traps.  Failures return a status and set a
+ *     thread-local message readable with pfm_last_error().  A CUDA error
+ *     returns PFM_ECUDA; the problem should then be destroyed.
+ */
+#ifndef PFM_H
+#define PFM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PFM_VERSION 1
+
+/* Symbols of the C ABI are the only ones the shared library exports. */
+#if defined(__GNUC__)
+#define PFM_API __attribute__((visibility("default")))
+#else
+#define PFM_API
+#endif
+
+typedef enum {
+    PFM_OK = 0,
+    PFM_EINVAL = 1,         /* bad argument, size or parameter */
+    PFM_EDAG = 2,           /* malformed label DAG */
+    PFM_ENOMEM = 3,         /* device allocation failed */
+    PFM_ECUDA = 4,          /* CUDA runtime or launch error */
+    PFM_ENONFINITE = 5,     /* NaN or Inf in inputs, energy or dual */
+    PFM_ETIMEOUT = 6,       /* a bounded device-side wait expired */
+    PFM_ENOTCONVERGED = 7,  /* gap target not met within max_iters */
+    PFM_EUNSUPPORTED = 8    /* valid request this build does not implement */
+} pfm_status;
+
+enum { PFM_NORM_ISO = 0, PFM_NORM_ANISO = 1 };
+
+/* Which labelling the flow step differentiates.  NORMALISED: the normalised
+ * u after the prox step (the gradient of the smoothed objective
+ * Eq. potts_bregmanopt with respect to div q_L).  PAPER_LITERAL: the
+ * unnormalised u exp(-d/c) as Algorithms 1 and 2 print it. */
+enum { PFM_GRAD_NORMALISED = 0, PFM_GRAD_PAPER_LITERAL = 1 };
+
+/* Storage type of the labelling u and the flows q (arithmetic is FP32;
+ * D and S are always stored in FP32). */
+enum { PFM_STORAGE_F32 = 0, PFM_STORAGE_BF16 = 1 };
+
+/* PFM_SCHEDULE_FUSED: one kernel per iteration, u and q double-buffered
+ * (fewest bytes moved).  PFM_SCHEDULE_INPLACE: two kernels per iteration
+ * updating u and q in place (fewest buffers: the paper's memory argument). */
+enum { PFM_SCHEDULE_FUSED = 0, PFM_SCHEDULE_INPLACE = 1 };
+
+typedef struct {
+    double c;          /* entropic weight c > 0 (Eq. potts_bregmanopt) */
+    double tau;        /* gradient step tau > 0; the applied step is c*tau */
+    int norm;          /* PFM_NORM_* */
+    int grad_source;   /* PFM_GRAD_* */
+    int storage;       /* PFM_STORAGE_* */
+    int schedule;      /* PFM_SCHEDULE_* */
+    int check_every;   /* iterations between gap checks in pfm_run_to_gap */
+    double gap_tol;    /* relative gap target (E - P) / |E| */
+} pfm_params;
+
+/* Problem description.  Nodes 0..n_nodes-1 are the non-source labels; edge e
+ * goes from edge_parent[e] (-1 = the source S) to edge_child[e] with weight
+ * edge_w[e] > 0 (w_(parent,child) of Eq. dagmf_original).  The Potts model is
+ * the flat DAG (S -> every label, w = 1).  Requirements checked at creation
+ * (PFM_EDAG otherwise): indices in range, no self loop or cycle, every node
+ * has a parent, every end-label has path weight W_(S,L) = 1 (so that the
+ * end-label simplex of Section 3.3 is the constraint u_S = 1).
+ * Capacity of node A at voxel x: s_node[A] * S_field[x]; either may be NULL
+ * (then 1); values must be finite and >= 0.  D must be finite.  Data terms
+ * exist on end-labels only (Eq. dagmf_primal). */
+typedef struct {
+    int ndim;               /* 2 or 3 */
+    int64_t dims[3];        /* nx, ny, nz (nz = 1 for ndim = 2) */
+    int n_nodes;
+    int n_edges;
+    const int32_t* edge_parent;   /* host [n_edges] */
+    const int32_t* edge_child;    /* host [n_edges] */
+    const double* edge_w;         /* host [n_edges] */
+    const float* D;               /* host or device [n_leaf][z][y][x] */
+    const float* S_field;         /* host or device [z][y][x], or NULL */
+    const float* s_node;          /* host [n_nodes], or NULL */
+} pfm_desc;
+
+typedef struct pfm_problem pfm_problem;
+
+/* Library version (PFM_VERSION) and the last error message of this thread. */
+PFM_API int pfm_version(void);
+PFM_API const char* pfm_last_error(void);
+
+/* Fills *p with defaults: c = 0.5, tau = 0.11, ISO, NORMALISED, F32, FUSED,
+ * check_every = 10, gap_tol = 1e-4. */
+PFM_API void pfm_params_default(pfm_params* p);
+
+/* Host-only query (no GPU needed): device bytes and number of full-grid
+ * buffers (one value per voxel each) that pfm_create would allocate.
+ * n_leaf_out may be NULL.  Returns PFM_EDAG / PFM_EINVAL like pfm_create. */
+PFM_API pfm_status pfm_footprint(const pfm_desc* desc, const pfm_params* params,
+                         size_t* device_bytes, int64_t* n_grid_buffers, int* n_leaf_out);
+
+/* Validates desc and params, allocates device state on the current device,
+ * copies D and S, and initialises u_L = 1/#leaves, q = 0 (Algorithm 1 and
+ * Algorithm 2, first line; q is not initialised by the paper and is read as
+ * zero).  stream is a cudaStream_t (may be NULL).  (sync) */
+PFM_API pfm_status pfm_create(const pfm_desc* desc, const pfm_params* params, void* stream,
+                      pfm_problem** out);
+
+/* Frees every device buffer of the problem (after a stream sync).  NULL ok. */
+PFM_API void pfm_destroy(pfm_problem* pb);
+
+/* Replaces D (and S_field when the problem has one; pass NULL otherwise),
+ * host or device pointers, same shapes as at creation.  Does not reset u, q.
+ * Asynchronous on the problem's stream. */
+PFM_API pfm_status pfm_set_data(pfm_problem* pb, const float* D, const float* S_field);
+
+/* u_L = 1/#leaves, q = 0, iteration counter = 0.  Asynchronous. */
+PFM_API pfm_status pfm_reset(pfm_problem* pb);
+
+/* Queues n_iters >= 0 iterations (Algorithm 1 / Algorithm 2 loop body) on
+ * the problem's stream.  Asynchronous; errors of the launches are reported
+ * here, device-side non-finite values by the next pfm_energy. */
+PFM_API pfm_status pfm_iterate(pfm_problem* pb, int n_iters);
+
+/* Primal energy E(u) (Eq. potts_original / Eq. dagmf_original, inner-node
+ * labellings u_A = sum_L W_(A,L) u_L, TV norm matching params.norm) and
+ * pseudo-flow dual P(q) = sum_x min_L d_L(x) (Eq. potts_pseudo /
+ * Eq. dagmf_pseudo), accumulated in FP64.  P <= E for every feasible pair
+ * (weak duality).  (sync)  PFM_ENONFINITE if either is not finite. */
+PFM_API pfm_status pfm_energy(pfm_problem* pb, double* primal, double* dual);
+
+/* Iterates in blocks of params.check_every until (E - P)/|E| <= gap_tol or
+ * max_iters iterations were run; reports iterations run and the last gap.
+ * Returns PFM_ENOTCONVERGED (with valid outputs) if the target was missed.
+ * (sync) */
+PFM_API pfm_status pfm_run_to_gap(pfm_problem* pb, int max_iters, int* iters_done, double* rel_gap);
+
+/* Copies of the state into caller memory (host or device).  (sync)
+ *   labels: FP32 [n_leaf][z][y][x]
+ *   argmax: int32 [z][y][x], index of the largest u_L (ties: lowest index)
+ *   flows : FP32 [n_nodes][ndim][z][y][x] */
+PFM_API pfm_status pfm_get_labels(pfm_problem* pb, float* dst);
+PFM_API pfm_status pfm_get_argmax(pfm_problem* pb, int32_t* dst);
+PFM_API pfm_status pfm_get_flows(pfm_problem* pb, float* dst);
+
+/* Overwrites the state from caller memory (host or device), same layouts as
+ * the getters, converted to the storage type.  Flows are projected onto the
+ * capacity set and the normal component at the last index of each axis is
+ * set to zero (a feasible flow is stored unchanged).  Labellings must be
+ * finite and >= 0 with a positive sum per voxel (PFM_EINVAL otherwise) and
+ * are stored as given: the next label update normalises them, and a
+ * labelling read with pfm_get_labels resumes bit for bit.  (sync) */
+PFM_API pfm_status pfm_set_labels(pfm_problem* pb, const float* src);
+PFM_API pfm_status pfm_set_flows(pfm_problem* pb, const float* src);
+
+/* Problem shape queries. */
+PFM_API pfm_status pfm_shape(const pfm_problem* pb, int* ndim, int64_t dims[3], int* n_leaf, int* n_nodes);
+
+/* Iterations run since creation or the last reset, and kernels this problem
+ * has launched since creation (for launch accounting). */
+PFM_API int64_t pfm_iterations_done(const pfm_problem* pb);
+PFM_API int64_t pfm_launch_count(const pfm_problem* pb);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PFM_H */

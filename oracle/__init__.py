@@ -52,7 +52,13 @@ def lib():
                      "orc_dag_path_weights", "orc_bruteforce_binary"):
             getattr(_lib, name).restype = C.c_int
         _lib.orc_project.restype = None
+        _lib.orc_threads.restype = C.c_int
     return _lib
+
+
+def threads():
+    """OpenMP threads the oracle's sweeps use."""
+    return lib().orc_threads()
 
 
 def _grid(spatial):

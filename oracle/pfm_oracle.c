@@ -18,7 +18,19 @@
 #include <stdlib.h>
 #include <string.h>
 
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
 long orc_nvox(const orc_grid* g) { return g->nx * g->ny * g->nz; }
+
+int orc_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
 
 static double cap(const double* S_field, const double* s_node, int node, long i) {
     double s = s_node ? s_node[node] : 1.0;

@@ -57,6 +57,8 @@ typedef struct {
 } orc_dag;
 
 long orc_nvox(const orc_grid* g);
+/* Number of OpenMP threads the sweeps use (1 without OpenMP). */
+int orc_threads(void);
 
 /* Discrete operators. */
 void orc_grad(const orc_grid* g, const double* u, double* out /* [ndim][n] */);

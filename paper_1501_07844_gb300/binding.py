@@ -1,0 +1,284 @@
+"""ctypes binding of libpfm: argument marshalling only.
+
+``lib()`` returns the loaded library with argument and result types set for
+every function declared in ``include/pfm.h``; ``Problem`` wraps one
+``pfm_problem`` and accepts torch tensors (CUDA or pinned/CPU) or numpy
+arrays for inputs and outputs.  Layouts are those of ``pfm.h``:
+D / labels ``[n_leaf, *spatial]``, flows ``[n_nodes, ndim, *spatial]``,
+spatial ``(ny, nx)`` or ``(nz, ny, nx)`` with x fastest.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+ISO, ANISO = 0, 1
+NORMALISED, PAPER_LITERAL = 0, 1
+F32, BF16 = 0, 1
+FUSED, INPLACE = 0, 1
+
+_STATUS = {0: "PFM_OK", 1: "PFM_EINVAL", 2: "PFM_EDAG", 3: "PFM_ENOMEM", 4: "PFM_ECUDA", 5: "PFM_ENONFINITE",
+           6: "PFM_ETIMEOUT", 7: "PFM_ENOTCONVERGED", 8: "PFM_EUNSUPPORTED"}
+
+
+class PfmError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (_STATUS.get(status, status), msg))
+        self.status = status
+        self.name = _STATUS.get(status, str(status))
+
+
+class pfm_params(C.Structure):
+    _fields_ = [("c", C.c_double), ("tau", C.c_double), ("norm", C.c_int), ("grad_source", C.c_int),
+                ("storage", C.c_int), ("schedule", C.c_int), ("check_every", C.c_int), ("gap_tol", C.c_double)]
+
+
+class pfm_desc(C.Structure):
+    _fields_ = [("ndim", C.c_int), ("dims", C.c_int64 * 3), ("n_nodes", C.c_int), ("n_edges", C.c_int),
+                ("edge_parent", C.POINTER(C.c_int32)), ("edge_child", C.POINTER(C.c_int32)),
+                ("edge_w", C.POINTER(C.c_double)), ("D", C.c_void_p), ("S_field", C.c_void_p),
+                ("s_node", C.POINTER(C.c_float))]
+
+
+_P = C.c_void_p
+_SIGS = {
+    "pfm_version": (C.c_int, []),
+    "pfm_last_error": (C.c_char_p, []),
+    "pfm_params_default": (None, [C.POINTER(pfm_params)]),
+    "pfm_footprint": (C.c_int, [C.POINTER(pfm_desc), C.POINTER(pfm_params), C.POINTER(C.c_size_t),
+                                C.POINTER(C.c_int64), C.POINTER(C.c_int)]),
+    "pfm_create": (C.c_int, [C.POINTER(pfm_desc), C.POINTER(pfm_params), _P, C.POINTER(_P)]),
+    "pfm_destroy": (None, [_P]),
+    "pfm_set_data": (C.c_int, [_P, _P, _P]),
+    "pfm_reset": (C.c_int, [_P]),
+    "pfm_iterate": (C.c_int, [_P, C.c_int]),
+    "pfm_energy": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "pfm_run_to_gap": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
+    "pfm_get_labels": (C.c_int, [_P, _P]),
+    "pfm_get_argmax": (C.c_int, [_P, _P]),
+    "pfm_get_flows": (C.c_int, [_P, _P]),
+    "pfm_set_labels": (C.c_int, [_P, _P]),
+    "pfm_set_flows": (C.c_int, [_P, _P]),
+    "pfm_shape": (C.c_int, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int64), C.POINTER(C.c_int),
+                            C.POINTER(C.c_int)]),
+    "pfm_iterations_done": (C.c_int64, [_P]),
+    "pfm_launch_count": (C.c_int64, [_P]),
+}
+
+_lib = None
+
+
+def library_path():
+    return _build.LIB
+
+
+def lib():
+    """Build (if stale) and load libpfm.so; raises if it cannot be loaded."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError("libpfm.so is missing at %s" % path)
+        L = C.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def check(status):
+    if status != 0:
+        raise PfmError(status, lib().pfm_last_error().decode(errors="replace"))
+    return status
+
+
+def _ptr(a):
+    """Address of a torch tensor or numpy array (must be contiguous)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        assert a.flags.c_contiguous
+        return a.ctypes.data
+    assert a.is_contiguous()
+    return a.data_ptr()
+
+
+def _as_f32(a):
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return np.ascontiguousarray(a, dtype=np.float32)
+    import torch
+    return a.to(torch.float32).contiguous()
+
+
+def _stream_handle(stream):
+    if stream is not None:
+        return stream
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except Exception:  # pragma: no cover - torch absent
+        pass
+    return None
+
+
+def params(c=0.5, tau=0.11, norm=ISO, grad_source=NORMALISED, storage=F32, schedule=FUSED, check_every=10,
+           gap_tol=1e-4):
+    p = pfm_params()
+    lib().pfm_params_default(C.byref(p))
+    p.c, p.tau, p.norm, p.grad_source = float(c), float(tau), int(norm), int(grad_source)
+    p.storage, p.schedule, p.check_every, p.gap_tol = int(storage), int(schedule), int(check_every), float(gap_tol)
+    return p
+
+
+class _Desc:
+    """Keeps the host arrays a pfm_desc points at alive."""
+
+    def __init__(self, spatial, n_nodes, edges, D_ptr, S_ptr, s_node):
+        spatial = tuple(int(s) for s in spatial)
+        self.ndim = len(spatial)
+        if self.ndim not in (2, 3):
+            raise ValueError("spatial shape must be 2-D or 3-D")
+        nx, ny, nz = spatial[-1], spatial[-2], (spatial[0] if self.ndim == 3 else 1)
+        self.parent = np.array([e[0] for e in edges], dtype=np.int32)
+        self.child = np.array([e[1] for e in edges], dtype=np.int32)
+        self.w = np.array([e[2] for e in edges], dtype=np.float64)
+        self.s_node = None if s_node is None else np.ascontiguousarray(np.asarray(s_node, dtype=np.float32))
+        d = pfm_desc()
+        d.ndim = self.ndim
+        d.dims[0], d.dims[1], d.dims[2] = nx, ny, nz
+        d.n_nodes = int(n_nodes)
+        d.n_edges = len(edges)
+        d.edge_parent = self.parent.ctypes.data_as(C.POINTER(C.c_int32))
+        d.edge_child = self.child.ctypes.data_as(C.POINTER(C.c_int32))
+        d.edge_w = self.w.ctypes.data_as(C.POINTER(C.c_double))
+        d.D = D_ptr
+        d.S_field = S_ptr
+        d.s_node = None if self.s_node is None else self.s_node.ctypes.data_as(C.POINTER(C.c_float))
+        self.c = d
+
+
+def footprint(spatial, n_nodes, edges, has_S_field=False, s_node=None, **kw):
+    """(device bytes, number of full-grid buffers, n_leaf) pfm_create would allocate (host-only)."""
+    dummy = C.c_void_p(1)  # D / S pointers are not dereferenced by pfm_footprint
+    d = _Desc(spatial, n_nodes, edges, dummy, dummy if has_S_field else None, s_node)
+    p = params(**kw)
+    nb, nbuf, nl = C.c_size_t(), C.c_int64(), C.c_int()
+    check(lib().pfm_footprint(C.byref(d.c), C.byref(p), C.byref(nb), C.byref(nbuf), C.byref(nl)))
+    return nb.value, nbuf.value, nl.value
+
+
+class Problem:
+    """One solver instance (``pfm_create`` ... ``pfm_destroy``).
+
+    D: [n_leaf, *spatial] float32 (torch CUDA/CPU tensor or numpy array);
+    S_field: [*spatial] or None; s_node: [n_nodes] or None;
+    edges: [(parent, child, w)], parent -1 = source; default = Potts (flat).
+    """
+
+    def __init__(self, D, S_field=None, s_node=None, n_nodes=None, edges=None, stream=None, **kw):
+        D = _as_f32(D)
+        S_field = _as_f32(S_field)
+        nl = D.shape[0]
+        if edges is None:
+            n_nodes, edges = nl, [(-1, L, 1.0) for L in range(nl)]
+        self.spatial = tuple(D.shape[1:])
+        self.n_nodes = int(n_nodes)
+        self.stream = _stream_handle(stream)
+        self._desc = _Desc(self.spatial, n_nodes, edges, _ptr(D), _ptr(S_field), s_node)
+        self._params = params(**kw)
+        h = C.c_void_p()
+        check(lib().pfm_create(C.byref(self._desc.c), C.byref(self._params), self.stream, C.byref(h)))
+        self._h = h
+        nd, dims, nleaf, nnod = C.c_int(), (C.c_int64 * 3)(), C.c_int(), C.c_int()
+        check(lib().pfm_shape(self._h, C.byref(nd), dims, C.byref(nleaf), C.byref(nnod)))
+        self.ndim, self.n_leaf = nd.value, nleaf.value
+        self.has_S_field = S_field is not None
+
+    # -- lifecycle
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().pfm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- solver calls
+    def reset(self):
+        check(lib().pfm_reset(self._h))
+
+    def set_data(self, D, S_field=None):
+        D, S_field = _as_f32(D), _as_f32(S_field)
+        check(lib().pfm_set_data(self._h, _ptr(D), _ptr(S_field)))
+
+    def iterate(self, n):
+        check(lib().pfm_iterate(self._h, int(n)))
+
+    def energy(self):
+        E, P = C.c_double(), C.c_double()
+        check(lib().pfm_energy(self._h, C.byref(E), C.byref(P)))
+        return E.value, P.value
+
+    def run_to_gap(self, max_iters):
+        it, gap = C.c_int(), C.c_double()
+        st = lib().pfm_run_to_gap(self._h, int(max_iters), C.byref(it), C.byref(gap))
+        if st not in (0, 7):
+            check(st)
+        return it.value, gap.value, st == 0
+
+    @property
+    def iterations(self):
+        return lib().pfm_iterations_done(self._h)
+
+    @property
+    def launches(self):
+        return lib().pfm_launch_count(self._h)
+
+    # -- state in / out (dst / src: torch CUDA tensor, pinned CPU tensor or numpy)
+    def _out(self, shape, dtype, out):
+        if out is not None:
+            return out
+        import torch
+        return torch.empty(shape, dtype=dtype, device="cuda")
+
+    def labels(self, out=None):
+        import torch
+        out = self._out((self.n_leaf,) + self.spatial, torch.float32, out)
+        check(lib().pfm_get_labels(self._h, _ptr(out)))
+        return out
+
+    def argmax(self, out=None):
+        import torch
+        out = self._out(self.spatial, torch.int32, out)
+        check(lib().pfm_get_argmax(self._h, _ptr(out)))
+        return out
+
+    def flows(self, out=None):
+        import torch
+        out = self._out((self.n_nodes, self.ndim) + self.spatial, torch.float32, out)
+        check(lib().pfm_get_flows(self._h, _ptr(out)))
+        return out
+
+    def set_labels(self, u):
+        u = _as_f32(u)
+        check(lib().pfm_set_labels(self._h, _ptr(u)))
+
+    def set_flows(self, q):
+        q = _as_f32(q)
+        check(lib().pfm_set_flows(self._h, _ptr(q)))

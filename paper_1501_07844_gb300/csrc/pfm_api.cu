@@ -1,0 +1,599 @@
+// pfm_api.cu -- the C ABI of libpfm (declared in include/pfm.h).
+//
+// Owns device state, validates problems (the label DAG of Section 3.3 and
+// the data), picks a kernel bucket, and queues iterations, energy/gap
+// reductions and readbacks on the problem's CUDA stream.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "../../include/pfm.h"
+#include "pfm_solver.cuh"
+
+namespace {
+
+thread_local std::string g_err;
+
+pfm_status fail(pfm_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+pfm_status cuda_fail(cudaError_t e, const char* where) {
+    const pfm_status st = (e == cudaErrorMemoryAllocation) ? PFM_ENOMEM : PFM_ECUDA;
+    return fail(st, "%s: %s", where, cudaGetErrorString(e));
+}
+
+#define PFM_CUDA(call, where)                         \
+    do {                                              \
+        cudaError_t e_ = (call);                      \
+        if (e_ != cudaSuccess) return cuda_fail(e_, where); \
+    } while (0)
+
+// Validated, host-side description of a label DAG.
+struct DagInfo {
+    int nn = 0, nl = 0;
+    bool flat = false;               // the Potts model: S -> every node, w = 1
+    std::vector<int> leaf_node;      // end-label j -> node id (ascending)
+    std::vector<double> W;           // [nn][nn] path weights W_(A,B)
+};
+
+// Checks the DAG of a problem description and computes path weights
+// W_(A,B) (Section 3.3 recursion) and the end-label list.
+pfm_status analyse_dag(const pfm_desc* d, DagInfo* out) {
+    const int nn = d->n_nodes, ne = d->n_edges;
+    if (nn < 1 || ne < 1 || !d->edge_parent || !d->edge_child || !d->edge_w)
+        return fail(PFM_EDAG, "DAG needs n_nodes >= 1 and n_edges >= 1 with edge arrays");
+    std::vector<int> indeg(nn, 0), nchild(nn, 0), rem(nn, 0);
+    for (int e = 0; e < ne; ++e) {
+        const int a = d->edge_parent[e], b = d->edge_child[e];
+        const double w = d->edge_w[e];
+        if (a < -1 || a >= nn || b < 0 || b >= nn || a == b)
+            return fail(PFM_EDAG, "edge %d (%d -> %d) out of range or self loop", e, a, b);
+        if (!(w > 0.0) || !isfinite(w)) return fail(PFM_EDAG, "edge %d weight must be finite and > 0", e);
+        indeg[b]++;
+        if (a >= 0) {
+            nchild[a]++;
+            rem[b]++;
+        }
+    }
+    for (int v = 0; v < nn; ++v)
+        if (indeg[v] == 0) return fail(PFM_EDAG, "node %d has no parent (unreachable from the source)", v);
+    // topological order (Kahn), source edges satisfied from the start
+    std::vector<int> order;
+    order.reserve(nn);
+    for (int v = 0; v < nn; ++v)
+        if (rem[v] == 0) order.push_back(v);
+    for (size_t h = 0; h < order.size(); ++h) {
+        const int v = order[h];
+        for (int e = 0; e < ne; ++e)
+            if (d->edge_parent[e] == v && --rem[d->edge_child[e]] == 0) order.push_back(d->edge_child[e]);
+    }
+    if ((int)order.size() != nn) return fail(PFM_EDAG, "label graph has a cycle");
+    out->nn = nn;
+    out->leaf_node.clear();
+    for (int v = 0; v < nn; ++v)
+        if (nchild[v] == 0) out->leaf_node.push_back(v);
+    out->nl = (int)out->leaf_node.size();
+    out->W.assign((size_t)nn * nn, 0.0);
+    for (int k = nn - 1; k >= 0; --k) {
+        const int A = order[k];
+        out->W[(size_t)A * nn + A] = 1.0;
+        for (int e = 0; e < ne; ++e)
+            if (d->edge_parent[e] == A)
+                for (int B = 0; B < nn; ++B)
+                    out->W[(size_t)A * nn + B] += d->edge_w[e] * out->W[(size_t)d->edge_child[e] * nn + B];
+    }
+    // W_(S,L) = 1 for every end-label: sum_L u_L = 1 is then u_S = 1
+    for (int L : out->leaf_node) {
+        double ws = 0.0;
+        for (int e = 0; e < ne; ++e)
+            if (d->edge_parent[e] == -1) ws += d->edge_w[e] * out->W[(size_t)d->edge_child[e] * nn + L];
+        if (fabs(ws - 1.0) > 1e-9)
+            return fail(PFM_EDAG, "end-label %d has source path weight %.12g (must be 1)", L, ws);
+    }
+    out->flat = (ne == nn);
+    for (int e = 0; e < ne && out->flat; ++e)
+        out->flat = d->edge_parent[e] == -1 && d->edge_w[e] == 1.0;
+    return PFM_OK;
+}
+
+int potts_bucket(int nl) { return nl <= 4 ? 4 : nl <= 8 ? 8 : nl <= 16 ? 16 : 0; }
+void dag_bucket(int nl, int nn, int* ml, int* mn) {
+    *ml = *mn = 0;
+    if (nl <= 8 && nn <= 12) {
+        *ml = 8;
+        *mn = 12;
+    } else if (nl <= 16 && nn <= 16) {
+        *ml = 16;
+        *mn = 16;
+    }
+}
+
+pfm_status check_params(const pfm_params* p) {
+    if (!p) return fail(PFM_EINVAL, "params is NULL");
+    if (!(p->c > 0) || !isfinite(p->c)) return fail(PFM_EINVAL, "c must be finite and > 0");
+    if (!(p->tau > 0) || !isfinite(p->tau)) return fail(PFM_EINVAL, "tau must be finite and > 0");
+    if (p->norm != PFM_NORM_ISO && p->norm != PFM_NORM_ANISO) return fail(PFM_EINVAL, "bad norm");
+    if (p->grad_source != PFM_GRAD_NORMALISED && p->grad_source != PFM_GRAD_PAPER_LITERAL)
+        return fail(PFM_EINVAL, "bad grad_source");
+    if (p->storage != PFM_STORAGE_F32 && p->storage != PFM_STORAGE_BF16) return fail(PFM_EINVAL, "bad storage");
+    if (p->schedule != PFM_SCHEDULE_FUSED && p->schedule != PFM_SCHEDULE_INPLACE)
+        return fail(PFM_EINVAL, "bad schedule");
+    if (p->check_every < 1) return fail(PFM_EINVAL, "check_every must be >= 1");
+    return PFM_OK;
+}
+
+pfm_status check_desc(const pfm_desc* d, DagInfo* dag) {
+    if (!d) return fail(PFM_EINVAL, "desc is NULL");
+    if (d->ndim != 2 && d->ndim != 3) return fail(PFM_EINVAL, "ndim must be 2 or 3");
+    for (int k = 0; k < 3; ++k)
+        if (d->dims[k] < 1 || d->dims[k] > (1 << 30)) return fail(PFM_EINVAL, "dims[%d] out of range", k);
+    if (d->ndim == 2 && d->dims[2] != 1) return fail(PFM_EINVAL, "2-D problems need dims[2] == 1");
+    const long long n = (long long)d->dims[0] * d->dims[1] * d->dims[2];
+    if (n > (1ll << 40)) return fail(PFM_EINVAL, "grid too large");
+    if (!d->D) return fail(PFM_EINVAL, "D is NULL");
+    pfm_status st = analyse_dag(d, dag);
+    if (st != PFM_OK) return st;
+    if (d->s_node)
+        for (int A = 0; A < d->n_nodes; ++A)
+            if (!(d->s_node[A] >= 0.f) || !isfinite(d->s_node[A]))
+                return fail(PFM_EINVAL, "s_node[%d] must be finite and >= 0", A);
+    if (dag->flat) {
+        if (!potts_bucket(dag->nl)) return fail(PFM_EUNSUPPORTED, "Potts supports at most 16 labels");
+    } else {
+        int ml, mn;
+        dag_bucket(dag->nl, dag->nn, &ml, &mn);
+        if (!ml) return fail(PFM_EUNSUPPORTED, "DAG models support at most 16 end-labels and 16 nodes");
+    }
+    return PFM_OK;
+}
+
+size_t elem_size(int storage) { return storage == PFM_STORAGE_F32 ? 4 : 2; }
+
+}  // namespace
+
+struct pfm_problem {
+    int ndim = 0, nx = 0, ny = 0, nz = 0, nl = 0, nn = 0;
+    long long n = 0;
+    bool flat = true;
+    pfm_params prm{};
+    cudaStream_t stream = nullptr;
+    void* u[2] = {nullptr, nullptr};
+    void* q[2] = {nullptr, nullptr};
+    int cur = 0;
+    float* D = nullptr;
+    float* S = nullptr;
+    float* abuf = nullptr;
+    float* snode_dev = nullptr;
+    unsigned* flags = nullptr;
+    double* partial = nullptr;
+    double* result = nullptr;
+    int energy_blocks = 0;
+    int zc = 32;
+    std::vector<float> s_node;
+    std::vector<float> W;  // [nn][nl]
+    int64_t iters = 0, launches = 0;
+    pfm::SolverBase* solver = nullptr;
+};
+
+namespace {
+
+pfm_status read_flags(pfm_problem* pb, unsigned* out) {
+    unsigned h = 0;
+    PFM_CUDA(cudaMemcpyAsync(&h, pb->flags, sizeof h, cudaMemcpyDeviceToHost, pb->stream), "read flags");
+    PFM_CUDA(cudaStreamSynchronize(pb->stream), "stream sync");
+    *out = h;
+    return PFM_OK;
+}
+
+pfm_status flags_status(unsigned f) {
+    if (f & pfm::FLAG_BAD_INPUT) return fail(PFM_ENONFINITE, "D not finite or S negative / not finite");
+    if (f & pfm::FLAG_NONFINITE) return fail(PFM_ENONFINITE, "non-finite normaliser, energy or dual");
+    if (f & pfm::FLAG_BAD_LABELS) return fail(PFM_EINVAL, "labelling with a negative entry or zero sum");
+    return PFM_OK;
+}
+
+void free_all(pfm_problem* pb) {
+    void* ptrs[] = {pb->u[0], pb->u[1], pb->q[0], pb->q[1], pb->D, pb->S, pb->abuf, pb->snode_dev,
+                    pb->flags, pb->partial, pb->result};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    delete pb->solver;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pfm_version(void) { return PFM_VERSION; }
+
+const char* pfm_last_error(void) { return g_err.c_str(); }
+
+void pfm_params_default(pfm_params* p) {
+    if (!p) return;
+    p->c = 0.5;
+    p->tau = 0.11;
+    p->norm = PFM_NORM_ISO;
+    p->grad_source = PFM_GRAD_NORMALISED;
+    p->storage = PFM_STORAGE_F32;
+    p->schedule = PFM_SCHEDULE_FUSED;
+    p->check_every = 10;
+    p->gap_tol = 1e-4;
+}
+
+pfm_status pfm_footprint(const pfm_desc* desc, const pfm_params* params, size_t* device_bytes,
+                         int64_t* n_grid_buffers, int* n_leaf_out) {
+    DagInfo dag;
+    pfm_status st = check_params(params);
+    if (st != PFM_OK) return st;
+    st = check_desc(desc, &dag);
+    if (st != PFM_OK) return st;
+    const long long n = (long long)desc->dims[0] * desc->dims[1] * desc->dims[2];
+    const int copies = params->schedule == PFM_SCHEDULE_FUSED ? 2 : 1;
+    const size_t ts = elem_size(params->storage);
+    int64_t bufs = 0;
+    size_t bytes = 0;
+    bufs += (int64_t)copies * dag.nl;                       // u
+    bytes += (size_t)copies * dag.nl * n * ts;
+    bufs += (int64_t)copies * dag.nn * desc->ndim;          // q
+    bytes += (size_t)copies * dag.nn * desc->ndim * n * ts;
+    bufs += dag.nl;                                          // D
+    bytes += (size_t)dag.nl * n * 4;
+    if (desc->S_field) {
+        bufs += 1;
+        bytes += (size_t)n * 4;
+    }
+    if (params->schedule == PFM_SCHEDULE_INPLACE && params->grad_source == PFM_GRAD_PAPER_LITERAL) {
+        bufs += 1;                                           // accumulator a(x)
+        bytes += (size_t)n * 4;
+    }
+    if (device_bytes) *device_bytes = bytes;
+    if (n_grid_buffers) *n_grid_buffers = bufs;
+    if (n_leaf_out) *n_leaf_out = dag.nl;
+    return PFM_OK;
+}
+
+pfm_status pfm_create(const pfm_desc* desc, const pfm_params* params, void* stream, pfm_problem** out) {
+    if (!out) return fail(PFM_EINVAL, "out is NULL");
+    *out = nullptr;
+    DagInfo dag;
+    pfm_status st = check_params(params);
+    if (st != PFM_OK) return st;
+    st = check_desc(desc, &dag);
+    if (st != PFM_OK) return st;
+
+    pfm_problem* pb = new pfm_problem();
+    pb->ndim = desc->ndim;
+    pb->nx = (int)desc->dims[0];
+    pb->ny = (int)desc->dims[1];
+    pb->nz = (int)desc->dims[2];
+    pb->n = (long long)pb->nx * pb->ny * pb->nz;
+    pb->nl = dag.nl;
+    pb->nn = dag.nn;
+    pb->flat = dag.flat;
+    pb->prm = *params;
+    pb->stream = (cudaStream_t)stream;
+    pb->s_node.assign(pb->nn, 1.0f);
+    if (desc->s_node)
+        for (int A = 0; A < pb->nn; ++A) pb->s_node[A] = desc->s_node[A];
+    pb->W.assign((size_t)pb->nn * pb->nl, 0.f);
+    for (int A = 0; A < pb->nn; ++A)
+        for (int j = 0; j < pb->nl; ++j) pb->W[(size_t)A * pb->nl + j] = (float)dag.W[(size_t)A * pb->nn + dag.leaf_node[j]];
+
+    auto bail = [&](pfm_status s) {
+        free_all(pb);
+        delete pb;
+        return s;
+    };
+    const size_t ts = elem_size(params->storage);
+    const long long n = pb->n;
+    const bool fused = params->schedule == PFM_SCHEDULE_FUSED;
+    const bool need_abuf = !fused && params->grad_source == PFM_GRAD_PAPER_LITERAL;
+    cudaError_t e;
+    for (int k = 0; k < (fused ? 2 : 1); ++k) {
+        if ((e = cudaMalloc(&pb->u[k], (size_t)pb->nl * n * ts)) != cudaSuccess) return bail(cuda_fail(e, "alloc u"));
+        if ((e = cudaMalloc(&pb->q[k], (size_t)pb->nn * pb->ndim * n * ts)) != cudaSuccess)
+            return bail(cuda_fail(e, "alloc q"));
+    }
+    if (!fused) {
+        pb->u[1] = pb->u[0];
+        pb->q[1] = pb->q[0];
+    }
+    if ((e = cudaMalloc(&pb->D, (size_t)pb->nl * n * 4)) != cudaSuccess) return bail(cuda_fail(e, "alloc D"));
+    if (desc->S_field && (e = cudaMalloc(&pb->S, (size_t)n * 4)) != cudaSuccess) return bail(cuda_fail(e, "alloc S"));
+    if (need_abuf && (e = cudaMalloc(&pb->abuf, (size_t)n * 4)) != cudaSuccess) return bail(cuda_fail(e, "alloc a"));
+    pb->energy_blocks = (int)std::min<long long>((n + pfm::ENERGY_NT - 1) / pfm::ENERGY_NT, 152 * 8);
+    if ((e = cudaMalloc(&pb->snode_dev, sizeof(float) * pb->nn)) != cudaSuccess) return bail(cuda_fail(e, "alloc"));
+    if ((e = cudaMalloc(&pb->flags, sizeof(unsigned))) != cudaSuccess) return bail(cuda_fail(e, "alloc"));
+    if ((e = cudaMalloc(&pb->partial, sizeof(double) * 2 * pb->energy_blocks)) != cudaSuccess)
+        return bail(cuda_fail(e, "alloc"));
+    if ((e = cudaMalloc(&pb->result, sizeof(double) * 2)) != cudaSuccess) return bail(cuda_fail(e, "alloc"));
+
+    cudaStream_t s = pb->stream;
+    if ((e = cudaMemsetAsync(pb->flags, 0, sizeof(unsigned), s)) != cudaSuccess) return bail(cuda_fail(e, "memset"));
+    if ((e = cudaMemcpyAsync(pb->D, desc->D, (size_t)pb->nl * n * 4, cudaMemcpyDefault, s)) != cudaSuccess)
+        return bail(cuda_fail(e, "copy D"));
+    if (pb->S && (e = cudaMemcpyAsync(pb->S, desc->S_field, (size_t)n * 4, cudaMemcpyDefault, s)) != cudaSuccess)
+        return bail(cuda_fail(e, "copy S"));
+    if ((e = cudaMemcpyAsync(pb->snode_dev, pb->s_node.data(), sizeof(float) * pb->nn, cudaMemcpyHostToDevice, s)) !=
+        cudaSuccess)
+        return bail(cuda_fail(e, "copy s_node"));
+    if ((e = pfm::launch_validate(pb->D, (long long)pb->nl * n, pb->S, n, pb->flags, s)) != cudaSuccess)
+        return bail(cuda_fail(e, "validate"));
+    pb->launches++;
+
+    pfm::ProblemView v{};
+    v.ndim = pb->ndim;
+    v.nx = pb->nx;
+    v.ny = pb->ny;
+    v.nz = pb->nz;
+    v.nl = pb->nl;
+    v.nn = pb->nn;
+    v.n = n;
+    v.c = (float)params->c;
+    v.tau = (float)params->tau;
+    v.literal = params->grad_source == PFM_GRAD_PAPER_LITERAL;
+    v.aniso = params->norm == PFM_NORM_ANISO;
+    v.D = pb->D;
+    v.S = pb->S;
+    v.abuf = pb->abuf;
+    v.flags = pb->flags;
+    v.s_node = pb->s_node.data();
+    v.W = pb->W.data();
+    const bool bf16 = params->storage == PFM_STORAGE_BF16;
+    if (pb->flat) {
+        const int ml = potts_bucket(pb->nl);
+        pb->solver = bf16 ? pfm::make_potts_bf16(ml, pb->ndim, v) : pfm::make_potts_f32(ml, pb->ndim, v);
+    } else {
+        int ml, mn;
+        dag_bucket(pb->nl, pb->nn, &ml, &mn);
+        pb->solver = bf16 ? pfm::make_dag_bf16(ml, mn, pb->ndim, v) : pfm::make_dag_f32(ml, mn, pb->ndim, v);
+    }
+    if (!pb->solver) return bail(fail(PFM_EUNSUPPORTED, "no kernel bucket for this problem"));
+    // z-chunk of the fused kernel: aim at >= ~2000 CTAs on large volumes
+    {
+        const long long tiles = (long long)((pb->nx + pfm::FTX - 1) / pfm::FTX) * ((pb->ny + pfm::FTY - 1) / pfm::FTY);
+        long long zc = (tiles * pb->nz) / 2048;
+        pb->zc = (int)std::max<long long>(4, std::min<long long>(64, zc));
+    }
+    st = pfm_reset(pb);
+    if (st != PFM_OK) return bail(st);
+    unsigned f = 0;
+    st = read_flags(pb, &f);
+    if (st != PFM_OK) return bail(st);
+    if (f & pfm::FLAG_BAD_INPUT) return bail(fail(PFM_ENONFINITE, "D not finite or S negative / not finite"));
+    *out = pb;
+    return PFM_OK;
+}
+
+void pfm_destroy(pfm_problem* pb) {
+    if (!pb) return;
+    cudaStreamSynchronize(pb->stream);
+    free_all(pb);
+    delete pb;
+}
+
+pfm_status pfm_set_data(pfm_problem* pb, const float* D, const float* S_field) {
+    if (!pb || !D) return fail(PFM_EINVAL, "NULL argument");
+    if ((S_field != nullptr) != (pb->S != nullptr))
+        return fail(PFM_EINVAL, "S_field must be given iff the problem was created with one");
+    PFM_CUDA(cudaMemcpyAsync(pb->D, D, (size_t)pb->nl * pb->n * 4, cudaMemcpyDefault, pb->stream), "copy D");
+    if (S_field) PFM_CUDA(cudaMemcpyAsync(pb->S, S_field, (size_t)pb->n * 4, cudaMemcpyDefault, pb->stream), "copy S");
+    PFM_CUDA(pfm::launch_validate(pb->D, (long long)pb->nl * pb->n, pb->S, pb->n, pb->flags, pb->stream), "validate");
+    pb->launches++;
+    return PFM_OK;
+}
+
+pfm_status pfm_reset(pfm_problem* pb) {
+    if (!pb) return fail(PFM_EINVAL, "NULL problem");
+    const size_t ts = elem_size(pb->prm.storage);
+    pb->cur = 0;
+    PFM_CUDA(pfm::launch_init_labels(pb->u[0], pb->prm.storage, pb->nl, pb->n, pb->stream), "init u");
+    pb->launches++;
+    PFM_CUDA(cudaMemsetAsync(pb->q[0], 0, (size_t)pb->nn * pb->ndim * pb->n * ts, pb->stream), "init q");
+    pb->iters = 0;
+    return PFM_OK;
+}
+
+pfm_status pfm_iterate(pfm_problem* pb, int n_iters) {
+    if (!pb) return fail(PFM_EINVAL, "NULL problem");
+    if (n_iters < 0) return fail(PFM_EINVAL, "n_iters must be >= 0");
+    const bool fused = pb->prm.schedule == PFM_SCHEDULE_FUSED;
+    for (int it = 0; it < n_iters; ++it) {
+        const int src = pb->cur, dst = fused ? 1 - pb->cur : pb->cur;
+        int nlaunch = 0;
+        cudaError_t e = pb->solver->step(pb->u[src], pb->u[dst], pb->q[src], pb->q[dst], fused, pb->zc, pb->stream,
+                                         &nlaunch);
+        pb->launches += nlaunch;
+        if (e != cudaSuccess) return cuda_fail(e, "iterate");
+        pb->cur = dst;
+        pb->iters++;
+    }
+    return PFM_OK;
+}
+
+pfm_status pfm_energy(pfm_problem* pb, double* primal, double* dual) {
+    if (!pb) return fail(PFM_EINVAL, "NULL problem");
+    PFM_CUDA(pb->solver->energy(pb->u[pb->cur], pb->q[pb->cur], pb->partial, pb->energy_blocks, pb->stream),
+             "energy");
+    PFM_CUDA(pfm::launch_energy_final(pb->partial, pb->energy_blocks, pb->result, pb->flags, pb->stream), "energy");
+    pb->launches += 2;
+    double h[2];
+    PFM_CUDA(cudaMemcpyAsync(h, pb->result, sizeof h, cudaMemcpyDeviceToHost, pb->stream), "read energy");
+    unsigned f = 0;
+    pfm_status st = read_flags(pb, &f);
+    if (st != PFM_OK) return st;
+    if (primal) *primal = h[0];
+    if (dual) *dual = h[1];
+    return flags_status(f);
+}
+
+pfm_status pfm_run_to_gap(pfm_problem* pb, int max_iters, int* iters_done, double* rel_gap) {
+    if (!pb) return fail(PFM_EINVAL, "NULL problem");
+    int done = 0;
+    double gap = INFINITY;
+    pfm_status st = PFM_OK;
+    while (done < max_iters) {
+        const int k = std::min(pb->prm.check_every, max_iters - done);
+        st = pfm_iterate(pb, k);
+        if (st != PFM_OK) break;
+        done += k;
+        double E, P;
+        st = pfm_energy(pb, &E, &P);
+        if (st != PFM_OK) break;
+        gap = (E - P) / fabs(E);
+        if (gap <= pb->prm.gap_tol) break;
+    }
+    if (iters_done) *iters_done = done;
+    if (rel_gap) *rel_gap = gap;
+    if (st != PFM_OK) return st;
+    if (!(gap <= pb->prm.gap_tol)) return fail(PFM_ENOTCONVERGED, "gap %.3g above target after %d iterations", gap, done);
+    return PFM_OK;
+}
+
+pfm_status pfm_get_labels(pfm_problem* pb, float* dst) {
+    if (!pb || !dst) return fail(PFM_EINVAL, "NULL argument");
+    const long long count = (long long)pb->nl * pb->n;
+    if (pb->prm.storage == PFM_STORAGE_F32) {
+        PFM_CUDA(cudaMemcpyAsync(dst, pb->u[pb->cur], count * 4, cudaMemcpyDefault, pb->stream), "copy labels");
+    } else {
+        float* tmp = nullptr;
+        cudaPointerAttributes at{};
+        const bool dev = cudaPointerGetAttributes(&at, dst) == cudaSuccess && at.type == cudaMemoryTypeDevice;
+        cudaGetLastError();
+        if (dev) {
+            tmp = dst;
+        } else {
+            PFM_CUDA(cudaMallocAsync((void**)&tmp, count * 4, pb->stream), "alloc staging");
+        }
+        cudaError_t e = pfm::launch_to_f32(pb->u[pb->cur], pb->prm.storage, count, tmp, pb->stream);
+        pb->launches++;
+        if (e == cudaSuccess && !dev) e = cudaMemcpyAsync(dst, tmp, count * 4, cudaMemcpyDefault, pb->stream);
+        if (!dev) cudaFreeAsync(tmp, pb->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "labels");
+    }
+    PFM_CUDA(cudaStreamSynchronize(pb->stream), "stream sync");
+    return PFM_OK;
+}
+
+pfm_status pfm_get_flows(pfm_problem* pb, float* dst) {
+    if (!pb || !dst) return fail(PFM_EINVAL, "NULL argument");
+    const long long count = (long long)pb->nn * pb->ndim * pb->n;
+    if (pb->prm.storage == PFM_STORAGE_F32) {
+        PFM_CUDA(cudaMemcpyAsync(dst, pb->q[pb->cur], count * 4, cudaMemcpyDefault, pb->stream), "copy flows");
+    } else {
+        float* tmp = nullptr;
+        cudaPointerAttributes at{};
+        const bool dev = cudaPointerGetAttributes(&at, dst) == cudaSuccess && at.type == cudaMemoryTypeDevice;
+        cudaGetLastError();
+        if (dev) {
+            tmp = dst;
+        } else {
+            PFM_CUDA(cudaMallocAsync((void**)&tmp, count * 4, pb->stream), "alloc staging");
+        }
+        cudaError_t e = pfm::launch_to_f32(pb->q[pb->cur], pb->prm.storage, count, tmp, pb->stream);
+        pb->launches++;
+        if (e == cudaSuccess && !dev) e = cudaMemcpyAsync(dst, tmp, count * 4, cudaMemcpyDefault, pb->stream);
+        if (!dev) cudaFreeAsync(tmp, pb->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "flows");
+    }
+    PFM_CUDA(cudaStreamSynchronize(pb->stream), "stream sync");
+    return PFM_OK;
+}
+
+pfm_status pfm_get_argmax(pfm_problem* pb, int32_t* dst) {
+    if (!pb || !dst) return fail(PFM_EINVAL, "NULL argument");
+    cudaPointerAttributes at{};
+    const bool dev = cudaPointerGetAttributes(&at, dst) == cudaSuccess && at.type == cudaMemoryTypeDevice;
+    cudaGetLastError();
+    int* tmp = dev ? (int*)dst : nullptr;
+    if (!dev) PFM_CUDA(cudaMallocAsync((void**)&tmp, pb->n * 4, pb->stream), "alloc staging");
+    cudaError_t e = pfm::launch_argmax(pb->u[pb->cur], pb->prm.storage, pb->nl, pb->n, tmp, pb->stream);
+    pb->launches++;
+    if (e == cudaSuccess && !dev) e = cudaMemcpyAsync(dst, tmp, pb->n * 4, cudaMemcpyDefault, pb->stream);
+    if (!dev) cudaFreeAsync(tmp, pb->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "argmax");
+    PFM_CUDA(cudaStreamSynchronize(pb->stream), "stream sync");
+    return PFM_OK;
+}
+
+static pfm_status stage_in(pfm_problem* pb, const float* src, long long count, float** dev_out, bool* owned) {
+    cudaPointerAttributes at{};
+    const bool dev = cudaPointerGetAttributes(&at, src) == cudaSuccess && at.type == cudaMemoryTypeDevice;
+    cudaGetLastError();
+    *owned = !dev;
+    if (dev) {
+        *dev_out = (float*)src;
+        return PFM_OK;
+    }
+    PFM_CUDA(cudaMallocAsync((void**)dev_out, count * 4, pb->stream), "alloc staging");
+    PFM_CUDA(cudaMemcpyAsync(*dev_out, src, count * 4, cudaMemcpyDefault, pb->stream), "copy in");
+    return PFM_OK;
+}
+
+pfm_status pfm_set_labels(pfm_problem* pb, const float* src) {
+    if (!pb || !src) return fail(PFM_EINVAL, "NULL argument");
+    float* tmp;
+    bool owned;
+    pfm_status st = stage_in(pb, src, (long long)pb->nl * pb->n, &tmp, &owned);
+    if (st != PFM_OK) return st;
+    PFM_CUDA(cudaMemsetAsync(pb->flags, 0, sizeof(unsigned), pb->stream), "memset");
+    cudaError_t e = pfm::launch_set_labels(tmp, pb->prm.storage, pb->nl, pb->n, pb->u[pb->cur], pb->flags, pb->stream);
+    pb->launches++;
+    if (owned) cudaFreeAsync(tmp, pb->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "set labels");
+    unsigned f = 0;
+    st = read_flags(pb, &f);
+    if (st != PFM_OK) return st;
+    if (f) {
+        cudaMemsetAsync(pb->flags, 0, sizeof(unsigned), pb->stream);
+        cudaStreamSynchronize(pb->stream);
+    }
+    return flags_status(f);
+}
+
+pfm_status pfm_set_flows(pfm_problem* pb, const float* src) {
+    if (!pb || !src) return fail(PFM_EINVAL, "NULL argument");
+    float* tmp;
+    bool owned;
+    pfm_status st = stage_in(pb, src, (long long)pb->nn * pb->ndim * pb->n, &tmp, &owned);
+    if (st != PFM_OK) return st;
+    cudaError_t e = pfm::launch_set_flows(tmp, pb->prm.storage, pb->nn, pb->ndim, pb->nx, pb->ny, pb->nz,
+                                          pb->snode_dev, pb->S, pb->prm.norm == PFM_NORM_ANISO, pb->q[pb->cur],
+                                          pb->stream);
+    pb->launches++;
+    if (owned) cudaFreeAsync(tmp, pb->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "set flows");
+    PFM_CUDA(cudaStreamSynchronize(pb->stream), "stream sync");
+    return PFM_OK;
+}
+
+pfm_status pfm_shape(const pfm_problem* pb, int* ndim, int64_t dims[3], int* n_leaf, int* n_nodes) {
+    if (!pb) return fail(PFM_EINVAL, "NULL problem");
+    if (ndim) *ndim = pb->ndim;
+    if (dims) {
+        dims[0] = pb->nx;
+        dims[1] = pb->ny;
+        dims[2] = pb->nz;
+    }
+    if (n_leaf) *n_leaf = pb->nl;
+    if (n_nodes) *n_nodes = pb->nn;
+    return PFM_OK;
+}
+
+int64_t pfm_iterations_done(const pfm_problem* pb) { return pb ? pb->iters : -1; }
+int64_t pfm_launch_count(const pfm_problem* pb) { return pb ? pb->launches : -1; }
+
+}  // extern "C"

@@ -1,0 +1,14 @@
+// DAG / HMF kernel buckets (path-weight form of Algorithm 2), storage bf16.
+#include "pfm_solver.cuh"
+
+namespace pfm {
+
+SolverBase* make_dag_bf16(int maxl, int maxn, int dim, const ProblemView& v) {
+#define PFM_DAG(L, N, DM) \
+    if (maxl == L && maxn == N && dim == DM) return new Solver<L, N, DM, true, __nv_bfloat16>(v);
+    PFM_DAG(8, 12, 2) PFM_DAG(8, 12, 3) PFM_DAG(16, 16, 2) PFM_DAG(16, 16, 3)
+#undef PFM_DAG
+    return nullptr;
+}
+
+}  // namespace pfm

@@ -1,0 +1,200 @@
+// pfm_misc.cu -- auxiliary kernels: initialisation, readback, checkpoint
+// import, input validation and the final FP64 energy reduction.
+#include <math.h>
+
+#include "pfm_solver.cuh"
+
+namespace pfm {
+
+namespace {
+
+constexpr int NT = 256;
+
+inline unsigned blocks_for(long long count) { return (unsigned)((count + NT - 1) / NT); }
+
+// u_L = 1/#leaves (Algorithm 1 and Algorithm 2, first line).
+template <typename T>
+__global__ void init_labels_kernel(T* u, int nl, long long n) {
+    const long long i = (long long)blockIdx.x * NT + threadIdx.x;
+    if (i >= (long long)nl * n) return;
+    stv<T>(u + i, 1.0f / nl);
+}
+
+// Thresholding of the relaxed labelling: index of the largest u_L, ties to
+// the lowest index.
+template <typename T>
+__global__ void argmax_kernel(const T* u, int nl, long long n, int* out) {
+    const long long i = (long long)blockIdx.x * NT + threadIdx.x;
+    if (i >= n) return;
+    float best = ldv<T>(u + i);
+    int arg = 0;
+    for (int j = 1; j < nl; ++j) {
+        const float v = ldv<T>(u + (long long)j * n + i);
+        if (v > best) {
+            best = v;
+            arg = j;
+        }
+    }
+    out[i] = arg;
+}
+
+template <typename T>
+__global__ void to_f32_kernel(const T* src, long long count, float* dst) {
+    const long long i = (long long)blockIdx.x * NT + threadIdx.x;
+    if (i < count) dst[i] = ldv<T>(src + i);
+}
+
+// Checkpoint import of a labelling: entries must be finite and >= 0 with a
+// positive sum per voxel; stored as given (the label update is invariant to
+// a per-voxel scale, so a labelling read back resumes bit for bit).
+template <typename T>
+__global__ void set_labels_kernel(const float* src, int nl, long long n, T* dst, unsigned* flags) {
+    const long long i = (long long)blockIdx.x * NT + threadIdx.x;
+    if (i >= n) return;
+    float s = 0.f;
+    bool ok = true;
+    for (int j = 0; j < nl; ++j) {
+        const float v = src[(long long)j * n + i];
+        ok = ok && (v >= 0.f) && isfinite(v);
+        s += v;
+    }
+    ok = ok && s > 0.f && isfinite(s);
+    if (!ok) {
+        atomicOr(flags, FLAG_BAD_LABELS);
+        return;
+    }
+    for (int j = 0; j < nl; ++j) stv<T>(dst + (long long)j * n + i, src[(long long)j * n + i]);
+}
+
+// Checkpoint import of flows: zero normal flux at the last index of each
+// axis, then projection onto the capacity set.
+template <typename T>
+__global__ void set_flows_kernel(const float* src, int nn, int ndim, int nx, int ny, int nz,
+                                 const float* s_node, const float* S, int aniso, T* dst) {
+    const long long n = (long long)nx * ny * nz;
+    const long long gi = (long long)blockIdx.x * NT + threadIdx.x;
+    if (gi >= (long long)nn * n) return;
+    const int A = (int)(gi / n);
+    const long long i = gi % n;
+    const int x = (int)(i % nx);
+    const int y = (int)((i / nx) % ny);
+    const int z = (int)(i / ((long long)nx * ny));
+    float yv[3] = {0.f, 0.f, 0.f};
+    for (int k = 0; k < ndim; ++k) yv[k] = src[((long long)A * ndim + k) * n + i];
+    if (x == nx - 1) yv[0] = 0.f;
+    if (y == ny - 1) yv[1] = 0.f;
+    if (ndim == 3 && z == nz - 1) yv[2] = 0.f;
+    const float s = s_node[A] * (S ? S[i] : 1.0f);
+    if (aniso) {
+        for (int k = 0; k < ndim; ++k) yv[k] = fminf(fmaxf(yv[k], -s), s);
+    } else {
+        // a flow that is feasible up to FP32 rounding (e.g. read back from a
+        // solver) is kept bit for bit; anything outside is scaled onto the ball
+        float r2 = 0.f;
+        for (int k = 0; k < ndim; ++k) r2 = fmaf(yv[k], yv[k], r2);
+        if (r2 > s * s * 1.000001f) {
+            const float f = s * rsqrtf(r2);
+            for (int k = 0; k < ndim; ++k) yv[k] *= f;
+        }
+    }
+    for (int k = 0; k < ndim; ++k) stv<T>(dst + ((long long)A * ndim + k) * n + i, yv[k]);
+}
+
+__global__ void validate_kernel(const float* D, long long nD, const float* S, long long nS, unsigned* flags) {
+    bool bad = false;
+    for (long long i = (long long)blockIdx.x * NT + threadIdx.x; i < nD; i += (long long)gridDim.x * NT)
+        bad = bad || !isfinite(D[i]);
+    if (S)
+        for (long long i = (long long)blockIdx.x * NT + threadIdx.x; i < nS; i += (long long)gridDim.x * NT)
+            bad = bad || !(S[i] >= 0.f) || !isfinite(S[i]);
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flags, FLAG_BAD_INPUT);
+}
+
+// Sums the per-block (E, P) partials in a fixed order (deterministic).
+__global__ void energy_final_kernel(const double* partial, int blocks, double* out, unsigned* flags) {
+    __shared__ double sE[1024], sP[1024];
+    double E = 0.0, P = 0.0;
+    for (int b = threadIdx.x; b < blocks; b += blockDim.x) {
+        E += partial[2 * b];
+        P += partial[2 * b + 1];
+    }
+    sE[threadIdx.x] = E;
+    sP[threadIdx.x] = P;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) {
+            sE[threadIdx.x] += sE[threadIdx.x + w];
+            sP[threadIdx.x] += sP[threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out[0] = sE[0];
+        out[1] = sP[0];
+        if (!isfinite(sE[0]) || !isfinite(sP[0])) atomicOr(flags, FLAG_NONFINITE);
+    }
+}
+
+}  // namespace
+
+#define PFM_BY_STORAGE(storage, CALL_F32, CALL_BF16) \
+    do {                                             \
+        if ((storage) == 0) {                        \
+            CALL_F32;                                \
+        } else {                                     \
+            CALL_BF16;                               \
+        }                                            \
+    } while (0)
+
+cudaError_t launch_init_labels(void* u, int storage, int nl, long long n, cudaStream_t s) {
+    const unsigned b = blocks_for((long long)nl * n);
+    PFM_BY_STORAGE(storage, (init_labels_kernel<float><<<b, NT, 0, s>>>((float*)u, nl, n)),
+                   (init_labels_kernel<__nv_bfloat16><<<b, NT, 0, s>>>((__nv_bfloat16*)u, nl, n)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_argmax(const void* u, int storage, int nl, long long n, int* out, cudaStream_t s) {
+    const unsigned b = blocks_for(n);
+    PFM_BY_STORAGE(storage, (argmax_kernel<float><<<b, NT, 0, s>>>((const float*)u, nl, n, out)),
+                   (argmax_kernel<__nv_bfloat16><<<b, NT, 0, s>>>((const __nv_bfloat16*)u, nl, n, out)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_to_f32(const void* src, int storage, long long count, float* dst, cudaStream_t s) {
+    const unsigned b = blocks_for(count);
+    PFM_BY_STORAGE(storage, (to_f32_kernel<float><<<b, NT, 0, s>>>((const float*)src, count, dst)),
+                   (to_f32_kernel<__nv_bfloat16><<<b, NT, 0, s>>>((const __nv_bfloat16*)src, count, dst)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_labels(const float* src, int storage, int nl, long long n, void* dst, unsigned* flags,
+                              cudaStream_t s) {
+    const unsigned b = blocks_for(n);
+    PFM_BY_STORAGE(storage, (set_labels_kernel<float><<<b, NT, 0, s>>>(src, nl, n, (float*)dst, flags)),
+                   (set_labels_kernel<__nv_bfloat16><<<b, NT, 0, s>>>(src, nl, n, (__nv_bfloat16*)dst, flags)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_flows(const float* src, int storage, int nn, int ndim, int nx, int ny, int nz,
+                             const float* s_node_dev, const float* S, int aniso, void* dst, cudaStream_t s) {
+    const unsigned b = blocks_for((long long)nn * nx * ny * nz);
+    PFM_BY_STORAGE(storage,
+                   (set_flows_kernel<float><<<b, NT, 0, s>>>(src, nn, ndim, nx, ny, nz, s_node_dev, S, aniso,
+                                                             (float*)dst)),
+                   (set_flows_kernel<__nv_bfloat16><<<b, NT, 0, s>>>(src, nn, ndim, nx, ny, nz, s_node_dev, S,
+                                                                     aniso, (__nv_bfloat16*)dst)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_validate(const float* D, long long nD, const float* S, long long nS, unsigned* flags,
+                            cudaStream_t s) {
+    validate_kernel<<<1216, NT, 0, s>>>(D, nD, S, nS, flags);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_energy_final(const double* partial, int blocks, double* out, unsigned* flags, cudaStream_t s) {
+    energy_final_kernel<<<1, 1024, 0, s>>>(partial, blocks, out, flags);
+    return cudaGetLastError();
+}
+
+}  // namespace pfm

@@ -1,0 +1,14 @@
+// Potts kernel buckets (flat DAG: one node per end-label), storage bf16.
+#include "pfm_solver.cuh"
+
+namespace pfm {
+
+SolverBase* make_potts_bf16(int maxl, int dim, const ProblemView& v) {
+#define PFM_POTTS(L, DM) \
+    if (maxl == L && dim == DM) return new Solver<L, L, DM, false, __nv_bfloat16>(v);
+    PFM_POTTS(4, 2) PFM_POTTS(4, 3) PFM_POTTS(8, 2) PFM_POTTS(8, 3) PFM_POTTS(16, 2) PFM_POTTS(16, 3)
+#undef PFM_POTTS
+    return nullptr;
+}
+
+}  // namespace pfm

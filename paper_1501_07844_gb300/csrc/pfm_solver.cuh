@@ -1,0 +1,122 @@
+// pfm_solver.cuh -- host-side launch logic per kernel bucket.
+//
+// A bucket fixes at compile time the register-array sizes (MAXL end-labels,
+// MAXN nodes), the spatial dimension and the storage type; the actual
+// counts are runtime values <= the bucket maxima.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "pfm_device.cuh"
+
+namespace pfm {
+
+// What a solver bucket needs from the problem (filled by the C-ABI layer).
+struct ProblemView {
+    int ndim, nx, ny, nz, nl, nn;
+    long long n;
+    float c, tau;
+    int literal, aniso;
+    const float* D;
+    const float* S;
+    float* abuf;
+    unsigned* flags;
+    const float* s_node;   // host [nn]
+    const float* W;        // host [nn][nl] path weights (DAG) or nullptr
+};
+
+struct SolverBase {
+    virtual ~SolverBase() {}
+    // One iteration reading (u_in, q_in) and writing (u_out, q_out); for the
+    // in-place schedule u_in == u_out and q_in == q_out.  Returns the number
+    // of kernels launched through *launches.
+    virtual cudaError_t step(const void* u_in, void* u_out, const void* q_in, void* q_out, bool fused,
+                             int zc, cudaStream_t s, int* launches) = 0;
+    // Per-block (E, P) partials of the energy of (u, q) into partial[2*blocks].
+    virtual cudaError_t energy(const void* u, const void* q, double* partial, int blocks, cudaStream_t s) = 0;
+};
+
+template <int MAXL, int MAXN, int DIM, bool IS_DAG, typename T>
+struct Solver final : SolverBase {
+    StepArgs<MAXL, MAXN> base{};
+    size_t fused_smem = 0;
+
+    explicit Solver(const ProblemView& v) {
+        base.D = v.D;
+        base.S = v.S;
+        base.abuf = v.abuf;
+        base.flags = v.flags;
+        base.nx = v.nx;
+        base.ny = v.ny;
+        base.nz = v.nz;
+        base.nl = v.nl;
+        base.nn = v.nn;
+        base.n = v.n;
+        base.literal = v.literal;
+        base.aniso = v.aniso;
+        base.inv_c = 1.0f / v.c;
+        base.ctau = v.c * v.tau;
+        for (int A = 0; A < MAXN; ++A) base.s_node[A] = A < v.nn ? v.s_node[A] : 0.f;
+        for (int A = 0; A < MAXN; ++A)
+            for (int j = 0; j < MAXL; ++j)
+                base.W[A][j] = (IS_DAG && A < v.nn && j < v.nl) ? v.W[A * v.nl + j] : 0.f;
+        fused_smem = sizeof(float) * 3 * MAXL * FNE;
+    }
+
+    cudaError_t step(const void* u_in, void* u_out, const void* q_in, void* q_out, bool fused, int zc,
+                     cudaStream_t s, int* launches) override {
+        StepArgs<MAXL, MAXN> a = base;
+        a.u_in = u_in;
+        a.u_out = u_out;
+        a.q_in = q_in;
+        a.q_out = q_out;
+        if (fused) {
+            if (fused_smem > 48 * 1024) {
+                cudaError_t e = cudaFuncSetAttribute(fused_step_kernel<MAXL, MAXN, DIM, IS_DAG, T>,
+                                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                     (int)fused_smem);
+                if (e != cudaSuccess) return e;
+            }
+            a.zc = zc < 1 ? 1 : zc;
+            dim3 grid((a.nx + FTX - 1) / FTX, (a.ny + FTY - 1) / FTY, (a.nz + a.zc - 1) / a.zc);
+            fused_step_kernel<MAXL, MAXN, DIM, IS_DAG, T><<<grid, FUSED_NT, fused_smem, s>>>(a);
+            *launches = 1;
+        } else {
+            const unsigned blocks = (unsigned)((a.n + POINT_NT - 1) / POINT_NT);
+            prox_inplace_kernel<MAXL, MAXN, DIM, IS_DAG, T><<<blocks, POINT_NT, 0, s>>>(a);
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
+            flow_inplace_kernel<MAXL, MAXN, DIM, IS_DAG, T><<<blocks, POINT_NT, 0, s>>>(a);
+            *launches = 2;
+        }
+        return cudaGetLastError();
+    }
+
+    cudaError_t energy(const void* u, const void* q, double* partial, int blocks, cudaStream_t s) override {
+        StepArgs<MAXL, MAXN> a = base;
+        a.u_in = u;
+        a.q_in = q;
+        energy_partial_kernel<MAXL, MAXN, DIM, IS_DAG, T><<<blocks, ENERGY_NT, 0, s>>>(a, partial);
+        return cudaGetLastError();
+    }
+};
+
+// Factories, one per translation unit (storage x model).
+SolverBase* make_potts_f32(int maxl, int dim, const ProblemView& v);
+SolverBase* make_potts_bf16(int maxl, int dim, const ProblemView& v);
+SolverBase* make_dag_f32(int maxl, int maxn, int dim, const ProblemView& v);
+SolverBase* make_dag_bf16(int maxl, int maxn, int dim, const ProblemView& v);
+
+// Auxiliary kernels (pfm_misc.cu).
+cudaError_t launch_init_labels(void* u, int storage, int nl, long long n, cudaStream_t s);
+cudaError_t launch_argmax(const void* u, int storage, int nl, long long n, int* out, cudaStream_t s);
+cudaError_t launch_to_f32(const void* src, int storage, long long count, float* dst, cudaStream_t s);
+cudaError_t launch_set_labels(const float* src, int storage, int nl, long long n, void* dst, unsigned* flags,
+                              cudaStream_t s);
+cudaError_t launch_set_flows(const float* src, int storage, int nn, int ndim, int nx, int ny, int nz,
+                             const float* s_node_dev, const float* S, int aniso, void* dst, cudaStream_t s);
+cudaError_t launch_validate(const float* D, long long nD, const float* S, long long nS, unsigned* flags,
+                            cudaStream_t s);
+cudaError_t launch_energy_final(const double* partial, int blocks, double* out, unsigned* flags, cudaStream_t s);
+
+}  // namespace pfm

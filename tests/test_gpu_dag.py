@@ -1,0 +1,59 @@
+"""GPU parity of the DAG / HMF path (Algorithm 2) against the FP64 oracle."""
+import numpy as np
+import pytest
+
+import synth
+from helpers import compare, gpu_problem
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("sched", [0, 1], ids=["fused", "inplace"])
+@pytest.mark.parametrize("mode", [0, 1], ids=["normalised", "literal"])
+def test_hmf_tree_small(sched, mode):
+    """Depth-3 tree: S -> 3 inner -> 4 leaves each (12 end-labels, 15 nodes),
+    per-node capacities in [0.05, 0.5], leaf D = |I - c_L|."""
+    prob = synth.hmf_problem(seed=3001, shape=(18, 22, 40), iters=60)
+    with gpu_problem(prob, schedule=sched, grad_source=mode) as gp:
+        compare(prob, gp, 60, grad_source=mode)
+
+
+@pytest.mark.parametrize("seed", [4001, 4002, 4003])
+def test_random_dag_volumes(seed):
+    """10 end-labels with up to two parents each, 4 inner nodes, S = 0.15."""
+    prob = synth.dagmf_problem(seed, (21, 26, 34), iters=50)
+    for sched in (0, 1):
+        with gpu_problem(prob, schedule=sched) as gp:
+            compare(prob, gp, 50)
+
+
+@pytest.mark.parametrize("spatial", [(33, 47), (9, 10, 11), (1, 1, 30)])
+def test_small_dag_bucket(spatial):
+    """A DAG that fits the smaller kernel bucket (<= 8 end-labels, <= 12 nodes)."""
+    rng = np.random.default_rng(77)
+    nn, edges = synth.random_dag(rng, 3, 5, 2)
+    prob = synth.random_problem(78, spatial, nl=5, s_kind="both", n_nodes=nn, edges=edges)
+    for sched in (0, 1):
+        with gpu_problem(prob, schedule=sched, norm=sched) as gp:
+            compare(prob, gp, 40, norm=sched)
+
+
+def test_chain_dag_with_inner_single_child():
+    edges = [(-1, 0, 1.0), (0, 1, 1.0), (-1, 2, 1.0), (-1, 3, 1.0)]
+    prob = synth.random_problem(79, (12, 14, 16), nl=3, s_kind="node", n_nodes=4, edges=edges)
+    with gpu_problem(prob) as gp:
+        compare(prob, gp, 40)
+
+
+def test_dag_zero_capacity_closed_form():
+    rng = np.random.default_rng(80)
+    nn, edges = synth.random_dag(rng, 4, 10, 2)
+    prob = synth.random_problem(81, (10, 12, 14), nl=10, s_kind="field", n_nodes=nn, edges=edges)
+    prob.S_field[:] = 0.0
+    k = 9
+    z = -k * prob.D.astype(np.float64) / prob.c
+    z -= z.max(0)
+    ref = np.exp(z) / np.exp(z).sum(0)
+    with gpu_problem(prob) as gp:
+        gp.iterate(k)
+        assert np.abs(gp.labels().cpu().numpy() - ref).max() <= 2e-5

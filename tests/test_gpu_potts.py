@@ -1,0 +1,178 @@
+"""GPU parity of the Potts path (Algorithm 1) against the FP64 oracle,
+through the C ABI, on seeded phantoms: element by element on small and
+ragged grids, every schedule and gradient mode, plus closed forms,
+invariants, error handling and checkpoint/resume."""
+import numpy as np
+import pytest
+
+import synth
+from helpers import compare, gpu_problem, oracle_run
+
+pytestmark = pytest.mark.gpu
+
+SCHEDULES = [("fused", 0), ("inplace", 1)]
+
+
+@pytest.mark.parametrize("sched", SCHEDULES, ids=lambda s: s[0])
+@pytest.mark.parametrize("mode", [0, 1], ids=["normalised", "literal"])
+def test_potts2d_phantom_128(sched, mode):
+    """2-D Potts phantom, 128 x 128, 4 labels, S = 0.1, c = 0.5, tau = 0.11, 200 iterations."""
+    prob = synth.potts2d_problem(seed=1000)
+    with gpu_problem(prob, schedule=sched[1], grad_source=mode) as gp:
+        compare(prob, gp, 200, grad_source=mode)
+
+
+@pytest.mark.parametrize("sched", SCHEDULES, ids=lambda s: s[0])
+def test_potts3d_ragged_tiles(sched):
+    """3-D, 8 labels, edge-weighted S, sizes that leave ragged x/y tiles and
+    several z-chunks."""
+    prob = synth.potts3d_problem(seed=2001, nl=8, shape=(37, 21, 45), iters=60)
+    with gpu_problem(prob, schedule=sched[1]) as gp:
+        compare(prob, gp, 60)
+
+
+@pytest.mark.parametrize("nl", [2, 3, 5, 12, 16])
+@pytest.mark.parametrize("spatial", [(19, 23, 35), (70, 33)], ids=["3d", "2d"])
+def test_label_counts(nl, spatial):
+    prob = synth.random_problem(10 + nl, spatial, nl=nl, s_kind="both", s_scale=0.4)
+    with gpu_problem(prob, schedule=0) as gp:
+        compare(prob, gp, 40)
+
+
+@pytest.mark.parametrize("sched", SCHEDULES, ids=lambda s: s[0])
+def test_anisotropic(sched):
+    prob = synth.random_problem(21, (17, 20, 33), nl=4, s_kind="field", s_scale=0.5)
+    with gpu_problem(prob, schedule=sched[1], norm=1) as gp:
+        compare(prob, gp, 50, norm=1)
+
+
+@pytest.mark.parametrize("spatial", [(1, 1, 1), (1, 1, 40), (5, 1, 1), (1, 37), (29, 1), (2, 2), (3, 65, 2)])
+def test_degenerate_shapes(spatial):
+    prob = synth.random_problem(31, spatial, nl=3, s_kind="field", s_scale=0.5)
+    for sched in (0, 1):
+        with gpu_problem(prob, schedule=sched) as gp:
+            compare(prob, gp, 25)
+
+
+def test_zero_capacity_closed_form():
+    """S = 0 pins q = 0 and u_L = softmax(-k D_L / c) after k iterations."""
+    prob = synth.random_problem(41, (9, 30, 40), nl=6)
+    prob.S_field[:] = 0.0
+    k = 13
+    z = -k * prob.D.astype(np.float64) / prob.c
+    z -= z.max(0)
+    ref = np.exp(z) / np.exp(z).sum(0)
+    for sched in (0, 1):
+        with gpu_problem(prob, schedule=sched) as gp:
+            gp.iterate(k)
+            u = gp.labels().cpu().numpy()
+            assert np.abs(u - ref).max() <= 2e-5
+            assert np.all(gp.flows().cpu().numpy() == 0.0)
+
+
+def test_invariants_after_each_iteration():
+    prob = synth.potts3d_problem(seed=2002, nl=8, shape=(24, 40, 36))
+    cap = prob.S_field[None, None].astype(np.float64)
+    for sched in (0, 1):
+        with gpu_problem(prob, schedule=sched) as gp:
+            for _ in range(6):
+                gp.iterate(5)
+                u = gp.labels().cpu().numpy().astype(np.float64)
+                q = gp.flows().cpu().numpy().astype(np.float64)
+                assert u.min() >= 0 and np.abs(u.sum(0) - 1).max() <= 1e-5
+                assert np.all(np.sqrt((q ** 2).sum(1)) <= cap * (1 + 1e-5) + 1e-12)
+                assert np.all(q[:, 0, :, :, -1] == 0) and np.all(q[:, 1, :, -1, :] == 0) and np.all(q[:, 2, -1] == 0)
+                E, P = gp.energy()
+                assert E - P >= -1e-6 * abs(E)
+
+
+def test_energy_reduction_on_oracle_state():
+    """pfm_energy of a state imported from the oracle equals the oracle's
+    energy of that state (only the FP32 per-voxel terms differ)."""
+    prob = synth.potts3d_problem(seed=2003, nl=8, shape=(30, 31, 50))
+    u, q, E_o, P_o = oracle_run(prob, 30)
+    with gpu_problem(prob) as gp:
+        gp.set_labels(u.astype(np.float32))
+        gp.set_flows(q.astype(np.float32))
+        E, P = gp.energy()
+    assert abs(E - E_o) <= 2e-6 * abs(E_o) and abs(P - P_o) <= 2e-6 * abs(P_o) + 1e-6
+
+
+@pytest.mark.parametrize("sched", SCHEDULES, ids=lambda s: s[0])
+def test_resume_is_bit_exact(sched):
+    prob = synth.potts3d_problem(seed=2004, nl=8, shape=(20, 26, 40))
+    with gpu_problem(prob, schedule=sched[1]) as a:
+        a.iterate(20)
+        ref_u, ref_q = a.labels().cpu().numpy(), a.flows().cpu().numpy()
+    with gpu_problem(prob, schedule=sched[1]) as b:
+        b.iterate(9)
+        u_mid, q_mid = b.labels().cpu().numpy(), b.flows().cpu().numpy()
+    with gpu_problem(prob, schedule=sched[1]) as c:
+        c.set_labels(u_mid)
+        c.set_flows(q_mid)
+        c.iterate(11)
+        assert np.array_equal(c.labels().cpu().numpy(), ref_u)
+        assert np.array_equal(c.flows().cpu().numpy(), ref_q)
+
+
+def test_argmax_ties_go_to_lowest_label():
+    prob = synth.random_problem(51, (4, 8), nl=4, s_kind="field")
+    prob.D[:] = 0.5
+    with gpu_problem(prob) as gp:
+        gp.iterate(3)
+        assert np.all(gp.argmax().cpu().numpy() == 0)
+
+
+def test_errors_are_reported_not_trapped():
+    import paper_1501_07844_gb300 as pfm
+    prob = synth.random_problem(61, (6, 7), nl=3, s_kind="field")
+    bad = prob.D.copy()
+    bad[1, 2, 3] = np.nan
+    with pytest.raises(pfm.PfmError) as ei:
+        pfm.Problem(bad, S_field=prob.S_field)
+    assert ei.value.name == "PFM_ENONFINITE"
+    negS = prob.S_field.copy()
+    negS[0, 0] = -1.0
+    with pytest.raises(pfm.PfmError) as ei:
+        pfm.Problem(prob.D, S_field=negS)
+    assert ei.value.name == "PFM_ENONFINITE"
+    with gpu_problem(prob) as gp:
+        u = np.full((3, 6, 7), 1 / 3, dtype=np.float32)
+        u[0, 1, 1] = -0.1
+        with pytest.raises(pfm.PfmError) as ei:
+            gp.set_labels(u)
+        assert ei.value.name == "PFM_EINVAL"
+        gp.iterate(2)          # the problem stays usable
+        gp.energy()
+        with pytest.raises(pfm.PfmError):
+            gp.iterate(-1)
+
+
+def test_run_to_gap_reaches_target():
+    prob = synth.potts2d_problem(seed=1001, n=64)
+    import paper_1501_07844_gb300 as pfm
+    with gpu_problem(prob, tau=0.25, c=1.0, gap_tol=1e-4, check_every=20) as gp:
+        it, gap, ok = gp.run_to_gap(5000)
+        assert ok and gap <= 1e-4 and it % 20 == 0 and gp.iterations == it
+    with gpu_problem(prob, gap_tol=1e-12) as gp:
+        it, gap, ok = gp.run_to_gap(30)
+        assert not ok and it == 30
+    assert pfm.lib().pfm_version() == 1
+
+
+def test_host_pointer_inputs_and_outputs():
+    """pfm_create and the getters accept pinned host memory (cudaMemcpyDefault)."""
+    import torch
+    import paper_1501_07844_gb300 as pfm
+    prob = synth.random_problem(71, (8, 9, 10), nl=4, s_kind="field")
+    D = torch.from_numpy(prob.D).pin_memory()
+    S = torch.from_numpy(prob.S_field).pin_memory()
+    with pfm.Problem(D, S_field=S) as gp, gpu_problem(prob) as ref:
+        gp.iterate(7)
+        ref.iterate(7)
+        out = torch.empty((4, 8, 9, 10), dtype=torch.float32).pin_memory()
+        gp.labels(out=out)
+        assert torch.equal(out, ref.labels().cpu())
+        am = torch.empty((8, 9, 10), dtype=torch.int32).pin_memory()
+        gp.argmax(out=am)
+        assert torch.equal(am, ref.argmax().cpu())
