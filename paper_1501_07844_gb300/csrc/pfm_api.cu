@@ -206,11 +206,15 @@ pfm_status flags_status(unsigned f) {
 }
 
 void free_all(pfm_problem* pb) {
-    void* ptrs[] = {pb->u[0], pb->u[1], pb->q[0], pb->q[1], pb->D, pb->S, pb->abuf, pb->snode_dev,
+    // the in-place schedule aliases u[1] = u[0] and q[1] = q[0]
+    void* ptrs[] = {pb->u[0], pb->u[1] != pb->u[0] ? pb->u[1] : nullptr, pb->q[0],
+                    pb->q[1] != pb->q[0] ? pb->q[1] : nullptr, pb->D, pb->S, pb->abuf, pb->snode_dev,
                     pb->flags, pb->partial, pb->result};
     for (void* p : ptrs)
         if (p) cudaFree(p);
+    cudaGetLastError();  // leave no stale error for the next call of this thread
     delete pb->solver;
+    pb->solver = nullptr;
 }
 
 }  // namespace
