@@ -196,6 +196,32 @@ PFM_API pfm_status pfm_shape(const pfm_problem* pb, int* ndim, int64_t dims[3], 
 PFM_API int64_t pfm_iterations_done(const pfm_problem* pb);
 PFM_API int64_t pfm_launch_count(const pfm_problem* pb);
 
+/* Allocation-free energy evaluation.  The paper has no counterpart: this is
+ * a service for callers that cannot call cudaMalloc -- code whose device
+ * memory belongs to an outer allocator that has already claimed the budget
+ * (a framework's caching allocator, a plugin host), or latency-critical
+ * loops where an allocation, which can synchronise the device, is not
+ * acceptable.  It computes what pfm_energy computes for a Potts problem
+ * (flat label set), but on caller-held FP32 device buffers and without
+ * allocating or freeing anything:
+ *   u  [n_labels][z][y][x], q [n_labels][ndim][z][y][x], D [n_labels][z][y][x],
+ *   S_field [z][y][x] or NULL (device); s_label [n_labels] or NULL (host);
+ *   out: device double[2] receiving (E, P); norm: PFM_NORM_*.
+ * The per-block partial sums live in a fixed 1 MiB device array compiled
+ * into the library (held on every GPU that loads it until the process
+ * exits), so the grid may have at most PFM_NOALLOC_MAX_VOXELS voxels;
+ * larger grids are rejected with PFM_EINVAL.  Nothing in the array needs to
+ * start at zero: each call overwrites the partials it reads.  Every call on
+ * a device shares that array, so calls that overlap on the GPU (different
+ * streams, or threads) race and give wrong results; serialise them.  The
+ * first call on each device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.
+ * Asynchronous on `stream` (a cudaStream_t, NULL = legacy default). */
+#define PFM_NOALLOC_MAX_VOXELS 16777216LL
+PFM_API pfm_status pfm_potts_energy_noalloc(int ndim, const int64_t dims[3], int n_labels, const float* u,
+                                            const float* q, const float* D, const float* S_field,
+                                            const float* s_label, int norm, double* out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

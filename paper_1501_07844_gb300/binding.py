@@ -65,6 +65,8 @@ _SIGS = {
                             C.POINTER(C.c_int)]),
     "pfm_iterations_done": (C.c_int64, [_P]),
     "pfm_launch_count": (C.c_int64, [_P]),
+    "pfm_potts_energy_noalloc": (C.c_int, [C.c_int, C.POINTER(C.c_int64), C.c_int, _P, _P, _P, _P,
+                                           C.POINTER(C.c_float), C.c_int, _P, _P]),
 }
 
 _lib = None

@@ -164,6 +164,15 @@ size_t elem_size(int storage) { return storage == PFM_STORAGE_F32 ? 4 : 2; }
 
 }  // namespace
 
+namespace pfm {
+// Sets the thread-local message returned by pfm_last_error (for entry points
+// defined in other translation units).
+pfm_status set_error(pfm_status st, const char* msg) {
+    g_err = msg;
+    return st;
+}
+}  // namespace pfm
+
 struct pfm_problem {
     int ndim = 0, nx = 0, ny = 0, nz = 0, nl = 0, nn = 0;
     long long n = 0;
