@@ -80,9 +80,13 @@ enum { PFM_GRAD_NORMALISED = 0, PFM_GRAD_PAPER_LITERAL = 1 };
 enum { PFM_STORAGE_F32 = 0, PFM_STORAGE_BF16 = 1 };
 
 /* PFM_SCHEDULE_FUSED: one kernel per iteration, u and q double-buffered
- * (fewest bytes moved).  PFM_SCHEDULE_INPLACE: two kernels per iteration
- * updating u and q in place (fewest buffers: the paper's memory argument). */
-enum { PFM_SCHEDULE_FUSED = 0, PFM_SCHEDULE_INPLACE = 1 };
+ * (fewest bytes moved); operands are staged by TMA when the problem allows
+ * it (Potts, <= 8 labels, row pitch a multiple of 16 bytes).
+ * PFM_SCHEDULE_INPLACE: two kernels per iteration updating u and q in place
+ * (fewest buffers: the paper's memory argument).
+ * PFM_SCHEDULE_FUSED_PLAIN: the fused schedule without TMA staging (operands
+ * loaded into registers), for comparison. */
+enum { PFM_SCHEDULE_FUSED = 0, PFM_SCHEDULE_INPLACE = 1, PFM_SCHEDULE_FUSED_PLAIN = 2 };
 
 typedef struct {
     double c;          /* entropic weight c > 0 (Eq. potts_bregmanopt) */
@@ -190,6 +194,11 @@ PFM_API pfm_status pfm_set_flows(pfm_problem* pb, const float* src);
 
 /* Problem shape queries. */
 PFM_API pfm_status pfm_shape(const pfm_problem* pb, int* ndim, int64_t dims[3], int* n_leaf, int* n_nodes);
+
+/* Kernel family pfm_iterate launches for this problem: "fused_tma"
+ * (TMA-staged fused iteration), "fused" (register-staged fused iteration)
+ * or "inplace" (two in-place kernels).  Static string; "" for NULL. */
+PFM_API const char* pfm_kernel_variant(const pfm_problem* pb);
 
 /* Iterations run since creation or the last reset, and kernels this problem
  * has launched since creation (for launch accounting). */

@@ -13,6 +13,7 @@ from .binding import (  # noqa: F401
     BF16,
     F32,
     FUSED,
+    FUSED_PLAIN,
     INPLACE,
     ISO,
     NORMALISED,

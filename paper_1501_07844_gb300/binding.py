@@ -17,7 +17,7 @@ from . import build as _build
 ISO, ANISO = 0, 1
 NORMALISED, PAPER_LITERAL = 0, 1
 F32, BF16 = 0, 1
-FUSED, INPLACE = 0, 1
+FUSED, INPLACE, FUSED_PLAIN = 0, 1, 2
 
 _STATUS = {0: "PFM_OK", 1: "PFM_EINVAL", 2: "PFM_EDAG", 3: "PFM_ENOMEM", 4: "PFM_ECUDA", 5: "PFM_ENONFINITE",
            6: "PFM_ETIMEOUT", 7: "PFM_ENOTCONVERGED", 8: "PFM_EUNSUPPORTED"}
@@ -63,6 +63,7 @@ _SIGS = {
     "pfm_set_flows": (C.c_int, [_P, _P]),
     "pfm_shape": (C.c_int, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int64), C.POINTER(C.c_int),
                             C.POINTER(C.c_int)]),
+    "pfm_kernel_variant": (C.c_char_p, [_P]),
     "pfm_iterations_done": (C.c_int64, [_P]),
     "pfm_launch_count": (C.c_int64, [_P]),
     "pfm_potts_energy_noalloc": (C.c_int, [C.c_int, C.POINTER(C.c_int64), C.c_int, _P, _P, _P, _P,
@@ -247,6 +248,10 @@ class Problem:
     @property
     def iterations(self):
         return lib().pfm_iterations_done(self._h)
+
+    @property
+    def variant(self):
+        return lib().pfm_kernel_variant(self._h).decode()
 
     @property
     def launches(self):

@@ -129,7 +129,8 @@ pfm_status check_params(const pfm_params* p) {
     if (p->grad_source != PFM_GRAD_NORMALISED && p->grad_source != PFM_GRAD_PAPER_LITERAL)
         return fail(PFM_EINVAL, "bad grad_source");
     if (p->storage != PFM_STORAGE_F32 && p->storage != PFM_STORAGE_BF16) return fail(PFM_EINVAL, "bad storage");
-    if (p->schedule != PFM_SCHEDULE_FUSED && p->schedule != PFM_SCHEDULE_INPLACE)
+    if (p->schedule != PFM_SCHEDULE_FUSED && p->schedule != PFM_SCHEDULE_INPLACE &&
+        p->schedule != PFM_SCHEDULE_FUSED_PLAIN)
         return fail(PFM_EINVAL, "bad schedule");
     if (p->check_every < 1) return fail(PFM_EINVAL, "check_every must be >= 1");
     return PFM_OK;
@@ -165,6 +166,41 @@ size_t elem_size(int storage) { return storage == PFM_STORAGE_F32 ? 4 : 2; }
 }  // namespace
 
 namespace pfm {
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+bool encode_tiled_map(CUtensorMap* map, const void* base, int elem_bytes, int rank, const unsigned long long* dims,
+                      const unsigned long long* strides, const unsigned* box) {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !p) {
+            cudaGetLastError();
+            return false;
+        }
+        fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    cuuint64_t d[5], s[4];
+    cuuint32_t b[5], e[5];
+    for (int k = 0; k < rank; ++k) {
+        d[k] = dims[k];
+        b[k] = box[k];
+        e[k] = 1;
+    }
+    for (int k = 0; k + 1 < rank; ++k) s[k] = strides[k];
+    const CUtensorMapDataType dt =
+        elem_bytes == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    // zero fill of out-of-bounds elements is the zero boundary flow
+    return fn(map, dt, (cuuint32_t)rank, const_cast<void*>(base), d, s, b, e, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // Sets the thread-local message returned by pfm_last_error (for entry points
 // defined in other translation units).
 pfm_status set_error(pfm_status st, const char* msg) {
@@ -254,7 +290,7 @@ pfm_status pfm_footprint(const pfm_desc* desc, const pfm_params* params, size_t*
     st = check_desc(desc, &dag);
     if (st != PFM_OK) return st;
     const long long n = (long long)desc->dims[0] * desc->dims[1] * desc->dims[2];
-    const int copies = params->schedule == PFM_SCHEDULE_FUSED ? 2 : 1;
+    const int copies = params->schedule == PFM_SCHEDULE_INPLACE ? 1 : 2;
     const size_t ts = elem_size(params->storage);
     int64_t bufs = 0;
     size_t bytes = 0;
@@ -312,7 +348,7 @@ pfm_status pfm_create(const pfm_desc* desc, const pfm_params* params, void* stre
     };
     const size_t ts = elem_size(params->storage);
     const long long n = pb->n;
-    const bool fused = params->schedule == PFM_SCHEDULE_FUSED;
+    const bool fused = params->schedule != PFM_SCHEDULE_INPLACE;
     const bool need_abuf = !fused && params->grad_source == PFM_GRAD_PAPER_LITERAL;
     cudaError_t e;
     for (int k = 0; k < (fused ? 2 : 1); ++k) {
@@ -375,6 +411,10 @@ pfm_status pfm_create(const pfm_desc* desc, const pfm_params* params, void* stre
         pb->solver = bf16 ? pfm::make_dag_bf16(ml, mn, pb->ndim, v) : pfm::make_dag_f32(ml, mn, pb->ndim, v);
     }
     if (!pb->solver) return bail(fail(PFM_EUNSUPPORTED, "no kernel bucket for this problem"));
+    if (params->schedule == PFM_SCHEDULE_FUSED) {
+        pb->solver->prepare_tma(pb->u, pb->q, pb->D, pb->S);
+    }
+    pb->solver->use_tma = params->schedule == PFM_SCHEDULE_FUSED;
     // z-chunk of the fused kernel: aim at >= ~2000 CTAs on large volumes
     {
         const long long tiles = (long long)((pb->nx + pfm::FTX - 1) / pfm::FTX) * ((pb->ny + pfm::FTY - 1) / pfm::FTY);
@@ -423,7 +463,7 @@ pfm_status pfm_reset(pfm_problem* pb) {
 pfm_status pfm_iterate(pfm_problem* pb, int n_iters) {
     if (!pb) return fail(PFM_EINVAL, "NULL problem");
     if (n_iters < 0) return fail(PFM_EINVAL, "n_iters must be >= 0");
-    const bool fused = pb->prm.schedule == PFM_SCHEDULE_FUSED;
+    const bool fused = pb->prm.schedule != PFM_SCHEDULE_INPLACE;
     for (int it = 0; it < n_iters; ++it) {
         const int src = pb->cur, dst = fused ? 1 - pb->cur : pb->cur;
         int nlaunch = 0;
@@ -604,6 +644,11 @@ pfm_status pfm_shape(const pfm_problem* pb, int* ndim, int64_t dims[3], int* n_l
     if (n_leaf) *n_leaf = pb->nl;
     if (n_nodes) *n_nodes = pb->nn;
     return PFM_OK;
+}
+
+const char* pfm_kernel_variant(const pfm_problem* pb) {
+    if (!pb || !pb->solver) return "";
+    return pb->solver->variant(pb->prm.schedule != PFM_SCHEDULE_INPLACE);
 }
 
 int64_t pfm_iterations_done(const pfm_problem* pb) { return pb ? pb->iters : -1; }

@@ -8,8 +8,15 @@
 #include <cuda_runtime.h>
 
 #include "pfm_device.cuh"
+#include "pfm_tma.cuh"
 
 namespace pfm {
+
+// Encodes a tiled TMA descriptor (pfm_api.cu; driver entry point looked up
+// through the runtime).  dims / box are innermost first; strides in bytes
+// for dims 1..rank-1.  Returns false if the driver rejects the map.
+bool encode_tiled_map(CUtensorMap* map, const void* base, int elem_bytes, int rank, const unsigned long long* dims,
+                      const unsigned long long* strides, const unsigned* box);
 
 // What a solver bucket needs from the problem (filled by the C-ABI layer).
 struct ProblemView {
@@ -34,12 +41,22 @@ struct SolverBase {
                              int zc, cudaStream_t s, int* launches) = 0;
     // Per-block (E, P) partials of the energy of (u, q) into partial[2*blocks].
     virtual cudaError_t energy(const void* u, const void* q, double* partial, int blocks, cudaStream_t s) = 0;
+    // Builds TMA descriptors for the double-buffered state; true if the
+    // TMA-pipelined fused kernel can run on this problem.
+    virtual bool prepare_tma(void* const* u, void* const* q, const float* D, const float* S) { return false; }
+    bool use_tma = true;  // cleared to force the register-staged fused kernel
+    // Name of the kernel family step() launches for the given schedule.
+    virtual const char* variant(bool fused) const = 0;
 };
 
 template <int MAXL, int MAXN, int DIM, bool IS_DAG, typename T>
 struct Solver final : SolverBase {
     StepArgs<MAXL, MAXN> base{};
     size_t fused_smem = 0;
+    static constexpr bool kTmaCapable = !IS_DAG && MAXL <= 8;
+    bool tma_ready = false;
+    const void* tma_u[2] = {nullptr, nullptr};
+    TmaMaps tma_maps[2];
 
     explicit Solver(const ProblemView& v) {
         base.D = v.D;
@@ -70,6 +87,20 @@ struct Solver final : SolverBase {
         a.u_out = u_out;
         a.q_in = q_in;
         a.q_out = q_out;
+        if constexpr (kTmaCapable) {
+            if (fused && tma_ready && use_tma) {
+                using Lay = TmaLayout<MAXL, DIM, T>;
+                const int k = (u_in == tma_u[0]) ? 0 : 1;
+                cudaError_t e = cudaFuncSetAttribute(fused_tma_kernel<MAXL, DIM, T>,
+                                                     cudaFuncAttributeMaxDynamicSharedMemorySize, Lay::total_bytes);
+                if (e != cudaSuccess) return e;
+                a.zc = zc < 1 ? 1 : zc;
+                dim3 grid((a.nx + FTX - 1) / FTX, (a.ny + FTY - 1) / FTY, (a.nz + a.zc - 1) / a.zc);
+                fused_tma_kernel<MAXL, DIM, T><<<grid, FUSED_NT, Lay::total_bytes, s>>>(a, tma_maps[k]);
+                *launches = 1;
+                return cudaGetLastError();
+            }
+        }
         if (fused) {
             if (fused_smem > 48 * 1024) {
                 cudaError_t e = cudaFuncSetAttribute(fused_step_kernel<MAXL, MAXN, DIM, IS_DAG, T>,
@@ -90,6 +121,46 @@ struct Solver final : SolverBase {
             *launches = 2;
         }
         return cudaGetLastError();
+    }
+
+    bool prepare_tma(void* const* u, void* const* q, const float* D, const float* S) override {
+        if constexpr (!kTmaCapable) {
+            return false;
+        } else {
+            using Lay = TmaLayout<MAXL, DIM, T>;
+            const int es = (int)sizeof(T);
+            // every row pitch must be a multiple of 16 bytes (FP32 D and S too)
+            if ((base.nx * es) % 16 != 0 || (base.nx * 4) % 16 != 0) return false;
+            const unsigned long long nx = base.nx, ny = base.ny, nz = base.nz, nl = base.nl;
+            const unsigned long long dims_u[4] = {nx, ny, nz, nl};
+            const unsigned long long dims_q[4] = {nx, ny, nz, (unsigned long long)DIM * nl};
+            const unsigned long long st_t[3] = {nx * es, nx * ny * es, nx * ny * nz * es};
+            const unsigned long long st_f[3] = {nx * 4, nx * ny * 4, nx * ny * nz * 4};
+            const unsigned box_u[4] = {(unsigned)TMA_BX, (unsigned)TMA_UY, 1u, (unsigned)nl};
+            const unsigned box_q[4] = {(unsigned)Lay::QBX, (unsigned)TMA_QY, 1u, (unsigned)(DIM * nl)};
+            const unsigned long long dims_s[3] = {nx, ny, nz};
+            const unsigned box_s[3] = {(unsigned)FTX, (unsigned)FTY, 1u};
+            for (int k = 0; k < 2; ++k) {
+                TmaMaps& m = tma_maps[k];
+                if (!encode_tiled_map(&m.u, u[k], es, 4, dims_u, st_t, box_u)) return false;
+                if (!encode_tiled_map(&m.q, q[k], es, 4, dims_q, st_t, box_q)) return false;
+                if (!encode_tiled_map(&m.D, D, 4, 4, dims_u, st_f, box_u)) return false;
+                if (S) {
+                    if (!encode_tiled_map(&m.S, S, 4, 3, dims_s, st_f, box_s)) return false;
+                } else {
+                    m.S = m.D;  // never read: the kernel skips S when the problem has no field
+                }
+                tma_u[k] = u[k];
+            }
+            tma_ready = true;
+            return true;
+        }
+    }
+
+    const char* variant(bool fused) const override {
+        if (!fused) return "inplace";
+        if (kTmaCapable && tma_ready && use_tma) return "fused_tma";
+        return "fused";
     }
 
     cudaError_t energy(const void* u, const void* q, double* partial, int blocks, cudaStream_t s) override {

@@ -1,0 +1,281 @@
+// pfm_tma.cuh -- TMA-pipelined fused iteration for the Potts model (sm_103a).
+//
+// Same arithmetic as fused_step_kernel (label prox of plane p on the
+// halo-extended 33 x 9 tile, then the flow step of plane p-1), but every
+// operand of a plane is brought into shared memory by the Tensor Memory
+// Accelerator (cp.async.bulk.tensor) one plane ahead, through a 3-stage ring
+// guarded by mbarriers:
+//   stage(p-1): flows and S of plane p-1, and the field g of plane p-1
+//   stage(p)  : u, D, flows of plane p (g written over u in place)
+//   stage(p+1): in flight
+// so memory latency overlaps the arithmetic of the current plane and no
+// operand is carried in registers across planes.  Out-of-range box elements
+// (x0-4 < 0, y0-1 < 0, z = -1, beyond the far edges) are zero-filled by the
+// TMA unit, which is exactly the zero boundary flow of the divergence.
+//
+// Every mbarrier wait is bounded by a cycle budget; on expiry the kernel
+// sets FLAG_TIMEOUT, stops issuing, waits (bounded) for its own copies in
+// flight and returns.
+#pragma once
+
+#include <cuda.h>
+
+#include "pfm_device.cuh"
+
+namespace pfm {
+
+constexpr unsigned FLAG_TIMEOUT = 8u;
+
+constexpr int TMA_BX = 40;       // u / D box width in x: x0 .. x0+39
+constexpr int TMA_UY = FEY;      // 9 rows for u and D: y0 .. y0+8
+constexpr int TMA_QY = FEY + 1;  // 10 rows for flows: y0-1 .. y0+8
+constexpr int TMA_STAGES = 3;
+constexpr long long TMA_WAIT_CYCLES = 4000000000ll;  // about 2 s at 2 GHz
+
+template <int MAXL, int DIM, typename T>
+struct TmaLayout {
+    // the flow box starts QOFF elements left of the tile (a TMA box must
+    // start on a 16-byte boundary) and spans x0-QOFF .. x0+FTX+QOFF-1
+    static constexpr int QOFF = 16 / (int)sizeof(T);
+    static constexpr int QBX = FTX + 2 * QOFF;
+    static constexpr int u_elems = MAXL * TMA_UY * TMA_BX;
+    static constexpr int q_elems = DIM * MAXL * TMA_QY * QBX;
+    static constexpr int s_elems = FTY * FTX;
+    static constexpr int align128(int b) { return (b + 127) / 128 * 128; }
+    static constexpr int u_off = 0;
+    static constexpr int d_off = align128(u_off + u_elems * (int)sizeof(T));
+    static constexpr int q_off = align128(d_off + u_elems * 4);
+    static constexpr int s_off = align128(q_off + q_elems * (int)sizeof(T));
+    static constexpr int stage_bytes = align128(s_off + s_elems * 4);
+    static constexpr int bar_off = TMA_STAGES * stage_bytes;
+    static constexpr int total_bytes = bar_off + 64 + 128;  // + slack to align the base to 128 B
+};
+
+struct TmaMaps {
+    CUtensorMap u, q, D, S;  // u / q of the input buffers of this launch
+};
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: false if the budget ran out before the phase completed.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > TMA_WAIT_CYCLES) return false;
+    return true;
+}
+
+__device__ __forceinline__ void tma_load_4d(unsigned dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                            unsigned bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+        "[%6];" ::"r"(dst),
+        "l"(reinterpret_cast<unsigned long long>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_load_3d(unsigned dst, const CUtensorMap* map, int c0, int c1, int c2,
+                                            unsigned bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(dst),
+        "l"(reinterpret_cast<unsigned long long>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
+        : "memory");
+}
+
+template <typename T> __device__ __forceinline__ float lds(const T* p);
+template <> __device__ __forceinline__ float lds<float>(const float* p) { return *p; }
+template <> __device__ __forceinline__ float lds<__nv_bfloat16>(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+template <typename T> __device__ __forceinline__ void sts(T* p, float v);
+template <> __device__ __forceinline__ void sts<float>(float* p, float v) { *p = v; }
+template <> __device__ __forceinline__ void sts<__nv_bfloat16>(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+
+template <int MAXL, int DIM, typename T>
+__global__ void __launch_bounds__(FUSED_NT, 1)
+fused_tma_kernel(const StepArgs<MAXL, MAXL> a, const __grid_constant__ TmaMaps maps) {
+    using Lay = TmaLayout<MAXL, DIM, T>;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ int s_abort;
+    // TMA destinations start on 128-byte boundaries
+    unsigned char* smem = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
+    const int t = threadIdx.x;
+    const int nl = a.nl;
+    const int x0 = blockIdx.x * FTX, y0 = blockIdx.y * FTY;
+    const int z0 = blockIdx.z * a.zc;
+    const int z1 = min(z0 + a.zc, a.nz);
+    const long long n = a.n;
+    const long long plane = (long long)a.nx * a.ny;
+    T* __restrict__ uout = static_cast<T*>(a.u_out);
+    T* __restrict__ qout = static_cast<T*>(a.q_out);
+    const int has_S = a.S != nullptr;
+    const unsigned bytes_u = (unsigned)(nl * TMA_UY * TMA_BX * sizeof(T));
+    const unsigned bytes_d = (unsigned)(nl * TMA_UY * TMA_BX * 4);
+    const unsigned bytes_q = (unsigned)(DIM * nl * TMA_QY * Lay::QBX * sizeof(T));
+    const unsigned bytes_s = has_S ? (unsigned)(FTX * FTY * 4) : 0u;
+    const unsigned bar0 = smem_addr(smem + Lay::bar_off);
+
+    auto stage_ptr = [&](int k) { return smem + k * Lay::stage_bytes; };
+    // producer: bring plane p (full, or flows only) into stage k
+    auto issue = [&](int p, int k, bool flows_only) {
+        const unsigned bar = bar0 + 8 * k;
+        unsigned char* st = stage_ptr(k);
+        mbar_expect_tx(bar, flows_only ? bytes_q : bytes_u + bytes_d + bytes_q + bytes_s);
+        tma_load_4d(smem_addr(st + Lay::q_off), &maps.q, x0 - Lay::QOFF, y0 - 1, p, 0, bar);
+        if (!flows_only) {
+            tma_load_4d(smem_addr(st + Lay::u_off), &maps.u, x0, y0, p, 0, bar);
+            tma_load_4d(smem_addr(st + Lay::d_off), &maps.D, x0, y0, p, 0, bar);
+            if (has_S) tma_load_3d(smem_addr(st + Lay::s_off), &maps.S, x0, y0, p, bar);
+        }
+    };
+
+    if (t == 0) {
+        for (int k = 0; k < TMA_STAGES; ++k) mbar_init(bar0 + 8 * k, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_abort = 0;
+        issue(z0 - 1, 0, true);   // flows of plane z0-1 (zero-filled when z0 = 0)
+        issue(z0, 1, false);
+    }
+    __syncthreads();
+
+    bool bad = false;
+    int inflight_hi = z0;  // highest plane issued
+    for (int p = z0; p <= z1; ++p) {
+        const int s = p - z0 + 1;
+        const int cs = s % 3, ps = (s + 2) % 3, ns = (s + 1) % 3;
+        if (t == 0 && p + 1 <= z1 && p + 1 < a.nz) {
+            issue(p + 1, ns, false);
+            inflight_hi = p + 1;
+        }
+        unsigned char* cst = stage_ptr(cs);
+        unsigned char* pst = stage_ptr(ps);
+        bool ok = true;
+        if (p == z0) ok = mbar_wait_bounded(bar0 + 8 * ps, 0u);
+        if (p < a.nz && ok) ok = mbar_wait_bounded(bar0 + 8 * cs, (unsigned)((s / 3) & 1));
+        if (!ok) {
+            atomicOr(a.flags, FLAG_TIMEOUT);
+            s_abort = 1;
+        }
+        __syncthreads();
+        if (s_abort) break;
+
+        // ---- label prox of plane p on the halo-extended tile
+        if (p < a.nz && t < FNE) {
+            const int ex = t % FEX, ey = t / FEX;
+            const int x = x0 + ex, y = y0 + ey;
+            if (x < a.nx && y < a.ny) {
+                T* uS = reinterpret_cast<T*>(cst + Lay::u_off);
+                const float* dS = reinterpret_cast<const float*>(cst + Lay::d_off);
+                const T* qS = reinterpret_cast<const T*>(cst + Lay::q_off);
+                const T* qP = reinterpret_cast<const T*>(pst + Lay::q_off);
+                const int ui = ey * TMA_BX + ex;               // (ex, ey) in the u/D box
+                const int qi = (ey + 1) * Lay::QBX + (ex + Lay::QOFF);  // (ex, ey) in the flow box
+                const int qstride = TMA_QY * Lay::QBX;
+                float u[MAXL], Dv[MAXL], e[MAXL], g[MAXL];
+#pragma unroll
+                for (int j = 0; j < MAXL; ++j) {
+                    if (j < nl) {
+                        u[j] = lds<T>(uS + j * TMA_UY * TMA_BX + ui);
+                        Dv[j] = dS[j * TMA_UY * TMA_BX + ui];
+                        const T* qx = qS + (0 * nl + j) * qstride;
+                        const T* qy = qS + (1 * nl + j) * qstride;
+                        float dv = (x < a.nx - 1 ? lds<T>(qx + qi) : 0.f) - lds<T>(qx + qi - 1);
+                        dv += (y < a.ny - 1 ? lds<T>(qy + qi) : 0.f) - lds<T>(qy + qi - Lay::QBX);
+                        if constexpr (DIM == 3) {
+                            const T* qz = qS + (2 * nl + j) * qstride;
+                            const T* qzp = qP + (2 * nl + j) * qstride;
+                            dv += (p < a.nz - 1 ? lds<T>(qz + qi) : 0.f) - lds<T>(qzp + qi);
+                        }
+                        e[j] = dv;
+                    } else {
+                        u[j] = Dv[j] = e[j] = 0.f;
+                    }
+                }
+                float nrm;
+                if (!label_prox<MAXL, MAXL, false>(a, e, Dv, u, g, nrm)) bad = true;
+#pragma unroll
+                for (int j = 0; j < MAXL; ++j)
+                    if (j < nl) sts<T>(uS + j * TMA_UY * TMA_BX + ui, g[j]);
+                if (ex < FTX && ey < FTY && p < z1) {
+                    const long long i = (long long)p * plane + (long long)y * a.nx + x;
+#pragma unroll
+                    for (int j = 0; j < MAXL; ++j)
+                        if (j < nl) stv<T>(uout + (long long)j * n + i, u[j]);
+                }
+            }
+        }
+        __syncthreads();
+
+        // ---- flow step of plane p-1
+        const int pm = p - 1;
+        if (pm >= z0 && t < FTX * FTY) {
+            const int mx = t % FTX, my = t / FTX;
+            const int x = x0 + mx, y = y0 + my;
+            if (x < a.nx && y < a.ny) {
+                const T* gP = reinterpret_cast<const T*>(pst + Lay::u_off);
+                const T* gC = reinterpret_cast<const T*>(cst + Lay::u_off);
+                const T* qP = reinterpret_cast<const T*>(pst + Lay::q_off);
+                const float* sP = reinterpret_cast<const float*>(pst + Lay::s_off);
+                const int ui = my * TMA_BX + mx;
+                const int qi = (my + 1) * Lay::QBX + (mx + Lay::QOFF);
+                const int qstride = TMA_QY * Lay::QBX;
+                const float sf = has_S ? sP[my * FTX + mx] : 1.0f;
+                const long long i = (long long)pm * plane + (long long)y * a.nx + x;
+#pragma unroll
+                for (int j = 0; j < MAXL; ++j) {
+                    if (j < nl) {
+                        const T* gj = gP + j * TMA_UY * TMA_BX;
+                        const float g0 = lds<T>(gj + ui);
+                        float yv[DIM];
+                        yv[0] = lds<T>(qP + (0 * nl + j) * qstride + qi) -
+                                a.ctau * (x < a.nx - 1 ? lds<T>(gj + ui + 1) - g0 : 0.f);
+                        yv[1] = lds<T>(qP + (1 * nl + j) * qstride + qi) -
+                                a.ctau * (y < a.ny - 1 ? lds<T>(gj + ui + TMA_BX) - g0 : 0.f);
+                        if constexpr (DIM == 3)
+                            yv[2] = lds<T>(qP + (2 * nl + j) * qstride + qi) -
+                                    a.ctau * (pm < a.nz - 1 ? lds<T>(gC + j * TMA_UY * TMA_BX + ui) - g0 : 0.f);
+                        project<DIM>(yv, a.s_node[j] * sf, a.aniso);
+                        T* qa = qout + (long long)j * DIM * n + i;
+#pragma unroll
+                        for (int k = 0; k < DIM; ++k) stv<T>(qa + k * n, yv[k]);
+                    }
+                }
+            }
+        }
+        // order this plane's shared-memory accesses before the TMA that
+        // refills stage ps at the next step
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+    }
+    if (bad) atomicOr(a.flags, FLAG_NONFINITE);
+    if (s_abort && t == 0) {
+        // bounded drain of this CTA's copies still in flight
+        for (int p = z0 - 1; p <= inflight_hi; ++p) {
+            const int s = p - z0 + 1;
+            mbar_wait_bounded(bar0 + 8 * (s % 3), (unsigned)((s / 3) & 1));
+        }
+    }
+}
+
+}  // namespace pfm

@@ -176,3 +176,41 @@ def test_host_pointer_inputs_and_outputs():
         am = torch.empty((8, 9, 10), dtype=torch.int32).pin_memory()
         gp.argmax(out=am)
         assert torch.equal(am, ref.argmax().cpu())
+
+
+@pytest.mark.parametrize("shape", [(23, 17, 40), (9, 40, 64), (40, 136)], ids=["3d_ragged_yz", "3d_two_tiles", "2d"])
+@pytest.mark.parametrize("nl", [3, 8])
+def test_tma_fused_kernel_parity(shape, nl):
+    """Row pitch a multiple of 16 bytes selects the TMA-staged fused kernel;
+    it must match the oracle and the register-staged fused kernel."""
+    import paper_1501_07844_gb300 as pfm
+    prob = synth.random_problem(90 + nl, shape, nl=nl, s_kind="both", s_scale=0.4)
+    with gpu_problem(prob, schedule=pfm.FUSED) as gp:
+        assert gp.variant == "fused_tma"
+        compare(prob, gp, 45)
+        u_t, q_t = gp.labels().cpu().numpy(), gp.flows().cpu().numpy()
+    with gpu_problem(prob, schedule=pfm.FUSED_PLAIN) as gp:
+        assert gp.variant == "fused"
+        gp.iterate(45)
+        assert np.abs(gp.labels().cpu().numpy() - u_t).max() <= 1e-6
+        assert np.abs(gp.flows().cpu().numpy() - q_t).max() <= 1e-6
+
+
+@pytest.mark.parametrize("mode,norm", [(1, 0), (0, 1)], ids=["literal", "aniso"])
+def test_tma_fused_modes(mode, norm):
+    prob = synth.potts3d_problem(seed=2005, nl=8, shape=(33, 27, 48))
+    with gpu_problem(prob, grad_source=mode, norm=norm) as gp:
+        assert gp.variant == "fused_tma"
+        compare(prob, gp, 40, grad_source=mode, norm=norm)
+
+
+def test_kernel_variant_selection():
+    import paper_1501_07844_gb300 as pfm
+    p8 = synth.random_problem(95, (5, 6, 32), nl=8, s_kind="field")
+    p_odd = synth.random_problem(96, (5, 6, 30), nl=8, s_kind="field")
+    p12 = synth.random_problem(97, (5, 6, 32), nl=12, s_kind="field")
+    with gpu_problem(p8) as a, gpu_problem(p_odd) as b, gpu_problem(p12) as c, \
+            gpu_problem(p8, schedule=pfm.INPLACE) as d, gpu_problem(p8, storage=pfm.BF16) as e, \
+            gpu_problem(p_odd, storage=pfm.BF16) as f:
+        assert (a.variant, b.variant, c.variant, d.variant, e.variant, f.variant) == \
+            ("fused_tma", "fused", "fused", "inplace", "fused_tma", "fused")
