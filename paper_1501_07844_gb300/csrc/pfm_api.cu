@@ -244,6 +244,7 @@ pfm_status read_flags(pfm_problem* pb, unsigned* out) {
 }
 
 pfm_status flags_status(unsigned f) {
+    if (f & pfm::FLAG_TIMEOUT) return fail(PFM_ETIMEOUT, "a bounded device-side wait expired (TMA pipeline)");
     if (f & pfm::FLAG_BAD_INPUT) return fail(PFM_ENONFINITE, "D not finite or S negative / not finite");
     if (f & pfm::FLAG_NONFINITE) return fail(PFM_ENONFINITE, "non-finite normaliser, energy or dual");
     if (f & pfm::FLAG_BAD_LABELS) return fail(PFM_EINVAL, "labelling with a negative entry or zero sum");
