@@ -51,6 +51,8 @@ struct TmaLayout {
     static constexpr int total_bytes = bar_off + 64 + 128;  // + slack to align the base to 128 B
 };
 
+// Staged flow box: coordinate 3 is node * DIM + component, as in the global
+// layout q[node][comp][z][y][x].
 struct TmaMaps {
     CUtensorMap u, q, D, S;  // u / q of the input buffers of this launch
 };
@@ -198,13 +200,13 @@ fused_tma_kernel(const StepArgs<MAXL, MAXL> a, const __grid_constant__ TmaMaps m
                     if (j < nl) {
                         u[j] = lds<T>(uS + j * TMA_UY * TMA_BX + ui);
                         Dv[j] = dS[j * TMA_UY * TMA_BX + ui];
-                        const T* qx = qS + (0 * nl + j) * qstride;
-                        const T* qy = qS + (1 * nl + j) * qstride;
+                        const T* qx = qS + (j * DIM + 0) * qstride;
+                        const T* qy = qS + (j * DIM + 1) * qstride;
                         float dv = (x < a.nx - 1 ? lds<T>(qx + qi) : 0.f) - lds<T>(qx + qi - 1);
                         dv += (y < a.ny - 1 ? lds<T>(qy + qi) : 0.f) - lds<T>(qy + qi - Lay::QBX);
                         if constexpr (DIM == 3) {
-                            const T* qz = qS + (2 * nl + j) * qstride;
-                            const T* qzp = qP + (2 * nl + j) * qstride;
+                            const T* qz = qS + (j * DIM + 2) * qstride;
+                            const T* qzp = qP + (j * DIM + 2) * qstride;
                             dv += (p < a.nz - 1 ? lds<T>(qz + qi) : 0.f) - lds<T>(qzp + qi);
                         }
                         e[j] = dv;
@@ -248,12 +250,12 @@ fused_tma_kernel(const StepArgs<MAXL, MAXL> a, const __grid_constant__ TmaMaps m
                         const T* gj = gP + j * TMA_UY * TMA_BX;
                         const float g0 = lds<T>(gj + ui);
                         float yv[DIM];
-                        yv[0] = lds<T>(qP + (0 * nl + j) * qstride + qi) -
+                        yv[0] = lds<T>(qP + (j * DIM + 0) * qstride + qi) -
                                 a.ctau * (x < a.nx - 1 ? lds<T>(gj + ui + 1) - g0 : 0.f);
-                        yv[1] = lds<T>(qP + (1 * nl + j) * qstride + qi) -
+                        yv[1] = lds<T>(qP + (j * DIM + 1) * qstride + qi) -
                                 a.ctau * (y < a.ny - 1 ? lds<T>(gj + ui + TMA_BX) - g0 : 0.f);
                         if constexpr (DIM == 3)
-                            yv[2] = lds<T>(qP + (2 * nl + j) * qstride + qi) -
+                            yv[2] = lds<T>(qP + (j * DIM + 2) * qstride + qi) -
                                     a.ctau * (pm < a.nz - 1 ? lds<T>(gC + j * TMA_UY * TMA_BX + ui) - g0 : 0.f);
                         project<DIM>(yv, a.s_node[j] * sf, a.aniso);
                         T* qa = qout + (long long)j * DIM * n + i;
