@@ -367,8 +367,6 @@ pfm_status pfm_create(const pfm_desc* desc, const pfm_params* params, void* stre
     pb->energy_blocks = (int)std::min<long long>((n + pfm::ENERGY_NT - 1) / pfm::ENERGY_NT, 152 * 8);
     if ((e = cudaMalloc(&pb->snode_dev, sizeof(float) * pb->nn)) != cudaSuccess) return bail(cuda_fail(e, "alloc"));
     if ((e = cudaMalloc(&pb->flags, sizeof(unsigned))) != cudaSuccess) return bail(cuda_fail(e, "alloc"));
-    if ((e = cudaMalloc(&pb->partial, sizeof(double) * 2 * pb->energy_blocks)) != cudaSuccess)
-        return bail(cuda_fail(e, "alloc"));
     if ((e = cudaMalloc(&pb->result, sizeof(double) * 2)) != cudaSuccess) return bail(cuda_fail(e, "alloc"));
 
     cudaStream_t s = pb->stream;
@@ -412,9 +410,9 @@ pfm_status pfm_create(const pfm_desc* desc, const pfm_params* params, void* stre
         pb->solver = bf16 ? pfm::make_dag_bf16(ml, mn, pb->ndim, v) : pfm::make_dag_f32(ml, mn, pb->ndim, v);
     }
     if (!pb->solver) return bail(fail(PFM_EUNSUPPORTED, "no kernel bucket for this problem"));
-    if (params->schedule == PFM_SCHEDULE_FUSED) {
-        pb->solver->prepare_tma(pb->u, pb->q, pb->D, pb->S);
-    }
+    // TMA descriptors serve the fused iteration (PFM_SCHEDULE_FUSED only) and
+    // the energy reduction (every schedule)
+    pb->solver->prepare_tma(pb->u, pb->q, pb->D, pb->S);
     pb->solver->use_tma = params->schedule == PFM_SCHEDULE_FUSED;
     // z-chunk of the fused kernel: aim at >= ~2000 CTAs on large volumes
     {
@@ -422,6 +420,9 @@ pfm_status pfm_create(const pfm_desc* desc, const pfm_params* params, void* stre
         long long zc = (tiles * pb->nz) / 2048;
         pb->zc = (int)std::max<long long>(4, std::min<long long>(64, zc));
     }
+    pb->energy_blocks = (int)std::max<long long>(pb->energy_blocks, pb->solver->tma_energy_blocks(pb->zc));
+    if ((e = cudaMalloc(&pb->partial, sizeof(double) * 2 * pb->energy_blocks)) != cudaSuccess)
+        return bail(cuda_fail(e, "alloc"));
     st = pfm_reset(pb);
     if (st != PFM_OK) return bail(st);
     unsigned f = 0;
@@ -480,9 +481,11 @@ pfm_status pfm_iterate(pfm_problem* pb, int n_iters) {
 
 pfm_status pfm_energy(pfm_problem* pb, double* primal, double* dual) {
     if (!pb) return fail(PFM_EINVAL, "NULL problem");
-    PFM_CUDA(pb->solver->energy(pb->u[pb->cur], pb->q[pb->cur], pb->partial, pb->energy_blocks, pb->stream),
+    int nblocks = 0;
+    PFM_CUDA(pb->solver->energy(pb->u[pb->cur], pb->q[pb->cur], pb->partial, pb->energy_blocks, pb->zc, pb->stream,
+                                &nblocks),
              "energy");
-    PFM_CUDA(pfm::launch_energy_final(pb->partial, pb->energy_blocks, pb->result, pb->flags, pb->stream), "energy");
+    PFM_CUDA(pfm::launch_energy_final(pb->partial, nblocks, pb->result, pb->flags, pb->stream), "energy");
     pb->launches += 2;
     double h[2];
     PFM_CUDA(cudaMemcpyAsync(h, pb->result, sizeof h, cudaMemcpyDeviceToHost, pb->stream), "read energy");

@@ -7,6 +7,8 @@
 
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "pfm_device.cuh"
 #include "pfm_tma.cuh"
 
@@ -39,8 +41,12 @@ struct SolverBase {
     // of kernels launched through *launches.
     virtual cudaError_t step(const void* u_in, void* u_out, const void* q_in, void* q_out, bool fused,
                              int zc, cudaStream_t s, int* launches) = 0;
-    // Per-block (E, P) partials of the energy of (u, q) into partial[2*blocks].
-    virtual cudaError_t energy(const void* u, const void* q, double* partial, int blocks, cudaStream_t s) = 0;
+    // Per-block (E, P) partials of the energy of (u, q) into partial[2*k];
+    // *nblocks receives k (<= max_blocks).
+    virtual cudaError_t energy(const void* u, const void* q, double* partial, int max_blocks, int zc, cudaStream_t s,
+                               int* nblocks) = 0;
+    // Number of partials the TMA energy kernel writes for chunk length zc (0 if it is not used).
+    virtual long long tma_energy_blocks(int zc) const { return 0; }
     // Builds TMA descriptors for the double-buffered state; true if the
     // TMA-pipelined fused kernel can run on this problem.
     virtual bool prepare_tma(void* const* u, void* const* q, const float* D, const float* S) { return false; }
@@ -163,11 +169,35 @@ struct Solver final : SolverBase {
         return "fused";
     }
 
-    cudaError_t energy(const void* u, const void* q, double* partial, int blocks, cudaStream_t s) override {
+    long long tma_energy_blocks(int zc) const override {
+        if (!(kTmaCapable && tma_ready)) return 0;
+        zc = zc < 1 ? 1 : zc;
+        return (long long)((base.nx + FTX - 1) / FTX) * ((base.ny + FTY - 1) / FTY) * ((base.nz + zc - 1) / zc);
+    }
+
+    cudaError_t energy(const void* u, const void* q, double* partial, int max_blocks, int zc, cudaStream_t s,
+                       int* nblocks) override {
         StepArgs<MAXL, MAXN> a = base;
         a.u_in = u;
         a.q_in = q;
+        if constexpr (kTmaCapable) {
+            const long long nb = tma_energy_blocks(zc);
+            if (nb > 0 && nb <= max_blocks) {
+                using Lay = TmaLayout<MAXL, DIM, T>;
+                const int k = (u == tma_u[0]) ? 0 : 1;
+                cudaError_t e = cudaFuncSetAttribute(energy_tma_kernel<MAXL, DIM, T>,
+                                                     cudaFuncAttributeMaxDynamicSharedMemorySize, Lay::total_bytes);
+                if (e != cudaSuccess) return e;
+                a.zc = zc < 1 ? 1 : zc;
+                dim3 grid((a.nx + FTX - 1) / FTX, (a.ny + FTY - 1) / FTY, (a.nz + a.zc - 1) / a.zc);
+                energy_tma_kernel<MAXL, DIM, T><<<grid, ENERGY_TMA_NT, Lay::total_bytes, s>>>(a, tma_maps[k], partial);
+                *nblocks = (int)nb;
+                return cudaGetLastError();
+            }
+        }
+        const int blocks = (int)std::min<long long>((a.n + ENERGY_NT - 1) / ENERGY_NT, (long long)max_blocks);
         energy_partial_kernel<MAXL, MAXN, DIM, IS_DAG, T><<<blocks, ENERGY_NT, 0, s>>>(a, partial);
+        *nblocks = blocks;
         return cudaGetLastError();
     }
 };

@@ -280,4 +280,170 @@ fused_tma_kernel(const StepArgs<MAXL, MAXL> a, const __grid_constant__ TmaMaps m
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// TMA-staged energy / dual of a Potts state (same boxes and maps as the
+// iteration).  Each CTA owns a 32 x 8 tile of a z-chunk; plane r needs u of
+// plane r+1 (z-gradient), so planes r+1 and r+2 are in flight while r is
+// summed; the own voxel's z-flow of plane r-1 (divergence) is carried in
+// registers.  One (E, P) partial per CTA, FP64 accumulation.
+// ---------------------------------------------------------------------------
+constexpr int ENERGY_TMA_NT = FTX * FTY;
+
+template <int MAXL, int DIM, typename T>
+__global__ void __launch_bounds__(ENERGY_TMA_NT, 1)
+energy_tma_kernel(const StepArgs<MAXL, MAXL> a, const __grid_constant__ TmaMaps maps, double* partial) {
+    using Lay = TmaLayout<MAXL, DIM, T>;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ int s_abort;
+    __shared__ double sE[ENERGY_TMA_NT / 32], sP[ENERGY_TMA_NT / 32];
+    unsigned char* smem = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
+    const int t = threadIdx.x;
+    const int nl = a.nl;
+    const int x0 = blockIdx.x * FTX, y0 = blockIdx.y * FTY;
+    const int z0 = blockIdx.z * a.zc;
+    const int z1 = min(z0 + a.zc, a.nz);
+    const long long n = a.n;
+    const long long plane = (long long)a.nx * a.ny;
+    const int has_S = a.S != nullptr;
+    const unsigned bytes = (unsigned)(nl * TMA_UY * TMA_BX * sizeof(T)) + (unsigned)(nl * TMA_UY * TMA_BX * 4) +
+                           (unsigned)(DIM * nl * TMA_QY * Lay::QBX * sizeof(T)) +
+                           (has_S ? (unsigned)(FTX * FTY * 4) : 0u);
+    const unsigned bar0 = smem_addr(smem + Lay::bar_off);
+    auto stage_ptr = [&](int k) { return smem + k * Lay::stage_bytes; };
+    auto issue = [&](int p, int k) {
+        const unsigned bar = bar0 + 8 * k;
+        unsigned char* st = stage_ptr(k);
+        mbar_expect_tx(bar, bytes);
+        tma_load_4d(smem_addr(st + Lay::q_off), &maps.q, x0 - Lay::QOFF, y0 - 1, p, 0, bar);
+        tma_load_4d(smem_addr(st + Lay::u_off), &maps.u, x0, y0, p, 0, bar);
+        tma_load_4d(smem_addr(st + Lay::d_off), &maps.D, x0, y0, p, 0, bar);
+        if (has_S) tma_load_3d(smem_addr(st + Lay::s_off), &maps.S, x0, y0, p, bar);
+    };
+    int issued_hi = z0;
+    if (t == 0) {
+        for (int k = 0; k < TMA_STAGES; ++k) mbar_init(bar0 + 8 * k, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_abort = 0;
+        issue(z0, 0);
+        if (z0 + 1 < a.nz) {
+            issue(z0 + 1, 1);
+            issued_hi = z0 + 1;
+        }
+    }
+    __syncthreads();
+    const int mx = t % FTX, my = t / FTX;
+    const int x = x0 + mx, y = y0 + my;
+    const bool own = x < a.nx && y < a.ny;
+    float qzp[MAXL];  // own z-flow of plane r-1
+#pragma unroll
+    for (int j = 0; j < MAXL; ++j) qzp[j] = 0.f;
+    if constexpr (DIM == 3) {
+        if (own && z0 > 0) {
+            const T* qin = static_cast<const T*>(a.q_in);
+            const long long i = (long long)(z0 - 1) * plane + (long long)y * a.nx + x;
+#pragma unroll
+            for (int j = 0; j < MAXL; ++j)
+                if (j < nl) qzp[j] = ldv<T>(qin + ((long long)j * DIM + 2) * n + i);
+        }
+    }
+    double accE = 0.0, accP = 0.0;
+    for (int r = z0; r < z1; ++r) {
+        const int s = r - z0;
+        const int cs = s % 3, n1 = (s + 1) % 3, n2 = (s + 2) % 3;
+        if (t == 0 && r + 2 <= z1 && r + 2 < a.nz) {
+            issue(r + 2, n2);
+            issued_hi = r + 2;
+        }
+        bool ok = mbar_wait_bounded(bar0 + 8 * cs, (unsigned)((s / 3) & 1));
+        if (ok && r + 1 < a.nz) ok = mbar_wait_bounded(bar0 + 8 * n1, (unsigned)(((s + 1) / 3) & 1));
+        if (!ok) {
+            atomicOr(a.flags, FLAG_TIMEOUT);
+            s_abort = 1;
+        }
+        __syncthreads();
+        if (s_abort) break;
+        if (own) {
+            const unsigned char* cst = stage_ptr(cs);
+            const unsigned char* nst = stage_ptr(n1);
+            const T* uS = reinterpret_cast<const T*>(cst + Lay::u_off);
+            const T* uN = reinterpret_cast<const T*>(nst + Lay::u_off);
+            const float* dS = reinterpret_cast<const float*>(cst + Lay::d_off);
+            const T* qS = reinterpret_cast<const T*>(cst + Lay::q_off);
+            const float* sS = reinterpret_cast<const float*>(cst + Lay::s_off);
+            const int ui = my * TMA_BX + mx;
+            const int qi = (my + 1) * Lay::QBX + (mx + Lay::QOFF);
+            const int qstride = TMA_QY * Lay::QBX;
+            const float sf = has_S ? sS[my * FTX + mx] : 1.0f;
+            float eData = 0.f, tv = 0.f, dmin = 3.0e38f;
+#pragma unroll
+            for (int j = 0; j < MAXL; ++j) {
+                if (j < nl) {
+                    const T* uj = uS + j * TMA_UY * TMA_BX;
+                    const float u0 = lds<T>(uj + ui);
+                    const float Dj = dS[j * TMA_UY * TMA_BX + ui];
+                    eData = fmaf(Dj, u0, eData);
+                    float gr[DIM];
+                    gr[0] = x < a.nx - 1 ? lds<T>(uj + ui + 1) - u0 : 0.f;
+                    gr[1] = y < a.ny - 1 ? lds<T>(uj + ui + TMA_BX) - u0 : 0.f;
+                    if constexpr (DIM == 3)
+                        gr[2] = r < a.nz - 1 ? lds<T>(uN + j * TMA_UY * TMA_BX + ui) - u0 : 0.f;
+                    float nv;
+                    if (a.aniso) {
+                        nv = 0.f;
+#pragma unroll
+                        for (int k = 0; k < DIM; ++k) nv += fabsf(gr[k]);
+                    } else {
+                        float r2 = 0.f;
+#pragma unroll
+                        for (int k = 0; k < DIM; ++k) r2 = fmaf(gr[k], gr[k], r2);
+                        nv = sqrtf(r2);
+                    }
+                    tv = fmaf(a.s_node[j] * sf, nv, tv);
+                    const T* qx = qS + (j * DIM + 0) * qstride;
+                    const T* qy = qS + (j * DIM + 1) * qstride;
+                    float dv = (x < a.nx - 1 ? lds<T>(qx + qi) : 0.f) - lds<T>(qx + qi - 1);
+                    dv += (y < a.ny - 1 ? lds<T>(qy + qi) : 0.f) - lds<T>(qy + qi - Lay::QBX);
+                    if constexpr (DIM == 3) {
+                        const float qz = lds<T>(qS + (j * DIM + 2) * qstride + qi);
+                        dv += (r < a.nz - 1 ? qz : 0.f) - qzp[j];
+                        qzp[j] = qz;
+                    }
+                    dmin = fminf(dmin, Dj + dv);
+                }
+            }
+            accE += (double)eData + (double)tv;
+            accP += (double)dmin;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+    }
+    if (s_abort && t == 0) {
+        for (int p = z0; p <= issued_hi; ++p) {
+            const int s = p - z0;
+            mbar_wait_bounded(bar0 + 8 * (s % 3), (unsigned)((s / 3) & 1));
+        }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        accE += __shfl_down_sync(0xffffffffu, accE, off);
+        accP += __shfl_down_sync(0xffffffffu, accP, off);
+    }
+    if ((t & 31) == 0) {
+        sE[t >> 5] = accE;
+        sP[t >> 5] = accP;
+    }
+    __syncthreads();
+    if (t == 0) {
+        double E = 0.0, P = 0.0;
+        for (int k = 0; k < ENERGY_TMA_NT / 32; ++k) {
+            E += sE[k];
+            P += sP[k];
+        }
+        const long long b = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+        partial[2 * b] = E;
+        partial[2 * b + 1] = P;
+    }
+}
+
 }  // namespace pfm
