@@ -88,11 +88,13 @@ __global__ void set_flows_kernel(const float* src, int nn, int ndim, int nx, int
     if (aniso) {
         for (int k = 0; k < ndim; ++k) yv[k] = fminf(fmaxf(yv[k], -s), s);
     } else {
-        // a flow that is feasible up to FP32 rounding (e.g. read back from a
-        // solver) is kept bit for bit; anything outside is scaled onto the ball
+        // a flow that is feasible up to the rounding of the storage type (e.g.
+        // read back from a solver) is kept bit for bit; anything outside is
+        // scaled onto the ball
+        const float slack = sizeof(T) == 4 ? 1.000001f : 1.02f;
         float r2 = 0.f;
         for (int k = 0; k < ndim; ++k) r2 = fmaf(yv[k], yv[k], r2);
-        if (r2 > s * s * 1.000001f) {
+        if (r2 > s * s * slack) {
             const float f = s * rsqrtf(r2);
             for (int k = 0; k < ndim; ++k) yv[k] *= f;
         }
