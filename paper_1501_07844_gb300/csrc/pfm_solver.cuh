@@ -102,7 +102,7 @@ struct Solver final : SolverBase {
                 if (e != cudaSuccess) return e;
                 a.zc = zc < 1 ? 1 : zc;
                 dim3 grid((a.nx + FTX - 1) / FTX, (a.ny + FTY - 1) / FTY, (a.nz + a.zc - 1) / a.zc);
-                fused_tma_kernel<MAXL, DIM, T><<<grid, FUSED_NT, Lay::total_bytes, s>>>(a, tma_maps[k]);
+                fused_tma_kernel<MAXL, DIM, T><<<grid, TMA_NT, Lay::total_bytes, s>>>(a, tma_maps[k]);
                 *launches = 1;
                 return cudaGetLastError();
             }

@@ -114,15 +114,29 @@ template <typename T> __device__ __forceinline__ void sts(T* p, float v);
 template <> __device__ __forceinline__ void sts<float>(float* p, float v) { *p = v; }
 template <> __device__ __forceinline__ void sts<__nv_bfloat16>(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
 
+// Two threads per voxel: thread pair (2v, 2v+1) shares voxel v, each owning
+// half of the labels, J(h, i) = 4*(i/2) + 2*h + i%2 (halves {0,1,4,5} and
+// {2,3,6,7}: the two lanes of a pair touch shared-memory banks 16 apart).
+// The per-voxel minimum and normaliser of the prox are combined with one
+// lane shuffle each; the flow step of a label needs nothing from the other
+// half.  This doubles the resident warps (20 per SM) for the same staging.
+constexpr int TMA_NT = 2 * FUSED_NT;  // 640 threads
+
+__device__ __forceinline__ int half_label(int h, int i) { return 4 * (i >> 1) + 2 * h + (i & 1); }
+
 template <int MAXL, int DIM, typename T>
-__global__ void __launch_bounds__(FUSED_NT, 1)
+__global__ void __launch_bounds__(TMA_NT, 1)
 fused_tma_kernel(const StepArgs<MAXL, MAXL> a, const __grid_constant__ TmaMaps maps) {
+    static_assert(MAXL % 4 == 0, "label halves need MAXL % 4 == 0");
+    constexpr int HL = MAXL / 2;
     using Lay = TmaLayout<MAXL, DIM, T>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ int s_abort;
     // TMA destinations start on 128-byte boundaries
     unsigned char* smem = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
     const int t = threadIdx.x;
+    const int h = t & 1;
+    const int v = t >> 1;
     const int nl = a.nl;
     const int x0 = blockIdx.x * FTX, y0 = blockIdx.y * FTY;
     const int z0 = blockIdx.z * a.zc;
@@ -137,6 +151,8 @@ fused_tma_kernel(const StepArgs<MAXL, MAXL> a, const __grid_constant__ TmaMaps m
     const unsigned bytes_q = (unsigned)(DIM * nl * TMA_QY * Lay::QBX * sizeof(T));
     const unsigned bytes_s = has_S ? (unsigned)(FTX * FTY * 4) : 0u;
     const unsigned bar0 = smem_addr(smem + Lay::bar_off);
+    constexpr int qstride = TMA_QY * Lay::QBX;
+    constexpr int ustride = TMA_UY * TMA_BX;
 
     auto stage_ptr = [&](int k) { return smem + k * Lay::stage_bytes; };
     // producer: bring plane p (full, or flows only) into stage k
@@ -161,6 +177,18 @@ fused_tma_kernel(const StepArgs<MAXL, MAXL> a, const __grid_constant__ TmaMaps m
     }
     __syncthreads();
 
+    // prox-phase voxel of this thread pair (halo-extended tile, row-major 33 x 9)
+    const bool inE = v < FNE;
+    const int ex = v % FEX, ey = v / FEX;
+    const int xe = x0 + ex, ye = y0 + ey;
+    const bool validE = inE && xe < a.nx && ye < a.ny;
+    const bool ownerE = validE && ex < FTX && ey < FTY;
+    // flow-phase voxel (owned 32 x 8 tile, row-major)
+    const bool inM = v < FTX * FTY;
+    const int mx = v % FTX, my = v / FTX;
+    const int xm = x0 + mx, ym = y0 + my;
+    const bool validM = inM && xm < a.nx && ym < a.ny;
+
     bool bad = false;
     int inflight_hi = z0;  // highest plane issued
     for (int p = z0; p <= z1; ++p) {
@@ -182,86 +210,93 @@ fused_tma_kernel(const StepArgs<MAXL, MAXL> a, const __grid_constant__ TmaMaps m
         __syncthreads();
         if (s_abort) break;
 
-        // ---- label prox of plane p on the halo-extended tile
-        if (p < a.nz && t < FNE) {
-            const int ex = t % FEX, ey = t / FEX;
-            const int x = x0 + ex, y = y0 + ey;
-            if (x < a.nx && y < a.ny) {
-                T* uS = reinterpret_cast<T*>(cst + Lay::u_off);
-                const float* dS = reinterpret_cast<const float*>(cst + Lay::d_off);
-                const T* qS = reinterpret_cast<const T*>(cst + Lay::q_off);
-                const T* qP = reinterpret_cast<const T*>(pst + Lay::q_off);
-                const int ui = ey * TMA_BX + ex;               // (ex, ey) in the u/D box
-                const int qi = (ey + 1) * Lay::QBX + (ex + Lay::QOFF);  // (ex, ey) in the flow box
-                const int qstride = TMA_QY * Lay::QBX;
-                float u[MAXL], Dv[MAXL], e[MAXL], g[MAXL];
+        // ---- label prox of plane p on the halo-extended tile (uniform branch)
+        if (p < a.nz) {
+            T* uS = reinterpret_cast<T*>(cst + Lay::u_off);
+            const float* dS = reinterpret_cast<const float*>(cst + Lay::d_off);
+            const T* qS = reinterpret_cast<const T*>(cst + Lay::q_off);
+            const T* qP = reinterpret_cast<const T*>(pst + Lay::q_off);
+            const int ui = ey * TMA_BX + ex;
+            const int qi = (ey + 1) * Lay::QBX + (ex + Lay::QOFF);
+            float u[HL], d[HL];
+            float mloc = 3.0e38f;
 #pragma unroll
-                for (int j = 0; j < MAXL; ++j) {
-                    if (j < nl) {
-                        u[j] = lds<T>(uS + j * TMA_UY * TMA_BX + ui);
-                        Dv[j] = dS[j * TMA_UY * TMA_BX + ui];
-                        const T* qx = qS + (j * DIM + 0) * qstride;
-                        const T* qy = qS + (j * DIM + 1) * qstride;
-                        float dv = (x < a.nx - 1 ? lds<T>(qx + qi) : 0.f) - lds<T>(qx + qi - 1);
-                        dv += (y < a.ny - 1 ? lds<T>(qy + qi) : 0.f) - lds<T>(qy + qi - Lay::QBX);
-                        if constexpr (DIM == 3) {
-                            const T* qz = qS + (j * DIM + 2) * qstride;
-                            const T* qzp = qP + (j * DIM + 2) * qstride;
-                            dv += (p < a.nz - 1 ? lds<T>(qz + qi) : 0.f) - lds<T>(qzp + qi);
-                        }
-                        e[j] = dv;
-                    } else {
-                        u[j] = Dv[j] = e[j] = 0.f;
-                    }
+            for (int i = 0; i < HL; ++i) {
+                const int j = half_label(h, i);
+                u[i] = 0.f;
+                d[i] = 0.f;
+                if (validE && j < nl) {
+                    u[i] = lds<T>(uS + j * ustride + ui);
+                    const T* qx = qS + (j * DIM + 0) * qstride + qi;
+                    const T* qy = qS + (j * DIM + 1) * qstride + qi;
+                    float dv = (xe < a.nx - 1 ? lds<T>(qx) : 0.f) - lds<T>(qx - 1);
+                    dv += (ye < a.ny - 1 ? lds<T>(qy) : 0.f) - lds<T>(qy - Lay::QBX);
+                    if constexpr (DIM == 3)
+                        dv += (p < a.nz - 1 ? lds<T>(qS + (j * DIM + 2) * qstride + qi) : 0.f) -
+                              lds<T>(qP + (j * DIM + 2) * qstride + qi);
+                    d[i] = dS[j * ustride + ui] + dv;
+                    mloc = fminf(mloc, d[i]);
                 }
-                float nrm;
-                if (!label_prox<MAXL, MAXL, false>(a, e, Dv, u, g, nrm)) bad = true;
+            }
+            // per-voxel shift m (NORMALISED only) and normaliser, over both halves
+            float m = fminf(mloc, __shfl_xor_sync(0xffffffffu, mloc, 1));
+            if (a.literal) m = 0.f;
+            float sloc = 0.f;
 #pragma unroll
-                for (int j = 0; j < MAXL; ++j)
-                    if (j < nl) sts<T>(uS + j * TMA_UY * TMA_BX + ui, g[j]);
-                if (ex < FTX && ey < FTY && p < z1) {
-                    const long long i = (long long)p * plane + (long long)y * a.nx + x;
+            for (int i = 0; i < HL; ++i) {
+                const int j = half_label(h, i);
+                if (validE && j < nl) {
+                    u[i] *= __expf(-(d[i] - m) * a.inv_c);
+                    sloc += u[i];
+                }
+            }
+            const float sum = sloc + __shfl_xor_sync(0xffffffffu, sloc, 1);
+            if (validE) {
+                if (!((sum > 0.f) && (sum <= 3.0e38f))) bad = true;
+                const float inv = 1.0f / sum;
+                const long long i0 = (long long)p * plane + (long long)ye * a.nx + xe;
 #pragma unroll
-                    for (int j = 0; j < MAXL; ++j)
-                        if (j < nl) stv<T>(uout + (long long)j * n + i, u[j]);
+                for (int i = 0; i < HL; ++i) {
+                    const int j = half_label(h, i);
+                    if (j < nl) {
+                        const float un = u[i] * inv;
+                        sts<T>(uS + j * ustride + ui, a.literal ? u[i] : un);
+                        if (ownerE && p < z1) stv<T>(uout + (long long)j * n + i0, un);
+                    }
                 }
             }
         }
         __syncthreads();
 
-        // ---- flow step of plane p-1
+        // ---- flow step of plane p-1 (one label half per thread)
         const int pm = p - 1;
-        if (pm >= z0 && t < FTX * FTY) {
-            const int mx = t % FTX, my = t / FTX;
-            const int x = x0 + mx, y = y0 + my;
-            if (x < a.nx && y < a.ny) {
-                const T* gP = reinterpret_cast<const T*>(pst + Lay::u_off);
-                const T* gC = reinterpret_cast<const T*>(cst + Lay::u_off);
-                const T* qP = reinterpret_cast<const T*>(pst + Lay::q_off);
-                const float* sP = reinterpret_cast<const float*>(pst + Lay::s_off);
-                const int ui = my * TMA_BX + mx;
-                const int qi = (my + 1) * Lay::QBX + (mx + Lay::QOFF);
-                const int qstride = TMA_QY * Lay::QBX;
-                const float sf = has_S ? sP[my * FTX + mx] : 1.0f;
-                const long long i = (long long)pm * plane + (long long)y * a.nx + x;
+        if (pm >= z0 && validM) {
+            const T* gP = reinterpret_cast<const T*>(pst + Lay::u_off);
+            const T* gC = reinterpret_cast<const T*>(cst + Lay::u_off);
+            const T* qP = reinterpret_cast<const T*>(pst + Lay::q_off);
+            const float* sP = reinterpret_cast<const float*>(pst + Lay::s_off);
+            const int ui = my * TMA_BX + mx;
+            const int qi = (my + 1) * Lay::QBX + (mx + Lay::QOFF);
+            const float sf = has_S ? sP[my * FTX + mx] : 1.0f;
+            const long long i0 = (long long)pm * plane + (long long)ym * a.nx + xm;
 #pragma unroll
-                for (int j = 0; j < MAXL; ++j) {
-                    if (j < nl) {
-                        const T* gj = gP + j * TMA_UY * TMA_BX;
-                        const float g0 = lds<T>(gj + ui);
-                        float yv[DIM];
-                        yv[0] = lds<T>(qP + (j * DIM + 0) * qstride + qi) -
-                                a.ctau * (x < a.nx - 1 ? lds<T>(gj + ui + 1) - g0 : 0.f);
-                        yv[1] = lds<T>(qP + (j * DIM + 1) * qstride + qi) -
-                                a.ctau * (y < a.ny - 1 ? lds<T>(gj + ui + TMA_BX) - g0 : 0.f);
-                        if constexpr (DIM == 3)
-                            yv[2] = lds<T>(qP + (j * DIM + 2) * qstride + qi) -
-                                    a.ctau * (pm < a.nz - 1 ? lds<T>(gC + j * TMA_UY * TMA_BX + ui) - g0 : 0.f);
-                        project<DIM>(yv, a.s_node[j] * sf, a.aniso);
-                        T* qa = qout + (long long)j * DIM * n + i;
+            for (int i = 0; i < HL; ++i) {
+                const int j = half_label(h, i);
+                if (j < nl) {
+                    const T* gj = gP + j * ustride;
+                    const float g0 = lds<T>(gj + ui);
+                    float yv[DIM];
+                    yv[0] = lds<T>(qP + (j * DIM + 0) * qstride + qi) -
+                            a.ctau * (xm < a.nx - 1 ? lds<T>(gj + ui + 1) - g0 : 0.f);
+                    yv[1] = lds<T>(qP + (j * DIM + 1) * qstride + qi) -
+                            a.ctau * (ym < a.ny - 1 ? lds<T>(gj + ui + TMA_BX) - g0 : 0.f);
+                    if constexpr (DIM == 3)
+                        yv[2] = lds<T>(qP + (j * DIM + 2) * qstride + qi) -
+                                a.ctau * (pm < a.nz - 1 ? lds<T>(gC + j * ustride + ui) - g0 : 0.f);
+                    project<DIM>(yv, a.s_node[j] * sf, a.aniso);
+                    T* qa = qout + (long long)j * DIM * n + i0;
 #pragma unroll
-                        for (int k = 0; k < DIM; ++k) stv<T>(qa + k * n, yv[k]);
-                    }
+                    for (int k = 0; k < DIM; ++k) stv<T>(qa + k * n, yv[k]);
                 }
             }
         }
@@ -279,7 +314,6 @@ fused_tma_kernel(const StepArgs<MAXL, MAXL> a, const __grid_constant__ TmaMaps m
         }
     }
 }
-
 
 // ---------------------------------------------------------------------------
 // TMA-staged energy / dual of a Potts state (same boxes and maps as the
