@@ -97,12 +97,20 @@ struct Solver final : SolverBase {
             if (fused && tma_ready && use_tma) {
                 using Lay = TmaLayout<MAXL, DIM, T>;
                 const int k = (u_in == tma_u[0]) ? 0 : 1;
-                cudaError_t e = cudaFuncSetAttribute(fused_tma_kernel<MAXL, DIM, T>,
-                                                     cudaFuncAttributeMaxDynamicSharedMemorySize, Lay::total_bytes);
-                if (e != cudaSuccess) return e;
                 a.zc = zc < 1 ? 1 : zc;
                 dim3 grid((a.nx + FTX - 1) / FTX, (a.ny + FTY - 1) / FTY, (a.nz + a.zc - 1) / a.zc);
-                fused_tma_kernel<MAXL, DIM, T><<<grid, TMA_NT, Lay::total_bytes, s>>>(a, tma_maps[k]);
+                cudaError_t e;
+                if (a.nl == MAXL) {
+                    e = cudaFuncSetAttribute(fused_tma_kernel<MAXL, DIM, T, true>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, Lay::total_bytes);
+                    if (e != cudaSuccess) return e;
+                    fused_tma_kernel<MAXL, DIM, T, true><<<grid, TMA_NT, Lay::total_bytes, s>>>(a, tma_maps[k]);
+                } else {
+                    e = cudaFuncSetAttribute(fused_tma_kernel<MAXL, DIM, T, false>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, Lay::total_bytes);
+                    if (e != cudaSuccess) return e;
+                    fused_tma_kernel<MAXL, DIM, T, false><<<grid, TMA_NT, Lay::total_bytes, s>>>(a, tma_maps[k]);
+                }
                 *launches = 1;
                 return cudaGetLastError();
             }

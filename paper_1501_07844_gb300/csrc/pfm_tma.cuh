@@ -124,7 +124,25 @@ constexpr int TMA_NT = 2 * FUSED_NT;  // 640 threads
 
 __device__ __forceinline__ int half_label(int h, int i) { return 4 * (i >> 1) + 2 * h + (i & 1); }
 
-template <int MAXL, int DIM, typename T>
+// Branch-free projection onto {|y| <= s} (s >= 0): scale min(1, s/|y|), with
+// s = 0 mapping every y to 0.
+template <int DIM>
+__device__ __forceinline__ void project_nb(float (&y)[DIM], float s, int aniso) {
+    if (aniso) {
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) y[k] = fminf(fmaxf(y[k], -s), s);
+    } else {
+        float r2 = 0.f;
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) r2 = fmaf(y[k], y[k], r2);
+        const float f = s > 0.f ? fminf(1.0f, s * rsqrtf(r2)) : 0.f;
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) y[k] *= f;
+    }
+}
+
+// EXACT: the problem has exactly MAXL labels (no per-label guards).
+template <int MAXL, int DIM, typename T, bool EXACT>
 __global__ void __launch_bounds__(TMA_NT, 1)
 fused_tma_kernel(const StepArgs<MAXL, MAXL> a, const __grid_constant__ TmaMaps maps) {
     static_assert(MAXL % 4 == 0, "label halves need MAXL % 4 == 0");
@@ -137,7 +155,7 @@ fused_tma_kernel(const StepArgs<MAXL, MAXL> a, const __grid_constant__ TmaMaps m
     const int t = threadIdx.x;
     const int h = t & 1;
     const int v = t >> 1;
-    const int nl = a.nl;
+    const int nl = EXACT ? MAXL : a.nl;
     const int x0 = blockIdx.x * FTX, y0 = blockIdx.y * FTY;
     const int z0 = blockIdx.z * a.zc;
     const int z1 = min(z0 + a.zc, a.nz);
@@ -151,6 +169,7 @@ fused_tma_kernel(const StepArgs<MAXL, MAXL> a, const __grid_constant__ TmaMaps m
     const unsigned bytes_q = (unsigned)(DIM * nl * TMA_QY * Lay::QBX * sizeof(T));
     const unsigned bytes_s = has_S ? (unsigned)(FTX * FTY * 4) : 0u;
     const unsigned bar0 = smem_addr(smem + Lay::bar_off);
+    const float kexp = -a.inv_c * 1.4426950408889634f;  // exp(-(d-m)/c) = 2^((d-m) kexp)
     constexpr int qstride = TMA_QY * Lay::QBX;
     constexpr int ustride = TMA_UY * TMA_BX;
 
@@ -218,6 +237,10 @@ fused_tma_kernel(const StepArgs<MAXL, MAXL> a, const __grid_constant__ TmaMaps m
             const T* qP = reinterpret_cast<const T*>(pst + Lay::q_off);
             const int ui = ey * TMA_BX + ex;
             const int qi = (ey + 1) * Lay::QBX + (ex + Lay::QOFF);
+            // Divergence without boundary tests: the normal flow component at
+            // the last index of each axis is an invariant zero of the stored
+            // state (zero at initialisation, kept by the flow step, enforced by
+            // pfm_set_flows) and the box is zero-filled outside the grid.
             float u[HL], d[HL];
             float mloc = 3.0e38f;
 #pragma unroll
@@ -225,15 +248,13 @@ fused_tma_kernel(const StepArgs<MAXL, MAXL> a, const __grid_constant__ TmaMaps m
                 const int j = half_label(h, i);
                 u[i] = 0.f;
                 d[i] = 0.f;
-                if (validE && j < nl) {
+                if (validE && (EXACT || j < nl)) {
                     u[i] = lds<T>(uS + j * ustride + ui);
                     const T* qx = qS + (j * DIM + 0) * qstride + qi;
                     const T* qy = qS + (j * DIM + 1) * qstride + qi;
-                    float dv = (xe < a.nx - 1 ? lds<T>(qx) : 0.f) - lds<T>(qx - 1);
-                    dv += (ye < a.ny - 1 ? lds<T>(qy) : 0.f) - lds<T>(qy - Lay::QBX);
+                    float dv = (lds<T>(qx) - lds<T>(qx - 1)) + (lds<T>(qy) - lds<T>(qy - Lay::QBX));
                     if constexpr (DIM == 3)
-                        dv += (p < a.nz - 1 ? lds<T>(qS + (j * DIM + 2) * qstride + qi) : 0.f) -
-                              lds<T>(qP + (j * DIM + 2) * qstride + qi);
+                        dv += lds<T>(qS + (j * DIM + 2) * qstride + qi) - lds<T>(qP + (j * DIM + 2) * qstride + qi);
                     d[i] = dS[j * ustride + ui] + dv;
                     mloc = fminf(mloc, d[i]);
                 }
@@ -245,8 +266,8 @@ fused_tma_kernel(const StepArgs<MAXL, MAXL> a, const __grid_constant__ TmaMaps m
 #pragma unroll
             for (int i = 0; i < HL; ++i) {
                 const int j = half_label(h, i);
-                if (validE && j < nl) {
-                    u[i] *= __expf(-(d[i] - m) * a.inv_c);
+                if (validE && (EXACT || j < nl)) {
+                    u[i] *= exp2f((d[i] - m) * kexp);
                     sloc += u[i];
                 }
             }
@@ -258,7 +279,7 @@ fused_tma_kernel(const StepArgs<MAXL, MAXL> a, const __grid_constant__ TmaMaps m
 #pragma unroll
                 for (int i = 0; i < HL; ++i) {
                     const int j = half_label(h, i);
-                    if (j < nl) {
+                    if (EXACT || j < nl) {
                         const float un = u[i] * inv;
                         sts<T>(uS + j * ustride + ui, a.literal ? u[i] : un);
                         if (ownerE && p < z1) stv<T>(uout + (long long)j * n + i0, un);
@@ -279,21 +300,23 @@ fused_tma_kernel(const StepArgs<MAXL, MAXL> a, const __grid_constant__ TmaMaps m
             const int qi = (my + 1) * Lay::QBX + (mx + Lay::QOFF);
             const float sf = has_S ? sP[my * FTX + mx] : 1.0f;
             const long long i0 = (long long)pm * plane + (long long)ym * a.nx + xm;
+            // forward differences are zero at the last index: fold that into the step
+            const float cx = xm < a.nx - 1 ? a.ctau : 0.f;
+            const float cy = ym < a.ny - 1 ? a.ctau : 0.f;
+            const float cz = pm < a.nz - 1 ? a.ctau : 0.f;
 #pragma unroll
             for (int i = 0; i < HL; ++i) {
                 const int j = half_label(h, i);
-                if (j < nl) {
+                if (EXACT || j < nl) {
                     const T* gj = gP + j * ustride;
                     const float g0 = lds<T>(gj + ui);
                     float yv[DIM];
-                    yv[0] = lds<T>(qP + (j * DIM + 0) * qstride + qi) -
-                            a.ctau * (xm < a.nx - 1 ? lds<T>(gj + ui + 1) - g0 : 0.f);
-                    yv[1] = lds<T>(qP + (j * DIM + 1) * qstride + qi) -
-                            a.ctau * (ym < a.ny - 1 ? lds<T>(gj + ui + TMA_BX) - g0 : 0.f);
+                    yv[0] = lds<T>(qP + (j * DIM + 0) * qstride + qi) - cx * (lds<T>(gj + ui + 1) - g0);
+                    yv[1] = lds<T>(qP + (j * DIM + 1) * qstride + qi) - cy * (lds<T>(gj + ui + TMA_BX) - g0);
                     if constexpr (DIM == 3)
                         yv[2] = lds<T>(qP + (j * DIM + 2) * qstride + qi) -
-                                a.ctau * (pm < a.nz - 1 ? lds<T>(gC + j * ustride + ui) - g0 : 0.f);
-                    project<DIM>(yv, a.s_node[j] * sf, a.aniso);
+                                cz * ((cz != 0.f ? lds<T>(gC + j * ustride + ui) : g0) - g0);
+                    project_nb<DIM>(yv, a.s_node[j] * sf, a.aniso);
                     T* qa = qout + (long long)j * DIM * n + i0;
 #pragma unroll
                     for (int k = 0; k < DIM; ++k) stv<T>(qa + k * n, yv[k]);
@@ -320,19 +343,25 @@ fused_tma_kernel(const StepArgs<MAXL, MAXL> a, const __grid_constant__ TmaMaps m
 // iteration).  Each CTA owns a 32 x 8 tile of a z-chunk; plane r needs u of
 // plane r+1 (z-gradient), so planes r+1 and r+2 are in flight while r is
 // summed; the own voxel's z-flow of plane r-1 (divergence) is carried in
-// registers.  One (E, P) partial per CTA, FP64 accumulation.
+// registers.  Four threads per voxel (lane 4k+h takes labels h, h+4, ...),
+// the per-voxel minimum of the dual combined by two lane shuffles.  One
+// (E, P) partial per CTA, FP64 accumulation.
 // ---------------------------------------------------------------------------
-constexpr int ENERGY_TMA_NT = FTX * FTY;
+constexpr int ENERGY_TMA_NT = 4 * FTX * FTY;  // 1024 threads
 
 template <int MAXL, int DIM, typename T>
 __global__ void __launch_bounds__(ENERGY_TMA_NT, 1)
 energy_tma_kernel(const StepArgs<MAXL, MAXL> a, const __grid_constant__ TmaMaps maps, double* partial) {
+    static_assert(MAXL % 4 == 0, "labels are split in four");
+    constexpr int QL = MAXL / 4;
     using Lay = TmaLayout<MAXL, DIM, T>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ int s_abort;
     __shared__ double sE[ENERGY_TMA_NT / 32], sP[ENERGY_TMA_NT / 32];
     unsigned char* smem = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
     const int t = threadIdx.x;
+    const int h = t & 3;
+    const int v = t >> 2;
     const int nl = a.nl;
     const int x0 = blockIdx.x * FTX, y0 = blockIdx.y * FTY;
     const int z0 = blockIdx.z * a.zc;
@@ -344,6 +373,8 @@ energy_tma_kernel(const StepArgs<MAXL, MAXL> a, const __grid_constant__ TmaMaps 
                            (unsigned)(DIM * nl * TMA_QY * Lay::QBX * sizeof(T)) +
                            (has_S ? (unsigned)(FTX * FTY * 4) : 0u);
     const unsigned bar0 = smem_addr(smem + Lay::bar_off);
+    constexpr int qstride = TMA_QY * Lay::QBX;
+    constexpr int ustride = TMA_UY * TMA_BX;
     auto stage_ptr = [&](int k) { return smem + k * Lay::stage_bytes; };
     auto issue = [&](int p, int k) {
         const unsigned bar = bar0 + 8 * k;
@@ -366,19 +397,21 @@ energy_tma_kernel(const StepArgs<MAXL, MAXL> a, const __grid_constant__ TmaMaps 
         }
     }
     __syncthreads();
-    const int mx = t % FTX, my = t / FTX;
+    const int mx = v % FTX, my = v / FTX;
     const int x = x0 + mx, y = y0 + my;
     const bool own = x < a.nx && y < a.ny;
-    float qzp[MAXL];  // own z-flow of plane r-1
+    float qzp[QL];  // own z-flow of plane r-1 for this thread's labels
 #pragma unroll
-    for (int j = 0; j < MAXL; ++j) qzp[j] = 0.f;
+    for (int i = 0; i < QL; ++i) qzp[i] = 0.f;
     if constexpr (DIM == 3) {
         if (own && z0 > 0) {
             const T* qin = static_cast<const T*>(a.q_in);
-            const long long i = (long long)(z0 - 1) * plane + (long long)y * a.nx + x;
+            const long long i0 = (long long)(z0 - 1) * plane + (long long)y * a.nx + x;
 #pragma unroll
-            for (int j = 0; j < MAXL; ++j)
-                if (j < nl) qzp[j] = ldv<T>(qin + ((long long)j * DIM + 2) * n + i);
+            for (int i = 0; i < QL; ++i) {
+                const int j = h + 4 * i;
+                if (j < nl) qzp[i] = ldv<T>(qin + ((long long)j * DIM + 2) * n + i0);
+            }
         }
     }
     double accE = 0.0, accP = 0.0;
@@ -397,6 +430,7 @@ energy_tma_kernel(const StepArgs<MAXL, MAXL> a, const __grid_constant__ TmaMaps 
         }
         __syncthreads();
         if (s_abort) break;
+        float eData = 0.f, tv = 0.f, dmin = 3.0e38f;
         if (own) {
             const unsigned char* cst = stage_ptr(cs);
             const unsigned char* nst = stage_ptr(n1);
@@ -407,21 +441,20 @@ energy_tma_kernel(const StepArgs<MAXL, MAXL> a, const __grid_constant__ TmaMaps 
             const float* sS = reinterpret_cast<const float*>(cst + Lay::s_off);
             const int ui = my * TMA_BX + mx;
             const int qi = (my + 1) * Lay::QBX + (mx + Lay::QOFF);
-            const int qstride = TMA_QY * Lay::QBX;
             const float sf = has_S ? sS[my * FTX + mx] : 1.0f;
-            float eData = 0.f, tv = 0.f, dmin = 3.0e38f;
 #pragma unroll
-            for (int j = 0; j < MAXL; ++j) {
+            for (int i = 0; i < QL; ++i) {
+                const int j = h + 4 * i;
                 if (j < nl) {
-                    const T* uj = uS + j * TMA_UY * TMA_BX;
+                    const T* uj = uS + j * ustride;
                     const float u0 = lds<T>(uj + ui);
-                    const float Dj = dS[j * TMA_UY * TMA_BX + ui];
+                    const float Dj = dS[j * ustride + ui];
                     eData = fmaf(Dj, u0, eData);
                     float gr[DIM];
                     gr[0] = x < a.nx - 1 ? lds<T>(uj + ui + 1) - u0 : 0.f;
                     gr[1] = y < a.ny - 1 ? lds<T>(uj + ui + TMA_BX) - u0 : 0.f;
                     if constexpr (DIM == 3)
-                        gr[2] = r < a.nz - 1 ? lds<T>(uN + j * TMA_UY * TMA_BX + ui) - u0 : 0.f;
+                        gr[2] = r < a.nz - 1 ? lds<T>(uN + j * ustride + ui) - u0 : 0.f;
                     float nv;
                     if (a.aniso) {
                         nv = 0.f;
@@ -440,14 +473,19 @@ energy_tma_kernel(const StepArgs<MAXL, MAXL> a, const __grid_constant__ TmaMaps 
                     dv += (y < a.ny - 1 ? lds<T>(qy + qi) : 0.f) - lds<T>(qy + qi - Lay::QBX);
                     if constexpr (DIM == 3) {
                         const float qz = lds<T>(qS + (j * DIM + 2) * qstride + qi);
-                        dv += (r < a.nz - 1 ? qz : 0.f) - qzp[j];
-                        qzp[j] = qz;
+                        dv += (r < a.nz - 1 ? qz : 0.f) - qzp[i];
+                        qzp[i] = qz;
                     }
                     dmin = fminf(dmin, Dj + dv);
                 }
             }
+        }
+        // minimum over the voxel's four label groups (lanes 4k .. 4k+3)
+        dmin = fminf(dmin, __shfl_xor_sync(0xffffffffu, dmin, 1));
+        dmin = fminf(dmin, __shfl_xor_sync(0xffffffffu, dmin, 2));
+        if (own) {
             accE += (double)eData + (double)tv;
-            accP += (double)dmin;
+            if (h == 0) accP += (double)dmin;
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
