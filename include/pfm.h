@@ -168,10 +168,18 @@ PFM_API pfm_status pfm_iterate(pfm_problem* pb, int n_iters);
  * (weak duality).  (sync)  PFM_ENONFINITE if either is not finite. */
 PFM_API pfm_status pfm_energy(pfm_problem* pb, double* primal, double* dual);
 
-/* Iterates in blocks of params.check_every until (E - P)/|E| <= gap_tol or
- * max_iters iterations were run; reports iterations run and the last gap.
- * Returns PFM_ENOTCONVERGED (with valid outputs) if the target was missed.
- * (sync) */
+/* Runs n_iters >= 1 iterations and returns E and P (as pfm_energy) of the
+ * state the LAST of them started from, i.e. after n_iters - 1 iterations.
+ * On the TMA-staged fused path that reduction happens inside the last
+ * iteration's kernel, which streams that state anyway (no extra pass);
+ * otherwise a separate reduction is queued just before it.  (sync) */
+PFM_API pfm_status pfm_iterate_energy(pfm_problem* pb, int n_iters, double* primal, double* dual);
+
+/* Iterates in blocks of params.check_every (each block through
+ * pfm_iterate_energy) until (E - P)/|E| <= gap_tol or max_iters iterations
+ * were run; reports iterations run and the last gap.  The gap is that of
+ * the state one iteration before the returned state.  Returns
+ * PFM_ENOTCONVERGED (with valid outputs) if the target was missed.  (sync) */
 PFM_API pfm_status pfm_run_to_gap(pfm_problem* pb, int max_iters, int* iters_done, double* rel_gap);
 
 /* Copies of the state into caller memory (host or device).  (sync)

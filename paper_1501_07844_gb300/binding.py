@@ -56,6 +56,7 @@ _SIGS = {
     "pfm_iterate": (C.c_int, [_P, C.c_int]),
     "pfm_energy": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "pfm_run_to_gap": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
+    "pfm_iterate_energy": (C.c_int, [_P, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "pfm_get_labels": (C.c_int, [_P, _P]),
     "pfm_get_argmax": (C.c_int, [_P, _P]),
     "pfm_get_flows": (C.c_int, [_P, _P]),
@@ -236,6 +237,12 @@ class Problem:
     def energy(self):
         E, P = C.c_double(), C.c_double()
         check(lib().pfm_energy(self._h, C.byref(E), C.byref(P)))
+        return E.value, P.value
+
+    def iterate_energy(self, n):
+        """n iterations; returns (E, P) of the state the last one started from."""
+        E, P = C.c_double(), C.c_double()
+        check(lib().pfm_iterate_energy(self._h, int(n), C.byref(E), C.byref(P)))
         return E.value, P.value
 
     def run_to_gap(self, max_iters):

@@ -497,6 +497,44 @@ pfm_status pfm_energy(pfm_problem* pb, double* primal, double* dual) {
     return flags_status(f);
 }
 
+pfm_status pfm_iterate_energy(pfm_problem* pb, int n_iters, double* primal, double* dual) {
+    if (!pb) return fail(PFM_EINVAL, "NULL problem");
+    if (n_iters < 1) return fail(PFM_EINVAL, "n_iters must be >= 1");
+    pfm_status st = pfm_iterate(pb, n_iters - 1);
+    if (st != PFM_OK) return st;
+    const bool fused = pb->prm.schedule != PFM_SCHEDULE_INPLACE;
+    const int src = pb->cur, dst = fused ? 1 - pb->cur : pb->cur;
+    int nlaunch = 0, nblocks = 0;
+    if (pb->solver->fuses_energy(fused)) {
+        // the last iteration reduces its own input while it streams it
+        PFM_CUDA(pb->solver->step(pb->u[src], pb->u[dst], pb->q[src], pb->q[dst], fused, pb->zc, pb->stream,
+                                  &nlaunch, pb->partial, &nblocks),
+                 "iterate");
+        pb->launches += nlaunch;
+    } else {
+        // separate reduction of the input, queued ahead of the last iteration
+        PFM_CUDA(pb->solver->energy(pb->u[src], pb->q[src], pb->partial, pb->energy_blocks, pb->zc, pb->stream,
+                                    &nblocks),
+                 "energy");
+        PFM_CUDA(pb->solver->step(pb->u[src], pb->u[dst], pb->q[src], pb->q[dst], fused, pb->zc, pb->stream,
+                                  &nlaunch),
+                 "iterate");
+        pb->launches += 1 + nlaunch;
+    }
+    pb->cur = dst;
+    pb->iters++;
+    PFM_CUDA(pfm::launch_energy_final(pb->partial, nblocks, pb->result, pb->flags, pb->stream), "energy");
+    pb->launches++;
+    double h[2];
+    PFM_CUDA(cudaMemcpyAsync(h, pb->result, sizeof h, cudaMemcpyDeviceToHost, pb->stream), "read energy");
+    unsigned f = 0;
+    st = read_flags(pb, &f);
+    if (st != PFM_OK) return st;
+    if (primal) *primal = h[0];
+    if (dual) *dual = h[1];
+    return flags_status(f);
+}
+
 pfm_status pfm_run_to_gap(pfm_problem* pb, int max_iters, int* iters_done, double* rel_gap) {
     if (!pb) return fail(PFM_EINVAL, "NULL problem");
     int done = 0;
@@ -504,12 +542,10 @@ pfm_status pfm_run_to_gap(pfm_problem* pb, int max_iters, int* iters_done, doubl
     pfm_status st = PFM_OK;
     while (done < max_iters) {
         const int k = std::min(pb->prm.check_every, max_iters - done);
-        st = pfm_iterate(pb, k);
+        double E, P;
+        st = pfm_iterate_energy(pb, k, &E, &P);
         if (st != PFM_OK) break;
         done += k;
-        double E, P;
-        st = pfm_energy(pb, &E, &P);
-        if (st != PFM_OK) break;
         gap = (E - P) / fabs(E);
         if (gap <= pb->prm.gap_tol) break;
     }

@@ -39,8 +39,12 @@ struct SolverBase {
     // One iteration reading (u_in, q_in) and writing (u_out, q_out); for the
     // in-place schedule u_in == u_out and q_in == q_out.  Returns the number
     // of kernels launched through *launches.
+    // With partial != nullptr, a kernel that can also evaluates the energy
+    // and dual of its input state into partial[2*k] and sets *nblocks = k;
+    // *nblocks = 0 means it did not (the caller reduces separately).
     virtual cudaError_t step(const void* u_in, void* u_out, const void* q_in, void* q_out, bool fused,
-                             int zc, cudaStream_t s, int* launches) = 0;
+                             int zc, cudaStream_t s, int* launches, double* partial = nullptr,
+                             int* nblocks = nullptr) = 0;
     // Per-block (E, P) partials of the energy of (u, q) into partial[2*k];
     // *nblocks receives k (<= max_blocks).
     virtual cudaError_t energy(const void* u, const void* q, double* partial, int max_blocks, int zc, cudaStream_t s,
@@ -53,6 +57,8 @@ struct SolverBase {
     bool use_tma = true;  // cleared to force the register-staged fused kernel
     // Name of the kernel family step() launches for the given schedule.
     virtual const char* variant(bool fused) const = 0;
+    // True if step() with a partials buffer evaluates the energy of its input.
+    virtual bool fuses_energy(bool fused) const { return false; }
 };
 
 template <int MAXL, int MAXN, int DIM, bool IS_DAG, typename T>
@@ -86,33 +92,42 @@ struct Solver final : SolverBase {
         fused_smem = sizeof(float) * 3 * MAXL * FNE;
     }
 
+    template <bool EXACT, bool WITH_E>
+    cudaError_t launch_tma(const StepArgs<MAXL, MAXN>& a, const TmaMaps& m, dim3 grid, double* partial,
+                           cudaStream_t s) {
+        using Lay = TmaLayout<MAXL, DIM, T>;
+        cudaError_t e = cudaFuncSetAttribute(fused_tma_kernel<MAXL, DIM, T, EXACT, WITH_E>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, Lay::total_bytes);
+        if (e != cudaSuccess) return e;
+        fused_tma_kernel<MAXL, DIM, T, EXACT, WITH_E><<<grid, TMA_NT, Lay::total_bytes, s>>>(a, m, partial);
+        return cudaGetLastError();
+    }
+
     cudaError_t step(const void* u_in, void* u_out, const void* q_in, void* q_out, bool fused, int zc,
-                     cudaStream_t s, int* launches) override {
+                     cudaStream_t s, int* launches, double* partial, int* nblocks) override {
         StepArgs<MAXL, MAXN> a = base;
         a.u_in = u_in;
         a.u_out = u_out;
         a.q_in = q_in;
         a.q_out = q_out;
+        if (nblocks) *nblocks = 0;
         if constexpr (kTmaCapable) {
             if (fused && tma_ready && use_tma) {
-                using Lay = TmaLayout<MAXL, DIM, T>;
                 const int k = (u_in == tma_u[0]) ? 0 : 1;
                 a.zc = zc < 1 ? 1 : zc;
                 dim3 grid((a.nx + FTX - 1) / FTX, (a.ny + FTY - 1) / FTY, (a.nz + a.zc - 1) / a.zc);
+                const bool exact = a.nl == MAXL;
                 cudaError_t e;
-                if (a.nl == MAXL) {
-                    e = cudaFuncSetAttribute(fused_tma_kernel<MAXL, DIM, T, true>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, Lay::total_bytes);
-                    if (e != cudaSuccess) return e;
-                    fused_tma_kernel<MAXL, DIM, T, true><<<grid, TMA_NT, Lay::total_bytes, s>>>(a, tma_maps[k]);
+                if (partial) {
+                    e = exact ? launch_tma<true, true>(a, tma_maps[k], grid, partial, s)
+                              : launch_tma<false, true>(a, tma_maps[k], grid, partial, s);
+                    if (nblocks) *nblocks = (int)(grid.x * grid.y * grid.z);
                 } else {
-                    e = cudaFuncSetAttribute(fused_tma_kernel<MAXL, DIM, T, false>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, Lay::total_bytes);
-                    if (e != cudaSuccess) return e;
-                    fused_tma_kernel<MAXL, DIM, T, false><<<grid, TMA_NT, Lay::total_bytes, s>>>(a, tma_maps[k]);
+                    e = exact ? launch_tma<true, false>(a, tma_maps[k], grid, nullptr, s)
+                              : launch_tma<false, false>(a, tma_maps[k], grid, nullptr, s);
                 }
                 *launches = 1;
-                return cudaGetLastError();
+                return e;
             }
         }
         if (fused) {
@@ -170,6 +185,8 @@ struct Solver final : SolverBase {
             return true;
         }
     }
+
+    bool fuses_energy(bool fused) const override { return fused && kTmaCapable && tma_ready && use_tma; }
 
     const char* variant(bool fused) const override {
         if (!fused) return "inplace";

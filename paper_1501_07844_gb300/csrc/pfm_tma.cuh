@@ -47,7 +47,10 @@ struct TmaLayout {
     static constexpr int q_off = align128(d_off + u_elems * 4);
     static constexpr int s_off = align128(q_off + q_elems * (int)sizeof(T));
     static constexpr int stage_bytes = align128(s_off + s_elems * 4);
-    static constexpr int bar_off = TMA_STAGES * stage_bytes;
+    // field g (what the flow step differentiates) of planes p-1 and p, FP32
+    static constexpr int g_elems = MAXL * TMA_UY * TMA_BX;
+    static constexpr int g_off = TMA_STAGES * stage_bytes;
+    static constexpr int bar_off = align128(g_off + 2 * g_elems * 4);
     static constexpr int total_bytes = bar_off + 64 + 128;  // + slack to align the base to 128 B
 };
 
@@ -142,14 +145,20 @@ __device__ __forceinline__ void project_nb(float (&y)[DIM], float s, int aniso) 
 }
 
 // EXACT: the problem has exactly MAXL labels (no per-label guards).
-template <int MAXL, int DIM, typename T, bool EXACT>
+// WITH_E: also accumulate the primal energy E(u) and the pseudo-flow dual
+// P(q) of the INPUT state (u_in, q_in) of this iteration into one (E, P)
+// partial per CTA: P of plane p from the prox's per-voxel minimum, E of
+// plane p-1 (whose z-gradient needs plane p) during the flow phase.  The
+// staged u is never overwritten, so its neighbours are still the input.
+template <int MAXL, int DIM, typename T, bool EXACT, bool WITH_E>
 __global__ void __launch_bounds__(TMA_NT, 1)
-fused_tma_kernel(const StepArgs<MAXL, MAXL> a, const __grid_constant__ TmaMaps maps) {
+fused_tma_kernel(const StepArgs<MAXL, MAXL> a, const __grid_constant__ TmaMaps maps, double* partial) {
     static_assert(MAXL % 4 == 0, "label halves need MAXL % 4 == 0");
     constexpr int HL = MAXL / 2;
     using Lay = TmaLayout<MAXL, DIM, T>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ int s_abort;
+    __shared__ double sE[TMA_NT / 32], sP[TMA_NT / 32];
     // TMA destinations start on 128-byte boundaries
     unsigned char* smem = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
     const int t = threadIdx.x;
@@ -172,6 +181,7 @@ fused_tma_kernel(const StepArgs<MAXL, MAXL> a, const __grid_constant__ TmaMaps m
     const float kexp = -a.inv_c * 1.4426950408889634f;  // exp(-(d-m)/c) = 2^((d-m) kexp)
     constexpr int qstride = TMA_QY * Lay::QBX;
     constexpr int ustride = TMA_UY * TMA_BX;
+    float* gbuf = reinterpret_cast<float*>(smem + Lay::g_off);
 
     auto stage_ptr = [&](int k) { return smem + k * Lay::stage_bytes; };
     // producer: bring plane p (full, or flows only) into stage k
@@ -209,6 +219,7 @@ fused_tma_kernel(const StepArgs<MAXL, MAXL> a, const __grid_constant__ TmaMaps m
     const bool validM = inM && xm < a.nx && ym < a.ny;
 
     bool bad = false;
+    double accE = 0.0, accP = 0.0;
     int inflight_hi = z0;  // highest plane issued
     for (int p = z0; p <= z1; ++p) {
         const int s = p - z0 + 1;
@@ -219,6 +230,8 @@ fused_tma_kernel(const StepArgs<MAXL, MAXL> a, const __grid_constant__ TmaMaps m
         }
         unsigned char* cst = stage_ptr(cs);
         unsigned char* pst = stage_ptr(ps);
+        float* gC = gbuf + (p & 1) * Lay::g_elems;        // g of plane p (written now)
+        const float* gP = gbuf + ((p + 1) & 1) * Lay::g_elems;  // g of plane p-1
         bool ok = true;
         if (p == z0) ok = mbar_wait_bounded(bar0 + 8 * ps, 0u);
         if (p < a.nz && ok) ok = mbar_wait_bounded(bar0 + 8 * cs, (unsigned)((s / 3) & 1));
@@ -231,7 +244,7 @@ fused_tma_kernel(const StepArgs<MAXL, MAXL> a, const __grid_constant__ TmaMaps m
 
         // ---- label prox of plane p on the halo-extended tile (uniform branch)
         if (p < a.nz) {
-            T* uS = reinterpret_cast<T*>(cst + Lay::u_off);
+            const T* uS = reinterpret_cast<const T*>(cst + Lay::u_off);
             const float* dS = reinterpret_cast<const float*>(cst + Lay::d_off);
             const T* qS = reinterpret_cast<const T*>(cst + Lay::q_off);
             const T* qP = reinterpret_cast<const T*>(pst + Lay::q_off);
@@ -259,9 +272,13 @@ fused_tma_kernel(const StepArgs<MAXL, MAXL> a, const __grid_constant__ TmaMaps m
                     mloc = fminf(mloc, d[i]);
                 }
             }
-            // per-voxel shift m (NORMALISED only) and normaliser, over both halves
-            float m = fminf(mloc, __shfl_xor_sync(0xffffffffu, mloc, 1));
-            if (a.literal) m = 0.f;
+            // per-voxel minimum over both halves: the dual term of this voxel,
+            // and the exponent shift (NORMALISED only)
+            const float dmin = fminf(mloc, __shfl_xor_sync(0xffffffffu, mloc, 1));
+            if constexpr (WITH_E) {
+                if (ownerE && p < z1 && h == 0) accP += (double)dmin;
+            }
+            const float m = a.literal ? 0.f : dmin;
             float sloc = 0.f;
 #pragma unroll
             for (int i = 0; i < HL; ++i) {
@@ -281,7 +298,7 @@ fused_tma_kernel(const StepArgs<MAXL, MAXL> a, const __grid_constant__ TmaMaps m
                     const int j = half_label(h, i);
                     if (EXACT || j < nl) {
                         const float un = u[i] * inv;
-                        sts<T>(uS + j * ustride + ui, a.literal ? u[i] : un);
+                        gC[j * ustride + ui] = a.literal ? u[i] : un;
                         if (ownerE && p < z1) stv<T>(uout + (long long)j * n + i0, un);
                     }
                 }
@@ -292,8 +309,6 @@ fused_tma_kernel(const StepArgs<MAXL, MAXL> a, const __grid_constant__ TmaMaps m
         // ---- flow step of plane p-1 (one label half per thread)
         const int pm = p - 1;
         if (pm >= z0 && validM) {
-            const T* gP = reinterpret_cast<const T*>(pst + Lay::u_off);
-            const T* gC = reinterpret_cast<const T*>(cst + Lay::u_off);
             const T* qP = reinterpret_cast<const T*>(pst + Lay::q_off);
             const float* sP = reinterpret_cast<const float*>(pst + Lay::s_off);
             const int ui = my * TMA_BX + mx;
@@ -304,24 +319,52 @@ fused_tma_kernel(const StepArgs<MAXL, MAXL> a, const __grid_constant__ TmaMaps m
             const float cx = xm < a.nx - 1 ? a.ctau : 0.f;
             const float cy = ym < a.ny - 1 ? a.ctau : 0.f;
             const float cz = pm < a.nz - 1 ? a.ctau : 0.f;
+            float eloc = 0.f;
 #pragma unroll
             for (int i = 0; i < HL; ++i) {
                 const int j = half_label(h, i);
                 if (EXACT || j < nl) {
-                    const T* gj = gP + j * ustride;
-                    const float g0 = lds<T>(gj + ui);
+                    const float* gj = gP + j * ustride;
+                    const float g0 = gj[ui];
                     float yv[DIM];
-                    yv[0] = lds<T>(qP + (j * DIM + 0) * qstride + qi) - cx * (lds<T>(gj + ui + 1) - g0);
-                    yv[1] = lds<T>(qP + (j * DIM + 1) * qstride + qi) - cy * (lds<T>(gj + ui + TMA_BX) - g0);
+                    yv[0] = lds<T>(qP + (j * DIM + 0) * qstride + qi) - cx * (gj[ui + 1] - g0);
+                    yv[1] = lds<T>(qP + (j * DIM + 1) * qstride + qi) - cy * (gj[ui + TMA_BX] - g0);
                     if constexpr (DIM == 3)
                         yv[2] = lds<T>(qP + (j * DIM + 2) * qstride + qi) -
-                                cz * ((cz != 0.f ? lds<T>(gC + j * ustride + ui) : g0) - g0);
-                    project_nb<DIM>(yv, a.s_node[j] * sf, a.aniso);
+                                cz * ((cz != 0.f ? gC[j * ustride + ui] : g0) - g0);
+                    const float sj = a.s_node[j] * sf;
+                    if constexpr (WITH_E) {
+                        // E of plane p-1 on the input labelling (staged u of planes p-1 and p)
+                        const T* uj = reinterpret_cast<const T*>(pst + Lay::u_off) + j * ustride;
+                        const float u0 = lds<T>(uj + ui);
+                        float gr[DIM];
+                        gr[0] = cx != 0.f ? lds<T>(uj + ui + 1) - u0 : 0.f;
+                        gr[1] = cy != 0.f ? lds<T>(uj + ui + TMA_BX) - u0 : 0.f;
+                        if constexpr (DIM == 3)
+                            gr[2] = cz != 0.f
+                                        ? lds<T>(reinterpret_cast<const T*>(cst + Lay::u_off) + j * ustride + ui) - u0
+                                        : 0.f;
+                        float nv;
+                        if (a.aniso) {
+                            nv = 0.f;
+#pragma unroll
+                            for (int k = 0; k < DIM; ++k) nv += fabsf(gr[k]);
+                        } else {
+                            float r2 = 0.f;
+#pragma unroll
+                            for (int k = 0; k < DIM; ++k) r2 = fmaf(gr[k], gr[k], r2);
+                            nv = sqrtf(r2);
+                        }
+                        const float Dj = reinterpret_cast<const float*>(pst + Lay::d_off)[j * ustride + ui];
+                        eloc = fmaf(Dj, u0, fmaf(sj, nv, eloc));
+                    }
+                    project_nb<DIM>(yv, sj, a.aniso);
                     T* qa = qout + (long long)j * DIM * n + i0;
 #pragma unroll
                     for (int k = 0; k < DIM; ++k) stv<T>(qa + k * n, yv[k]);
                 }
             }
+            if constexpr (WITH_E) accE += (double)eloc;
         }
         // order this plane's shared-memory accesses before the TMA that
         // refills stage ps at the next step
@@ -334,6 +377,28 @@ fused_tma_kernel(const StepArgs<MAXL, MAXL> a, const __grid_constant__ TmaMaps m
         for (int p = z0 - 1; p <= inflight_hi; ++p) {
             const int s = p - z0 + 1;
             mbar_wait_bounded(bar0 + 8 * (s % 3), (unsigned)((s / 3) & 1));
+        }
+    }
+    if constexpr (WITH_E) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            accE += __shfl_down_sync(0xffffffffu, accE, off);
+            accP += __shfl_down_sync(0xffffffffu, accP, off);
+        }
+        if ((t & 31) == 0) {
+            sE[t >> 5] = accE;
+            sP[t >> 5] = accP;
+        }
+        __syncthreads();
+        if (t == 0) {
+            double E = 0.0, P = 0.0;
+            for (int k = 0; k < TMA_NT / 32; ++k) {
+                E += sE[k];
+                P += sP[k];
+            }
+            const long long b = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+            partial[2 * b] = E;
+            partial[2 * b + 1] = P;
         }
     }
 }

@@ -214,3 +214,25 @@ def test_kernel_variant_selection():
             gpu_problem(p_odd, storage=pfm.BF16) as f:
         assert (a.variant, b.variant, c.variant, d.variant, e.variant, f.variant) == \
             ("fused_tma", "fused", "fused", "inplace", "fused_tma", "fused")
+
+
+@pytest.mark.parametrize("sched", [0, 1, 2], ids=["fused_tma", "inplace", "fused_plain"])
+@pytest.mark.parametrize("storage", [0, 1], ids=["f32", "bf16"])
+def test_iterate_energy_reports_input_of_last_iteration(sched, storage):
+    """pfm_iterate_energy(n) returns E and P of the state after n-1 iterations
+    (reduced inside the last iteration on the TMA path) and leaves the state
+    after n iterations, identical to plain iterations."""
+    prob = synth.potts3d_problem(seed=2400, nl=8, shape=(19, 27, 40))
+    with gpu_problem(prob, schedule=sched, storage=storage) as a, \
+            gpu_problem(prob, schedule=sched, storage=storage) as b:
+        a.iterate(6)
+        E_ref, P_ref = a.energy()
+        a.iterate(1)
+        E, P = b.iterate_energy(7)
+        assert abs(E - E_ref) <= 1e-6 * abs(E_ref) and abs(P - P_ref) <= 1e-6 * abs(P_ref) + 1e-6
+        assert np.array_equal(a.labels().cpu().numpy(), b.labels().cpu().numpy())
+        assert np.array_equal(a.flows().cpu().numpy(), b.flows().cpu().numpy())
+        assert b.iterations == 7
+    if storage == 0:
+        _, _, E_o, P_o = oracle_run(prob, 6)
+        assert abs(E - E_o) <= 1e-5 * abs(E_o) and abs(P - P_o) <= 1e-5 * abs(P_o)
