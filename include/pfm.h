@@ -213,6 +213,36 @@ PFM_API const char* pfm_kernel_variant(const pfm_problem* pb);
 PFM_API int64_t pfm_iterations_done(const pfm_problem* pb);
 PFM_API int64_t pfm_launch_count(const pfm_problem* pb);
 
+/* ---- Batches (many independent problems, one persistent kernel per
+ * iteration) ----
+ * A batch advances n problems of possibly different grid sizes and label
+ * DAGs in lockstep: each pfm_batch_iterate iteration is ONE launch of a
+ * persistent kernel whose CTAs walk a work list of (member, x tile, y tile,
+ * z chunk) items, and runs of 20 iterations are replayed from a captured
+ * CUDA graph.  All members share params (the schedule is always the
+ * double-buffered one) and ndim; each member is an ordinary pfm_problem
+ * owned by the batch: read it back with pfm_get_* through
+ * pfm_batch_member, but advance it only through pfm_batch_iterate.  stream
+ * NULL makes the batch create its own stream (capture needs one other than
+ * the legacy default stream).  Errors of member creation are reported with
+ * the member index. */
+typedef struct pfm_batch pfm_batch;
+PFM_API pfm_status pfm_batch_create(int n, const pfm_desc* descs, const pfm_params* params, void* stream,
+                                    pfm_batch** out);
+PFM_API void pfm_batch_destroy(pfm_batch* b);
+PFM_API int pfm_batch_size(const pfm_batch* b);
+PFM_API pfm_status pfm_batch_member(pfm_batch* b, int index, pfm_problem** out);
+/* n_iters >= 0 iterations of every member (asynchronous). */
+PFM_API pfm_status pfm_batch_iterate(pfm_batch* b, int n_iters);
+/* E and P of every member (arrays of pfm_batch_size entries).  (sync) */
+PFM_API pfm_status pfm_batch_energy(pfm_batch* b, double* primal, double* dual);
+/* Autotuner: times trial_iters iterations for each z-chunk length in
+ * {8, 16, 32, 64} and persistent grid sizes (resident CTAs, twice that, one
+ * CTA per item), keeps the fastest, then RESETS every member to the initial
+ * state (u = 1/#leaves, q = 0).  Reports the choice.  (sync) */
+PFM_API pfm_status pfm_batch_tune(pfm_batch* b, int trial_iters, int* zc_out, int* grid_out);
+PFM_API int64_t pfm_batch_launch_count(const pfm_batch* b);
+
 /* Allocation-free energy evaluation.  The paper has no counterpart: this is
  * a service for callers that cannot call cudaMalloc -- code whose device
  * memory belongs to an outer allocator that has already claimed the budget

@@ -11,6 +11,7 @@ binding raises if the library cannot be loaded.
 from .binding import (  # noqa: F401
     ANISO,
     BF16,
+    Batch,
     F32,
     FUSED,
     FUSED_PLAIN,

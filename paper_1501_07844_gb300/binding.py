@@ -67,6 +67,14 @@ _SIGS = {
     "pfm_kernel_variant": (C.c_char_p, [_P]),
     "pfm_iterations_done": (C.c_int64, [_P]),
     "pfm_launch_count": (C.c_int64, [_P]),
+    "pfm_batch_create": (C.c_int, [C.c_int, C.c_void_p, C.POINTER(pfm_params), _P, C.POINTER(_P)]),
+    "pfm_batch_destroy": (None, [_P]),
+    "pfm_batch_size": (C.c_int, [_P]),
+    "pfm_batch_member": (C.c_int, [_P, C.c_int, C.POINTER(_P)]),
+    "pfm_batch_iterate": (C.c_int, [_P, C.c_int]),
+    "pfm_batch_energy": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "pfm_batch_tune": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "pfm_batch_launch_count": (C.c_int64, [_P]),
     "pfm_potts_energy_noalloc": (C.c_int, [C.c_int, C.POINTER(C.c_int64), C.c_int, _P, _P, _P, _P,
                                            C.POINTER(C.c_float), C.c_int, _P, _P]),
 }
@@ -296,3 +304,92 @@ class Problem:
     def set_flows(self, q):
         q = _as_f32(q)
         check(lib().pfm_set_flows(self._h, _ptr(q)))
+
+
+class _Member(Problem):
+    """A batch member: a pfm_problem owned by its batch (read-only use)."""
+
+    def __init__(self, handle, spatial, n_nodes):
+        self._h = handle
+        self.spatial = tuple(spatial)
+        self.n_nodes = int(n_nodes)
+        nd, dims, nleaf, nnod = C.c_int(), (C.c_int64 * 3)(), C.c_int(), C.c_int()
+        check(lib().pfm_shape(self._h, C.byref(nd), dims, C.byref(nleaf), C.byref(nnod)))
+        self.ndim, self.n_leaf = nd.value, nleaf.value
+
+    def close(self):  # owned by the batch
+        self._h = None
+
+    def iterate(self, n):
+        raise RuntimeError("batch members advance only through Batch.iterate")
+
+
+class Batch:
+    """Many independent problems advanced together (pfm_batch_*).
+
+    problems: list of dicts with keys D, S_field, s_node, n_nodes, edges
+    (as for Problem); every member shares the keyword parameters."""
+
+    def __init__(self, problems, stream=None, **kw):
+        kw.setdefault("schedule", FUSED)
+        self._keep = []
+        descs = (pfm_desc * len(problems))()
+        self._shapes = []
+        for k, p in enumerate(problems):
+            D = _as_f32(p["D"])
+            S = _as_f32(p.get("S_field"))
+            edges = p.get("edges")
+            nn = p.get("n_nodes")
+            if edges is None:
+                nn, edges = D.shape[0], [(-1, L, 1.0) for L in range(D.shape[0])]
+            d = _Desc(tuple(D.shape[1:]), nn, edges, _ptr(D), _ptr(S), p.get("s_node"))
+            self._keep += [D, S, d]
+            descs[k] = d.c
+            self._shapes.append((tuple(D.shape[1:]), nn))
+        self._params = params(**kw)
+        h = C.c_void_p()
+        check(lib().pfm_batch_create(len(problems), C.cast(descs, C.c_void_p), C.byref(self._params),
+                                     stream if stream is not None else _stream_handle(None), C.byref(h)))
+        self._h = h
+        self.members = []
+        for k, (spatial, nn) in enumerate(self._shapes):
+            m = C.c_void_p()
+            check(lib().pfm_batch_member(self._h, k, C.byref(m)))
+            self.members.append(_Member(m, spatial, nn))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            for m in self.members:
+                m.close()
+            lib().pfm_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def iterate(self, n):
+        check(lib().pfm_batch_iterate(self._h, int(n)))
+
+    def energy(self):
+        n = len(self.members)
+        E, P = (C.c_double * n)(), (C.c_double * n)()
+        check(lib().pfm_batch_energy(self._h, E, P))
+        return list(E), list(P)
+
+    def tune(self, trial_iters=3):
+        zc, grid = C.c_int(), C.c_int()
+        check(lib().pfm_batch_tune(self._h, int(trial_iters), C.byref(zc), C.byref(grid)))
+        return zc.value, grid.value
+
+    @property
+    def launches(self):
+        return lib().pfm_batch_launch_count(self._h)

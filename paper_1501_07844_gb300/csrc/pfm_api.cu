@@ -235,6 +235,28 @@ struct pfm_problem {
 
 namespace {
 
+pfm::ProblemView view_of(const pfm_problem* pb) {
+    pfm::ProblemView v{};
+    v.ndim = pb->ndim;
+    v.nx = pb->nx;
+    v.ny = pb->ny;
+    v.nz = pb->nz;
+    v.nl = pb->nl;
+    v.nn = pb->nn;
+    v.n = pb->n;
+    v.c = (float)pb->prm.c;
+    v.tau = (float)pb->prm.tau;
+    v.literal = pb->prm.grad_source == PFM_GRAD_PAPER_LITERAL;
+    v.aniso = pb->prm.norm == PFM_NORM_ANISO;
+    v.D = pb->D;
+    v.S = pb->S;
+    v.abuf = pb->abuf;
+    v.flags = pb->flags;
+    v.s_node = pb->s_node.data();
+    v.W = pb->W.data();
+    return v;
+}
+
 pfm_status read_flags(pfm_problem* pb, unsigned* out) {
     unsigned h = 0;
     PFM_CUDA(cudaMemcpyAsync(&h, pb->flags, sizeof h, cudaMemcpyDeviceToHost, pb->stream), "read flags");
@@ -382,24 +404,7 @@ pfm_status pfm_create(const pfm_desc* desc, const pfm_params* params, void* stre
         return bail(cuda_fail(e, "validate"));
     pb->launches++;
 
-    pfm::ProblemView v{};
-    v.ndim = pb->ndim;
-    v.nx = pb->nx;
-    v.ny = pb->ny;
-    v.nz = pb->nz;
-    v.nl = pb->nl;
-    v.nn = pb->nn;
-    v.n = n;
-    v.c = (float)params->c;
-    v.tau = (float)params->tau;
-    v.literal = params->grad_source == PFM_GRAD_PAPER_LITERAL;
-    v.aniso = params->norm == PFM_NORM_ANISO;
-    v.D = pb->D;
-    v.S = pb->S;
-    v.abuf = pb->abuf;
-    v.flags = pb->flags;
-    v.s_node = pb->s_node.data();
-    v.W = pb->W.data();
+    const pfm::ProblemView v = view_of(pb);
     const bool bf16 = params->storage == PFM_STORAGE_BF16;
     if (pb->flat) {
         const int ml = potts_bucket(pb->nl);
@@ -693,5 +698,247 @@ const char* pfm_kernel_variant(const pfm_problem* pb) {
 
 int64_t pfm_iterations_done(const pfm_problem* pb) { return pb ? pb->iters : -1; }
 int64_t pfm_launch_count(const pfm_problem* pb) { return pb ? pb->launches : -1; }
+
+// ---------------------------------------------------------------------------
+// Batches: many independent problems advanced together by one persistent
+// kernel per iteration (work list over all members' tiles); iterations are
+// replayed from captured CUDA graphs.
+// ---------------------------------------------------------------------------
+}  // extern "C"
+
+struct pfm_batch {
+    std::vector<pfm_problem*> probs;
+    std::vector<pfm::BatchMember> members;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    pfm::BatchBase* runner = nullptr;
+    int zc = 16;
+    int grid = 0;
+    int sms = 0;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    int64_t launches = 0;
+};
+
+namespace {
+
+constexpr int kGraphIters = 20;  // iterations per captured graph (even: parity preserved)
+
+void batch_drop_graphs(pfm_batch* b) {
+    for (int p = 0; p < 2; ++p)
+        if (b->graph[p]) {
+            cudaGraphExecDestroy(b->graph[p]);
+            b->graph[p] = nullptr;
+        }
+}
+
+void batch_free(pfm_batch* b) {
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    batch_drop_graphs(b);
+    delete b->runner;
+    for (pfm_problem* p : b->probs) pfm_destroy(p);
+    if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+    cudaGetLastError();
+    delete b;
+}
+
+pfm_status batch_setup(pfm_batch* b, int zc, int grid) {
+    batch_drop_graphs(b);
+    PFM_CUDA(b->runner->setup(b->members.data(), (int)b->members.size(), zc), "batch setup");
+    b->zc = zc;
+    const int resident = b->runner->ctas_per_sm() * b->sms;
+    b->grid = grid > 0 ? grid : std::min(resident, b->runner->n_items());
+    return PFM_OK;
+}
+
+pfm_status batch_launch_direct(pfm_batch* b, int parity, int n) {
+    for (int i = 0; i < n; ++i) {
+        PFM_CUDA(b->runner->launch((parity + i) & 1, b->grid, b->stream), "batch launch");
+        b->launches++;
+    }
+    return PFM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+pfm_status pfm_batch_create(int n, const pfm_desc* descs, const pfm_params* params, void* stream, pfm_batch** out) {
+    if (!out) return fail(PFM_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (n < 1 || !descs) return fail(PFM_EINVAL, "need n >= 1 descriptions");
+    pfm_status st = check_params(params);
+    if (st != PFM_OK) return st;
+    if (params->schedule == PFM_SCHEDULE_INPLACE)
+        return fail(PFM_EUNSUPPORTED, "batches use the double-buffered (fused) schedule");
+    pfm_batch* b = new pfm_batch();
+    if (stream) {
+        b->stream = (cudaStream_t)stream;
+    } else {
+        // graph capture needs a stream other than the legacy default stream
+        cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            delete b;
+            return cuda_fail(e, "batch stream");
+        }
+        b->own_stream = true;
+    }
+    pfm_params p2 = *params;
+    p2.schedule = PFM_SCHEDULE_FUSED_PLAIN;
+    int ndim = descs[0].ndim, maxl = 0, maxn = 0;
+    bool any_dag = false;
+    for (int k = 0; k < n; ++k) {
+        if (descs[k].ndim != ndim) {
+            batch_free(b);
+            return fail(PFM_EINVAL, "all members of a batch need the same ndim");
+        }
+        pfm_problem* pb = nullptr;
+        st = pfm_create(&descs[k], &p2, b->stream, &pb);
+        if (st != PFM_OK) {
+            const std::string msg = "member " + std::to_string(k) + ": " + g_err;
+            batch_free(b);
+            return fail(st, "%s", msg.c_str());
+        }
+        b->probs.push_back(pb);
+        maxl = std::max(maxl, pb->nl);
+        maxn = std::max(maxn, pb->nn);
+        any_dag = any_dag || !pb->flat;
+    }
+    const bool bf16 = params->storage == PFM_STORAGE_BF16;
+    if (!any_dag) {
+        const int ml = potts_bucket(maxl);
+        b->runner = bf16 ? pfm::make_batch_potts_bf16(ml, ndim) : pfm::make_batch_potts_f32(ml, ndim);
+    } else {
+        int ml, mn;
+        dag_bucket(maxl, maxn, &ml, &mn);
+        if (ml) b->runner = bf16 ? pfm::make_batch_dag_bf16(ml, mn, ndim) : pfm::make_batch_dag_f32(ml, mn, ndim);
+    }
+    if (!b->runner) {
+        batch_free(b);
+        return fail(PFM_EUNSUPPORTED, "no batched kernel bucket for these members");
+    }
+    for (pfm_problem* pb : b->probs) {
+        pfm::BatchMember m;
+        m.view = view_of(pb);
+        for (int k = 0; k < 2; ++k) {
+            m.u[k] = pb->u[k];
+            m.q[k] = pb->q[k];
+        }
+        b->members.push_back(m);
+    }
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
+    st = batch_setup(b, 16, 0);
+    if (st != PFM_OK) {
+        batch_free(b);
+        return st;
+    }
+    *out = b;
+    return PFM_OK;
+}
+
+void pfm_batch_destroy(pfm_batch* b) {
+    if (b) batch_free(b);
+}
+
+int pfm_batch_size(const pfm_batch* b) { return b ? (int)b->probs.size() : 0; }
+
+pfm_status pfm_batch_member(pfm_batch* b, int index, pfm_problem** out) {
+    if (!b || !out || index < 0 || index >= (int)b->probs.size()) return fail(PFM_EINVAL, "bad batch member index");
+    *out = b->probs[index];
+    return PFM_OK;
+}
+
+pfm_status pfm_batch_iterate(pfm_batch* b, int n_iters) {
+    if (!b) return fail(PFM_EINVAL, "NULL batch");
+    if (n_iters < 0) return fail(PFM_EINVAL, "n_iters must be >= 0");
+    const int parity = b->probs[0]->cur;
+    int left = n_iters;
+    if (left >= kGraphIters) {
+        if (!b->graph[parity]) {
+            cudaGraph_t g = nullptr;
+            PFM_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal), "graph capture");
+            cudaError_t e = cudaSuccess;
+            for (int i = 0; i < kGraphIters && e == cudaSuccess; ++i) e = b->runner->launch((parity + i) & 1, b->grid, b->stream);
+            cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+            if (e != cudaSuccess) return cuda_fail(e, "graph capture");
+            if (e2 != cudaSuccess) return cuda_fail(e2, "graph capture");
+            e = cudaGraphInstantiate(&b->graph[parity], g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");
+        }
+        while (left >= kGraphIters) {
+            PFM_CUDA(cudaGraphLaunch(b->graph[parity], b->stream), "graph launch");
+            b->launches += kGraphIters;
+            left -= kGraphIters;
+        }
+    }
+    pfm_status st = batch_launch_direct(b, parity, left);
+    if (st != PFM_OK) return st;
+    for (pfm_problem* pb : b->probs) {
+        pb->cur = (parity + n_iters) & 1;
+        pb->iters += n_iters;
+    }
+    return PFM_OK;
+}
+
+pfm_status pfm_batch_energy(pfm_batch* b, double* primal, double* dual) {
+    if (!b || !primal || !dual) return fail(PFM_EINVAL, "NULL argument");
+    pfm_status first = PFM_OK;
+    for (size_t k = 0; k < b->probs.size(); ++k) {
+        pfm_status st = pfm_energy(b->probs[k], &primal[k], &dual[k]);
+        if (st != PFM_OK && first == PFM_OK) first = st;
+    }
+    return first;
+}
+
+pfm_status pfm_batch_tune(pfm_batch* b, int trial_iters, int* zc_out, int* grid_out) {
+    if (!b) return fail(PFM_EINVAL, "NULL batch");
+    if (trial_iters < 1) return fail(PFM_EINVAL, "trial_iters must be >= 1");
+    cudaEvent_t e0, e1;
+    PFM_CUDA(cudaEventCreate(&e0), "event");
+    PFM_CUDA(cudaEventCreate(&e1), "event");
+    float best = 3.0e38f;
+    int best_zc = b->zc, best_grid = b->grid;
+    const int zcs[] = {8, 16, 32, 64};
+    pfm_status st = PFM_OK;
+    for (int zc : zcs) {
+        if ((st = batch_setup(b, zc, 0)) != PFM_OK) break;
+        const int resident = b->grid;
+        const int grids[] = {resident, std::min(2 * resident, b->runner->n_items()), b->runner->n_items()};
+        for (int gi = 0; gi < 3; ++gi) {
+            if (gi > 0 && grids[gi] == grids[gi - 1]) continue;
+            b->grid = grids[gi];
+            const int parity = b->probs[0]->cur;
+            if ((st = batch_launch_direct(b, parity, 1)) != PFM_OK) break;  // warm-up
+            cudaEventRecord(e0, b->stream);
+            if ((st = batch_launch_direct(b, parity + 1, trial_iters)) != PFM_OK) break;
+            cudaEventRecord(e1, b->stream);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) {
+                best = ms;
+                best_zc = zc;
+                best_grid = grids[gi];
+            }
+        }
+        if (st != PFM_OK) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != PFM_OK) return st;
+    // the trials advanced the members: start again from the initial state
+    for (pfm_problem* pb : b->probs) {
+        if ((st = pfm_reset(pb)) != PFM_OK) return st;
+    }
+    if ((st = batch_setup(b, best_zc, best_grid)) != PFM_OK) return st;
+    PFM_CUDA(cudaStreamSynchronize(b->stream), "stream sync");
+    if (zc_out) *zc_out = b->zc;
+    if (grid_out) *grid_out = b->grid;
+    return PFM_OK;
+}
+
+int64_t pfm_batch_launch_count(const pfm_batch* b) { return b ? b->launches : -1; }
 
 }  // extern "C"

@@ -11,4 +11,12 @@ SolverBase* make_dag_f32(int maxl, int maxn, int dim, const ProblemView& v) {
     return nullptr;
 }
 
+BatchBase* make_batch_dag_f32(int maxl, int maxn, int dim) {
+#define PFM_BDAG(L, N, DM) \
+    if (maxl == L && maxn == N && dim == DM) return new BatchRunner<L, N, DM, true, float>();
+    PFM_BDAG(8, 12, 2) PFM_BDAG(8, 12, 3) PFM_BDAG(16, 16, 2) PFM_BDAG(16, 16, 3)
+#undef PFM_BDAG
+    return nullptr;
+}
+
 }  // namespace pfm

@@ -148,18 +148,18 @@ __device__ __forceinline__ bool label_prox(const StepArgs<MAXL, MAXN>& a, const 
 // chunk: label prox of plane p on the halo-extended tile (results to shared
 // memory), then the flow step of plane p-1, whose z-gradient needs plane p.
 // ---------------------------------------------------------------------------
+// One tile (bx, by) of z-chunk bz; sg = [3][MAXL][FNE] shared floats (the
+// field g of three planes).  Every thread of the CTA must call it.
 template <int MAXL, int MAXN, int DIM, bool IS_DAG, typename T>
-__global__ void __launch_bounds__(FUSED_NT, 1)
-fused_step_kernel(const StepArgs<MAXL, MAXN> a) {
-    extern __shared__ float sg[];  // [3][MAXL][FNE]: field g of three planes
+__device__ __forceinline__ void fused_tile(const StepArgs<MAXL, MAXN>& a, int bx, int by, int bz, float* sg) {
     const int t = threadIdx.x;
     const bool inE = t < FNE;
     const int ex = t % FEX, ey = t / FEX;
-    const int x = blockIdx.x * FTX + ex;
-    const int y = blockIdx.y * FTY + ey;
+    const int x = bx * FTX + ex;
+    const int y = by * FTY + ey;
     const bool valid = inE && x < a.nx && y < a.ny;
     const bool owner = valid && ex < FTX && ey < FTY;
-    const int z0 = blockIdx.z * a.zc;
+    const int z0 = bz * a.zc;
     const int z1 = min(z0 + a.zc, a.nz);
     const long long n = a.n;
     const long long plane = (long long)a.nx * a.ny;
@@ -291,6 +291,44 @@ fused_step_kernel(const StepArgs<MAXL, MAXN> a) {
         for (int j = 0; j < MAXL; ++j) gprev[j] = gcur[j];
     }
     if (bad) atomicOr(a.flags, FLAG_NONFINITE);
+}
+
+template <int MAXL, int MAXN, int DIM, bool IS_DAG, typename T>
+__global__ void __launch_bounds__(FUSED_NT, 1)
+fused_step_kernel(const StepArgs<MAXL, MAXN> a) {
+    extern __shared__ float sg[];
+    fused_tile<MAXL, MAXN, DIM, IS_DAG, T>(a, blockIdx.x, blockIdx.y, blockIdx.z, sg);
+}
+
+// ---------------------------------------------------------------------------
+// Batched iteration: one persistent launch advances many independent
+// volumes (each with its own grid, label DAG and buffers) by one iteration.
+// items[k] = (volume, x tile, y tile, z chunk); CTAs take items round-robin
+// and stage the volume's arguments in shared memory.  vols[] holds the
+// arguments of this launch's parity (inputs / outputs already swapped).
+// ---------------------------------------------------------------------------
+template <int MAXL, int MAXN>
+constexpr size_t batch_smem_bytes() {
+    return (sizeof(float) * 3 * MAXL * FNE + 15) / 16 * 16 + sizeof(StepArgs<MAXL, MAXN>);
+}
+
+template <int MAXL, int MAXN, int DIM, bool IS_DAG, typename T>
+__global__ void __launch_bounds__(FUSED_NT, 1)
+batched_step_kernel(const StepArgs<MAXL, MAXN>* __restrict__ vols, const int4* __restrict__ items, int n_items) {
+    extern __shared__ float sg[];
+    using Args = StepArgs<MAXL, MAXN>;
+    Args* sa = reinterpret_cast<Args*>(reinterpret_cast<unsigned char*>(sg) +
+                                       (sizeof(float) * 3 * MAXL * FNE + 15) / 16 * 16);
+    static_assert(sizeof(Args) % 4 == 0, "argument block copied as words");
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+        const int4 w = items[it];
+        __syncthreads();  // the previous item is done with sa and sg
+        const int* src = reinterpret_cast<const int*>(vols + w.x);
+        int* dst = reinterpret_cast<int*>(sa);
+        for (int k = threadIdx.x; k < (int)(sizeof(Args) / 4); k += blockDim.x) dst[k] = src[k];
+        __syncthreads();
+        fused_tile<MAXL, MAXN, DIM, IS_DAG, T>(*sa, w.y, w.z, w.w, sg);
+    }
 }
 
 // ---------------------------------------------------------------------------

@@ -11,4 +11,12 @@ SolverBase* make_potts_bf16(int maxl, int dim, const ProblemView& v) {
     return nullptr;
 }
 
+BatchBase* make_batch_potts_bf16(int maxl, int dim) {
+#define PFM_BPOTTS(L, DM) \
+    if (maxl == L && dim == DM) return new BatchRunner<L, L, DM, false, __nv_bfloat16>();
+    PFM_BPOTTS(4, 2) PFM_BPOTTS(4, 3) PFM_BPOTTS(8, 2) PFM_BPOTTS(8, 3) PFM_BPOTTS(16, 2) PFM_BPOTTS(16, 3)
+#undef PFM_BPOTTS
+    return nullptr;
+}
+
 }  // namespace pfm

@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <vector>
 
 #include "pfm_device.cuh"
 #include "pfm_tma.cuh"
@@ -227,11 +228,125 @@ struct Solver final : SolverBase {
     }
 };
 
+// ---------------------------------------------------------------------------
+// Batched iteration over many volumes (pfm_batch_*).
+// ---------------------------------------------------------------------------
+struct BatchMember {
+    ProblemView view;
+    void* u[2];
+    void* q[2];
+};
+
+struct BatchBase {
+    virtual ~BatchBase() {}
+    // Builds the argument table (both parities) and the work list for chunk length zc.
+    virtual cudaError_t setup(const BatchMember* m, int n, int zc) = 0;
+    // One iteration of every member: inputs are buffer `parity`, outputs 1 - parity.
+    virtual cudaError_t launch(int parity, int grid, cudaStream_t s) = 0;
+    virtual int n_items() const = 0;
+    // Resident CTAs per SM of the batched kernel (occupancy).
+    virtual int ctas_per_sm() const = 0;
+};
+
+template <int MAXL, int MAXN, int DIM, bool IS_DAG, typename T>
+struct BatchRunner final : BatchBase {
+    using Args = StepArgs<MAXL, MAXN>;
+    Args* dev = nullptr;   // [2][nvol]
+    int4* items = nullptr;
+    int nvol = 0, nitems = 0;
+    size_t smem = batch_smem_bytes<MAXL, MAXN>();
+
+    ~BatchRunner() override {
+        if (dev) cudaFree(dev);
+        if (items) cudaFree(items);
+    }
+
+    static Args make_args(const ProblemView& v, int zc) {
+        Args a{};
+        a.D = v.D;
+        a.S = v.S;
+        a.abuf = v.abuf;
+        a.flags = v.flags;
+        a.nx = v.nx;
+        a.ny = v.ny;
+        a.nz = v.nz;
+        a.nl = v.nl;
+        a.nn = v.nn;
+        a.n = v.n;
+        a.literal = v.literal;
+        a.aniso = v.aniso;
+        a.inv_c = 1.0f / v.c;
+        a.ctau = v.c * v.tau;
+        a.zc = zc;
+        for (int A = 0; A < MAXN; ++A) a.s_node[A] = A < v.nn ? v.s_node[A] : 0.f;
+        for (int A = 0; A < MAXN; ++A)
+            for (int j = 0; j < MAXL; ++j) a.W[A][j] = (IS_DAG && A < v.nn && j < v.nl) ? v.W[A * v.nl + j] : 0.f;
+        return a;
+    }
+
+    cudaError_t setup(const BatchMember* m, int n, int zc) override {
+        if (dev) cudaFree(dev);
+        if (items) cudaFree(items);
+        dev = nullptr;
+        items = nullptr;
+        nvol = n;
+        std::vector<Args> host(2 * (size_t)n);
+        std::vector<int4> work;
+        for (int k = 0; k < n; ++k) {
+            for (int p = 0; p < 2; ++p) {
+                Args a = make_args(m[k].view, zc);
+                a.u_in = m[k].u[p];
+                a.u_out = m[k].u[1 - p];
+                a.q_in = m[k].q[p];
+                a.q_out = m[k].q[1 - p];
+                host[(size_t)p * n + k] = a;
+            }
+            const ProblemView& v = m[k].view;
+            // x tiles fastest, so the CTAs that run together are neighbours
+            for (int bz = 0; bz < (v.nz + zc - 1) / zc; ++bz)
+                for (int by = 0; by < (v.ny + FTY - 1) / FTY; ++by)
+                    for (int bx = 0; bx < (v.nx + FTX - 1) / FTX; ++bx) work.push_back(make_int4(k, bx, by, bz));
+        }
+        nitems = (int)work.size();
+        cudaError_t e = cudaMalloc(&dev, sizeof(Args) * host.size());
+        if (e != cudaSuccess) return e;
+        e = cudaMalloc(&items, sizeof(int4) * work.size());
+        if (e != cudaSuccess) return e;
+        e = cudaMemcpy(dev, host.data(), sizeof(Args) * host.size(), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return e;
+        e = cudaMemcpy(items, work.data(), sizeof(int4) * work.size(), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return e;
+        return cudaFuncSetAttribute(batched_step_kernel<MAXL, MAXN, DIM, IS_DAG, T>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    }
+
+    cudaError_t launch(int parity, int grid, cudaStream_t s) override {
+        batched_step_kernel<MAXL, MAXN, DIM, IS_DAG, T>
+            <<<grid, FUSED_NT, smem, s>>>(dev + (size_t)parity * nvol, items, nitems);
+        return cudaGetLastError();
+    }
+
+    int n_items() const override { return nitems; }
+
+    int ctas_per_sm() const override {
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, batched_step_kernel<MAXL, MAXN, DIM, IS_DAG, T>,
+                                                          FUSED_NT, smem) != cudaSuccess)
+            b = 1;
+        cudaGetLastError();
+        return b < 1 ? 1 : b;
+    }
+};
+
 // Factories, one per translation unit (storage x model).
 SolverBase* make_potts_f32(int maxl, int dim, const ProblemView& v);
 SolverBase* make_potts_bf16(int maxl, int dim, const ProblemView& v);
 SolverBase* make_dag_f32(int maxl, int maxn, int dim, const ProblemView& v);
 SolverBase* make_dag_bf16(int maxl, int maxn, int dim, const ProblemView& v);
+BatchBase* make_batch_potts_f32(int maxl, int dim);
+BatchBase* make_batch_potts_bf16(int maxl, int dim);
+BatchBase* make_batch_dag_f32(int maxl, int maxn, int dim);
+BatchBase* make_batch_dag_bf16(int maxl, int maxn, int dim);
 
 // Auxiliary kernels (pfm_misc.cu).
 cudaError_t launch_init_labels(void* u, int storage, int nl, long long n, cudaStream_t s);
