@@ -219,7 +219,8 @@ def run_batched(args, rank, world):
     import synth
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     vols = synth.dagmf_batch(seed=4000 + 100 * rank, count=32)
-    stream = torch.cuda.current_stream()
+    stream = torch.cuda.Stream()  # a capturable (non-default) stream shared with the events
+    torch.cuda.set_stream(stream)
     probs = [dict(D=torch.from_numpy(p.D).cuda(), S_field=torch.from_numpy(p.S_field).cuda(), s_node=p.s_node,
                   n_nodes=p.n_nodes, edges=p.edges) for p in vols]
     b = pfm.Batch(probs, c=0.5, tau=0.11, stream=stream.cuda_stream)

@@ -213,6 +213,22 @@ PFM_API const char* pfm_kernel_variant(const pfm_problem* pb);
 PFM_API int64_t pfm_iterations_done(const pfm_problem* pb);
 PFM_API int64_t pfm_launch_count(const pfm_problem* pb);
 
+/* Reverse-mode step of one Potts iteration (the paper has no gradient; this differentiates the unrolled iteration of
+ * Algorithm 1, NORMALISED gradient source, ISO or ANISO, flat label set).
+ * Given the forward input state (u_k, q_k) of an iteration, its output
+ * labelling u_k1, and the adjoints (ubar_k1, qbar_k1) of its outputs
+ * (u_k1, q_k1), writes the adjoints (ubar_k, qbar_k) of its inputs and
+ * ADDS this iteration's contribution to Dbar (gradient w.r.t. D) and Sbar
+ * (gradient w.r.t. S_field; ignored if the problem has no field).  All
+ * buffers are caller-owned FP32 device memory in the getters' layouts;
+ * ubar_k may alias ubar_k1 and qbar_k may alias qbar_k1.  work: device
+ * scratch of (ndim + 1) * n_leaf * n floats.  D, S, c, tau, the capacities
+ * and the norm are the problem's.  Asynchronous on the problem's stream.
+ * PFM_EUNSUPPORTED for DAG problems, PAPER_LITERAL or more than 16 labels. */
+PFM_API pfm_status pfm_adjoint_step(pfm_problem* pb, const float* u_k, const float* q_k, const float* u_k1,
+                                    const float* ubar_k1, const float* qbar_k1, float* ubar_k, float* qbar_k,
+                                    float* Dbar, float* Sbar, float* work);
+
 /* ---- Batches (many independent problems, one persistent kernel per
  * iteration) ----
  * A batch advances n problems of possibly different grid sizes and label

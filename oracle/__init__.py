@@ -46,7 +46,7 @@ def lib():
     if _lib is None:
         _lib = C.CDLL(_build_mod.build())
         for name in ("orc_potts_iterate", "orc_potts_energy", "orc_potts_init", "orc_grad", "orc_div",
-                     "orc_alm_potts_init", "orc_alm_potts_iterate"):
+                     "orc_alm_potts_init", "orc_alm_potts_iterate", "orc_ishikawa_init", "orc_ishikawa_iterate"):
             getattr(_lib, name).restype = None
         for name in ("orc_dag_iterate", "orc_dag_energy", "orc_dag_init", "orc_dag_n_leaves",
                      "orc_dag_path_weights", "orc_bruteforce_binary"):
@@ -203,6 +203,25 @@ def dag_energy(dag, D, u, q, S_field=None, s_node=None, norm=ISO):
     if r != 0:
         raise ValueError("malformed DAG")
     return E.value, P.value
+
+
+def ishikawa_init(spatial, nlev):
+    """Algorithm 3, first line: u = 1/(N+1) over the N+1 labels; N flow fields = 0."""
+    g = _grid(spatial)
+    u = np.empty((nlev + 1,) + tuple(spatial))
+    q = np.empty((nlev, g.ndim) + tuple(spatial))
+    lib().orc_ishikawa_init(C.byref(g), C.c_int(nlev), _p(u), _p(q))
+    return u, q
+
+
+def ishikawa_iterate(D, u, q, iters, c, tau, S_field=None, s_level=None, norm=ISO, grad_source=NORMALISED):
+    """Algorithm 3 loop body, ``iters`` times, in place on (u, q); D is [N+1, *spatial]."""
+    D = _f64(D)
+    g = _grid(D.shape[1:])
+    prm = _params(c, tau, norm, grad_source)
+    lib().orc_ishikawa_iterate(C.byref(g), C.c_int(D.shape[0] - 1), _p(D), _p(_f64(S_field)), _p(_f64(s_level)),
+                               C.byref(prm), C.c_int(iters), _p(u), _p(q))
+    return u, q
 
 
 def alm_potts(D, iters, gamma, step, S_field=None, s_node=None, norm=ISO, state=None):

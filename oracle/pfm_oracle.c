@@ -462,6 +462,58 @@ int orc_dag_energy(const orc_grid* g, const orc_dag* dag, const double* D,
 }
 
 /* ---------------------------------------------------------------------------
+ * Algorithm 3: pseudo-flow continuous Ishikawa model.  nlev = N levels,
+ * N+1 labels.  The excess of label L_i accumulates the divergences of the
+ * flows of levels 1..i (top-down), the labelling is normalised over all
+ * N+1 labels, and the flow of level i is driven by the sum of the labels
+ * L_i..L_N (bottom-up accumulation).
+ * ------------------------------------------------------------------------- */
+void orc_ishikawa_init(const orc_grid* g, int nlev, double* u, double* q) {
+    const long n = orc_nvox(g);
+    for (long i = 0; i < (long)(nlev + 1) * n; ++i) u[i] = 1.0 / (nlev + 1);
+    memset(q, 0, sizeof(double) * (size_t)nlev * g->ndim * n);
+}
+
+void orc_ishikawa_iterate(const orc_grid* g, int nlev, const double* D,
+                          const double* S_field, const double* s_level,
+                          const orc_params* p, int iters, double* u, double* q) {
+    const long n = orc_nvox(g);
+    const int nd = g->ndim, nlab = nlev + 1;
+    double* d = (double*)malloc(sizeof(double) * (size_t)nlab * n);
+    double* dv = (double*)malloc(sizeof(double) * n);
+    double* gb = (double*)malloc(sizeof(double) * nd * n);
+    for (int it = 0; it < iters; ++it) {
+        /* d_{L_0} = 0; d_{L_i} = d_{L_{i-1}} + div q_{L_i} for i = 1..N */
+        for (long x = 0; x < n; ++x) d[x] = 0.0;
+        for (int i = 1; i <= nlev; ++i) {
+            orc_div(g, q + (long)(i - 1) * nd * n, dv);
+            for (long x = 0; x < n; ++x) d[(long)i * n + x] = d[(long)(i - 1) * n + x] + dv[x];
+        }
+        /* d_{L_i} += D_{L_i} for every label */
+        for (long k = 0; k < (long)nlab * n; ++k) d[k] += D[k];
+        /* u_{L_i} <- u_{L_i} exp(-d_{L_i}/c) */
+        for (long k = 0; k < (long)nlab * n; ++k) u[k] *= exp(-d[k] / p->c);
+        if (p->grad_source == ORC_PAPER_LITERAL) {
+            memcpy(d, u, sizeof(double) * (size_t)nlab * n); /* d <- u before normalising */
+            potts_normalise(n, nlab, u);
+        } else {
+            potts_normalise(n, nlab, u);
+            memcpy(d, u, sizeof(double) * (size_t)nlab * n);
+        }
+        /* d_{L_i} += d_{L_{i+1}} for i = N-1 .. 1 */
+        for (int i = nlev - 1; i >= 1; --i)
+            for (long x = 0; x < n; ++x) d[(long)i * n + x] += d[(long)(i + 1) * n + x];
+        /* q_{L_i} <- Proj(q_{L_i} - c tau grad d_{L_i}) for i = 1..N */
+        for (int i = 1; i <= nlev; ++i)
+            flow_step(g, p->norm, p->c * p->tau, d + (long)i * n, S_field, s_level, i - 1,
+                      q + (long)(i - 1) * nd * n, gb);
+    }
+    free(d);
+    free(dv);
+    free(gb);
+}
+
+/* ---------------------------------------------------------------------------
  * Explicit-flow augmented Lagrangian continuous max-flow (Potts).
  *
  * Primal Eq. potts_primal: maximise sum_x p_S s.t. p_L <= D_L, |q_L| <= S_L,

@@ -92,6 +92,14 @@ int orc_dag_energy(const orc_grid* g, const orc_dag* dag, const double* D,
                    const double* u, const double* q,
                    double* primal, double* dual);
 
+/* Algorithm 3 (continuous Ishikawa model): N+1 ordered labels L_0..L_N,
+ * N flow fields q_{L_1}..q_{L_N} with per-level capacities s_level[i-1]
+ * (times S_field), u: [N+1][n], q: [N][ndim][n], D: [N+1][n]. */
+void orc_ishikawa_init(const orc_grid* g, int nlev, double* u, double* q);
+void orc_ishikawa_iterate(const orc_grid* g, int nlev, const double* D,
+                          const double* S_field, const double* s_level,
+                          const orc_params* p, int iters, double* u, double* q);
+
 /* Explicit-flow ("full-flow") augmented-Lagrangian continuous max-flow for
  * the Potts model (primal Eq. potts_primal, multipliers u of
  * Eq. potts_primaldual).  Independent algorithm used to pin the optimum.

@@ -67,6 +67,7 @@ _SIGS = {
     "pfm_kernel_variant": (C.c_char_p, [_P]),
     "pfm_iterations_done": (C.c_int64, [_P]),
     "pfm_launch_count": (C.c_int64, [_P]),
+    "pfm_adjoint_step": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "pfm_batch_create": (C.c_int, [C.c_int, C.c_void_p, C.POINTER(pfm_params), _P, C.POINTER(_P)]),
     "pfm_batch_destroy": (None, [_P]),
     "pfm_batch_size": (C.c_int, [_P]),
@@ -300,6 +301,11 @@ class Problem:
     def set_labels(self, u):
         u = _as_f32(u)
         check(lib().pfm_set_labels(self._h, _ptr(u)))
+
+    def adjoint_step(self, u_k, q_k, u_k1, ubar_k1, qbar_k1, ubar_k, qbar_k, Dbar, Sbar, work):
+        """pfm_adjoint_step on FP32 CUDA tensors (see pfm.h)."""
+        check(lib().pfm_adjoint_step(self._h, _ptr(u_k), _ptr(q_k), _ptr(u_k1), _ptr(ubar_k1), _ptr(qbar_k1),
+                                     _ptr(ubar_k), _ptr(qbar_k), _ptr(Dbar), _ptr(Sbar), _ptr(work)))
 
     def set_flows(self, q):
         q = _as_f32(q)

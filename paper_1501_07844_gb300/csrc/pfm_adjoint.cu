@@ -1,0 +1,174 @@
+// pfm_adjoint.cu -- reverse-mode (adjoint) step of one Potts iteration.
+//
+// Forward iteration k (NORMALISED gradient source), per voxel and label j:
+//   d_j  = D_j + div q_j                       (q = q^k)
+//   u'_j = u_j e_j / a,  e_j = exp(-(d_j - m)/c),  a = sum_l u_l e_l   (u = u^k)
+//   y_j  = q_j - c tau grad u'_j
+//   q'_j = Proj_{|.| <= s_j S}(y_j)
+// Given the adjoints (ubar', qbar') of (u^{k+1}, q^{k+1}), three kernels
+// produce (ubar, qbar) of (u^k, q^k) and accumulate Dbar and Sbar:
+//   K1 (projection):  ybar_j = J_proj^T qbar'_j,  Sbar += sum_j s_j * dProj/ds . qbar'_j
+//   K2 (label prox):  ubar'_j += c tau div ybar_j            (adjoint of -c tau grad)
+//                     zbar_j = u'_j (ubar'_j - <u', ubar'>)   (softmax Jacobian)
+//                     ubar_j = (e_j / a) (ubar'_j - <u', ubar'>),  dbar_j = -zbar_j / c
+//                     Dbar_j += dbar_j
+//   K3 (divergence):  qbar_j = ybar_j - grad dbar_j           (adjoint of div is -grad)
+// Projection Jacobian (ISO): identity inside the ball; outside,
+// (s/|y|)(I - yhat yhat^T) with d/ds = yhat.  ANISO: per component, identity
+// inside the box, zero outside with d/ds = sign(y).
+#include <cuda_runtime.h>
+
+#include "../../include/pfm.h"
+#include "pfm_solver.cuh"
+
+namespace pfm {
+pfm_status set_error(pfm_status st, const char* msg);
+
+namespace {
+
+constexpr int NT = 256;
+
+using AdjArgs = AdjLaunch;
+
+__device__ __forceinline__ void coords(long long i, int nx, int ny, int& x, int& y, int& z) {
+    x = (int)(i % nx);
+    const long long r = i / nx;
+    y = (int)(r % ny);
+    z = (int)(r / ny);
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(NT) adj_proj_kernel(const AdjArgs a) {
+    const long long i = (long long)blockIdx.x * NT + threadIdx.x;
+    if (i >= a.n) return;
+    int x, y, z;
+    coords(i, a.nx, a.ny, x, y, z);
+    const long long n = a.n, plane = (long long)a.nx * a.ny;
+    const float sf = a.S ? a.S[i] : 1.0f;
+    float sbar = 0.f;
+    for (int j = 0; j < a.nl; ++j) {
+        const float* u1 = a.u_k1 + (long long)j * n + i;
+        const float g0 = *u1;
+        float gr[DIM];
+        gr[0] = x < a.nx - 1 ? u1[1] - g0 : 0.f;
+        gr[1] = y < a.ny - 1 ? u1[a.nx] - g0 : 0.f;
+        if constexpr (DIM == 3) gr[2] = z < a.nz - 1 ? u1[plane] - g0 : 0.f;
+        float yv[DIM], qb[DIM], yb[DIM];
+        for (int k = 0; k < DIM; ++k) {
+            yv[k] = a.q_k[((long long)j * DIM + k) * n + i] - a.ctau * gr[k];
+            qb[k] = a.qbar_k1[((long long)j * DIM + k) * n + i];
+        }
+        const float s = a.s_node[j] * sf;
+        float ds = 0.f;  // d q' / d s . qbar'
+        if (a.aniso) {
+            for (int k = 0; k < DIM; ++k) {
+                if (yv[k] > s) {
+                    yb[k] = 0.f;
+                    ds += qb[k];
+                } else if (yv[k] < -s) {
+                    yb[k] = 0.f;
+                    ds -= qb[k];
+                } else {
+                    yb[k] = qb[k];
+                }
+            }
+        } else {
+            float r2 = 0.f;
+            for (int k = 0; k < DIM; ++k) r2 += yv[k] * yv[k];
+            if (r2 > s * s && r2 > 0.f) {
+                const float r = sqrtf(r2);
+                float yq = 0.f;
+                for (int k = 0; k < DIM; ++k) yq += yv[k] * qb[k];
+                yq /= r;  // yhat . qbar'
+                for (int k = 0; k < DIM; ++k) yb[k] = (s / r) * (qb[k] - (yv[k] / r) * yq);
+                ds = yq;
+            } else {
+                for (int k = 0; k < DIM; ++k) yb[k] = qb[k];
+            }
+        }
+        for (int k = 0; k < DIM; ++k) a.ybar[((long long)j * DIM + k) * n + i] = yb[k];
+        sbar += a.s_node[j] * ds;
+    }
+    if (a.Sbar) a.Sbar[i] += sbar;
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(NT) adj_prox_kernel(const AdjArgs a) {
+    const long long i = (long long)blockIdx.x * NT + threadIdx.x;
+    if (i >= a.n) return;
+    int x, y, z;
+    coords(i, a.nx, a.ny, x, y, z);
+    const long long n = a.n, plane = (long long)a.nx * a.ny;
+    float d[16], ub[16], u1[16];
+    float m = 3.0e38f;
+    float dot = 0.f;
+    for (int j = 0; j < a.nl; ++j) {
+        // d_j = D_j + div q_j  (forward recomputation)
+        const float* qa = a.q_k + (long long)j * DIM * n + i;
+        float dv = (x < a.nx - 1 ? qa[0] : 0.f) - (x > 0 ? qa[-1] : 0.f);
+        dv += (y < a.ny - 1 ? qa[n] : 0.f) - (y > 0 ? qa[n - a.nx] : 0.f);
+        if constexpr (DIM == 3) dv += (z < a.nz - 1 ? qa[2 * n] : 0.f) - (z > 0 ? qa[2 * n - plane] : 0.f);
+        d[j] = a.D[(long long)j * n + i] + dv;
+        m = fminf(m, d[j]);
+        // ubar'_j + c tau div ybar_j
+        const float* yb = a.ybar + (long long)j * DIM * n + i;
+        float dy = (x < a.nx - 1 ? yb[0] : 0.f) - (x > 0 ? yb[-1] : 0.f);
+        dy += (y < a.ny - 1 ? yb[n] : 0.f) - (y > 0 ? yb[n - a.nx] : 0.f);
+        if constexpr (DIM == 3) dy += (z < a.nz - 1 ? yb[2 * n] : 0.f) - (z > 0 ? yb[2 * n - plane] : 0.f);
+        ub[j] = a.ubar_k1[(long long)j * n + i] + a.ctau * dy;
+        u1[j] = a.u_k1[(long long)j * n + i];
+        dot += u1[j] * ub[j];
+    }
+    float asum = 0.f;
+    for (int j = 0; j < a.nl; ++j) {
+        d[j] = __expf(-(d[j] - m) / a.c);  // e_j (shifted)
+        asum += a.u_k[(long long)j * n + i] * d[j];
+    }
+    const float inv_a = 1.0f / asum;
+    for (int j = 0; j < a.nl; ++j) {
+        const float w = ub[j] - dot;
+        a.ubar_k[(long long)j * n + i] = d[j] * inv_a * w;
+        const float dbar = -u1[j] * w / a.c;
+        a.dbar[(long long)j * n + i] = dbar;
+        a.Dbar[(long long)j * n + i] += dbar;
+    }
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(NT) adj_div_kernel(const AdjArgs a) {
+    const long long i = (long long)blockIdx.x * NT + threadIdx.x;
+    if (i >= a.n) return;
+    int x, y, z;
+    coords(i, a.nx, a.ny, x, y, z);
+    const long long n = a.n, plane = (long long)a.nx * a.ny;
+    for (int j = 0; j < a.nl; ++j) {
+        const float* db = a.dbar + (long long)j * n + i;
+        const float d0 = *db;
+        float gr[DIM];
+        gr[0] = x < a.nx - 1 ? db[1] - d0 : 0.f;
+        gr[1] = y < a.ny - 1 ? db[a.nx] - d0 : 0.f;
+        if constexpr (DIM == 3) gr[2] = z < a.nz - 1 ? db[plane] - d0 : 0.f;
+        for (int k = 0; k < DIM; ++k) {
+            const long long o = ((long long)j * DIM + k) * n + i;
+            a.qbar_k[o] = a.ybar[o] - gr[k];
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_adjoint(const AdjArgs& a, int ndim, cudaStream_t s) {
+    const unsigned b = (unsigned)((a.n + NT - 1) / NT);
+    if (ndim == 3) {
+        adj_proj_kernel<3><<<b, NT, 0, s>>>(a);
+        adj_prox_kernel<3><<<b, NT, 0, s>>>(a);
+        adj_div_kernel<3><<<b, NT, 0, s>>>(a);
+    } else {
+        adj_proj_kernel<2><<<b, NT, 0, s>>>(a);
+        adj_prox_kernel<2><<<b, NT, 0, s>>>(a);
+        adj_div_kernel<2><<<b, NT, 0, s>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace pfm

@@ -696,6 +696,44 @@ const char* pfm_kernel_variant(const pfm_problem* pb) {
     return pb->solver->variant(pb->prm.schedule != PFM_SCHEDULE_INPLACE);
 }
 
+pfm_status pfm_adjoint_step(pfm_problem* pb, const float* u_k, const float* q_k, const float* u_k1,
+                            const float* ubar_k1, const float* qbar_k1, float* ubar_k, float* qbar_k, float* Dbar,
+                            float* Sbar, float* work) {
+    if (!pb) return fail(PFM_EINVAL, "NULL problem");
+    if (!u_k || !q_k || !u_k1 || !ubar_k1 || !qbar_k1 || !ubar_k || !qbar_k || !Dbar || !work)
+        return fail(PFM_EINVAL, "NULL buffer");
+    if (!pb->flat) return fail(PFM_EUNSUPPORTED, "the adjoint covers the Potts model (flat label set)");
+    if (pb->nl > 16) return fail(PFM_EUNSUPPORTED, "the adjoint supports at most 16 labels");
+    if (pb->prm.grad_source != PFM_GRAD_NORMALISED)
+        return fail(PFM_EUNSUPPORTED, "the adjoint differentiates the NORMALISED iteration");
+    pfm::AdjLaunch L{};
+    L.u_k = u_k;
+    L.q_k = q_k;
+    L.u_k1 = u_k1;
+    L.ubar_k1 = ubar_k1;
+    L.qbar_k1 = qbar_k1;
+    L.ubar_k = ubar_k;
+    L.qbar_k = qbar_k;
+    L.Dbar = Dbar;
+    L.Sbar = pb->S ? Sbar : nullptr;
+    L.ybar = work;
+    L.dbar = work + (size_t)pb->nl * pb->ndim * pb->n;
+    L.D = pb->D;
+    L.S = pb->S;
+    L.nx = pb->nx;
+    L.ny = pb->ny;
+    L.nz = pb->nz;
+    L.nl = pb->nl;
+    L.n = pb->n;
+    L.c = (float)pb->prm.c;
+    L.ctau = (float)(pb->prm.c * pb->prm.tau);
+    L.aniso = pb->prm.norm == PFM_NORM_ANISO;
+    for (int j = 0; j < 16; ++j) L.s_node[j] = j < pb->nl ? pb->s_node[j] : 0.f;
+    PFM_CUDA(pfm::launch_adjoint(L, pb->ndim, pb->stream), "adjoint");
+    pb->launches += 3;
+    return PFM_OK;
+}
+
 int64_t pfm_iterations_done(const pfm_problem* pb) { return pb ? pb->iters : -1; }
 int64_t pfm_launch_count(const pfm_problem* pb) { return pb ? pb->launches : -1; }
 

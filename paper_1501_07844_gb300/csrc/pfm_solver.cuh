@@ -348,6 +348,29 @@ BatchBase* make_batch_potts_bf16(int maxl, int dim);
 BatchBase* make_batch_dag_f32(int maxl, int maxn, int dim);
 BatchBase* make_batch_dag_bf16(int maxl, int maxn, int dim);
 
+// Adjoint of one Potts iteration (pfm_adjoint.cu).
+struct AdjLaunch {
+    const float* u_k;      // [nl][n]
+    const float* q_k;      // [nl][dim][n]
+    const float* u_k1;     // [nl][n]
+    const float* ubar_k1;  // [nl][n]
+    const float* qbar_k1;  // [nl][dim][n]
+    float* ubar_k;         // [nl][n]  (may alias ubar_k1)
+    float* qbar_k;         // [nl][dim][n]  (may alias qbar_k1)
+    float* Dbar;           // [nl][n], accumulated
+    float* Sbar;           // [n], accumulated, or nullptr
+    float* ybar;           // work [nl][dim][n]
+    float* dbar;           // work [nl][n]
+    const float* D;
+    const float* S;
+    int nx, ny, nz, nl;
+    long long n;
+    float c, ctau;
+    int aniso;
+    float s_node[16];
+};
+cudaError_t launch_adjoint(const AdjLaunch& a, int ndim, cudaStream_t s);
+
 // Auxiliary kernels (pfm_misc.cu).
 cudaError_t launch_init_labels(void* u, int storage, int nl, long long n, cudaStream_t s);
 cudaError_t launch_argmax(const void* u, int storage, int nl, long long n, int* out, cudaStream_t s);

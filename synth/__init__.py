@@ -11,6 +11,8 @@ from .phantoms import (  # noqa: F401
     diff_problem,
     hmf_problem,
     hmf_tree,
+    ishikawa_chain,
+    ishikawa_problem,
     potts2d_problem,
     potts3d_problem,
     random_dag,

@@ -207,3 +207,35 @@ def random_problem(seed, spatial, nl=3, s_scale=0.3, s_kind="field", c=0.5, tau=
         if s_kind == "node":
             s_node *= s_scale
     return Problem(D, S, s_node, nn, e, c=c, tau=tau, iters=iters, name="random")
+
+
+def ishikawa_chain(nlev):
+    """The Ishikawa model (N levels, N+1 ordered labels) as a label DAG:
+    chain S -> A_1 -> ... -> A_N of inner nodes, label L_0 under S and
+    label L_i under A_i.  Node ids: A_i = i - 1 (i = 1..N), L_i = N + i.
+    The labels carry no flow of their own (capacity 0); A_i's flow is the
+    flow of level i."""
+    N = int(nlev)
+    edges = [(-1, 0, 1.0), (-1, N, 1.0)]
+    for i in range(1, N):
+        edges.append((i - 1, i, 1.0))          # A_i -> A_{i+1}
+    for i in range(1, N + 1):
+        edges.append((i - 1, N + i, 1.0))      # A_i -> L_i
+    return 2 * N + 1, edges
+
+
+def ishikawa_problem(seed, spatial, nlev=4, sigma=0.08, iters=50):
+    """Ordered labels c_i = i/N on a noisy staircase image; per-level
+    capacities U[0.1, 0.4] (leaves 0)."""
+    rng = np.random.default_rng(seed)
+    spatial = tuple(spatial)
+    lab = np.zeros(spatial, dtype=np.int32)
+    coords = np.meshgrid(*[np.arange(s) for s in spatial], indexing="ij")
+    lab = np.minimum((coords[-1] * (nlev + 1)) // spatial[-1], nlev).astype(np.int32)
+    cl = np.arange(nlev + 1) / nlev
+    I = cl[lab] + rng.normal(0.0, sigma, size=spatial)
+    D = np.abs(I[None] - cl.reshape((-1,) + (1,) * len(spatial))).astype(np.float32)
+    nn, edges = ishikawa_chain(nlev)
+    s_node = np.zeros(nn, dtype=np.float32)
+    s_node[:nlev] = rng.uniform(0.1, 0.4, size=nlev)
+    return Problem(D, None, s_node, nn, edges, c=0.5, tau=0.11, iters=iters, truth=lab, name="ishikawa")

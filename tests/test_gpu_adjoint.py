@@ -1,0 +1,153 @@
+"""Adjoint of the unrolled Potts iteration (gradients w.r.t. D and S).
+
+References: (1) autograd through a plain PyTorch FP64 restatement of one
+iteration (the same discretisation, written here independently of the
+CUDA kernels); (2) central finite differences of the FP64 oracle's forward
+run.  Loss: L = -sum_x log u_{t(x)}(x) after K iterations."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def torch_iteration(D, S, u, q, c, tau, s_label, aniso):
+    """One NORMALISED iteration in FP64 torch ops: prox then flow step."""
+    import torch
+    nd = q.shape[1]
+
+    def grad(f):  # forward difference, zero at the last index; f [..., *spatial]
+        outs = []
+        for k in range(nd):
+            ax = f.dim() - 1 - k
+            d = torch.zeros_like(f)
+            n = f.shape[ax]
+            d.narrow(ax, 0, n - 1).copy_(f.narrow(ax, 1, n - 1) - f.narrow(ax, 0, n - 1))
+            outs.append(d)
+        return torch.stack(outs, dim=1)
+
+    def div(g):  # -grad^T, g [L, nd, *spatial]
+        out = torch.zeros_like(g[:, 0])
+        for k in range(nd):
+            f = g[:, k]
+            ax = f.dim() - 1 - k
+            n = f.shape[ax]
+            fz = torch.cat([f.narrow(ax, 0, n - 1), torch.zeros_like(f.narrow(ax, 0, 1))], dim=ax)
+            sh = torch.cat([torch.zeros_like(f.narrow(ax, 0, 1)), f.narrow(ax, 0, n - 1)], dim=ax)
+            out = out + fz - sh
+        return out
+
+    d = D + div(q)
+    z = torch.log(u) - d / c
+    un = torch.softmax(z, dim=0)
+    y = q - c * tau * grad(un)
+    cap = s_label.view(-1, *([1] * (y.dim() - 1))) * S.unsqueeze(0).unsqueeze(0)
+    if aniso:
+        qn = torch.maximum(torch.minimum(y, cap), -cap)
+    else:
+        r = torch.sqrt((y * y).sum(1, keepdim=True))
+        f = torch.where(r > cap, cap / torch.clamp(r, min=1e-300), torch.ones_like(r))
+        qn = y * f
+    return un, qn
+
+
+def reference_grads(prob, iters, s_label, aniso, target):
+    import torch
+    D = torch.tensor(prob.D, dtype=torch.float64, requires_grad=True)
+    S = torch.tensor(prob.S_field, dtype=torch.float64, requires_grad=True)
+    nl = D.shape[0]
+    u = torch.full(D.shape, 1.0 / nl, dtype=torch.float64)
+    q = torch.zeros((nl, D.dim() - 1) + tuple(D.shape[1:]), dtype=torch.float64)
+    sl = torch.tensor(s_label, dtype=torch.float64)
+    for _ in range(iters):
+        u, q = torch_iteration(D, S, u, q, prob.c, prob.tau, sl, aniso)
+    L = -torch.log(torch.gather(u, 0, torch.tensor(target).unsqueeze(0).long())).sum()
+    L.backward()
+    return D.grad.numpy(), S.grad.numpy(), float(L)
+
+
+def gpu_grads(prob, iters, s_label, aniso, target, ce):
+    import torch
+    from paper_1501_07844_gb300.autograd import potts_solve
+    D = torch.tensor(prob.D, device="cuda", requires_grad=True)
+    S = torch.tensor(prob.S_field, device="cuda", requires_grad=True)
+    u = potts_solve(D, S, iters=iters, c=prob.c, tau=prob.tau, norm=int(aniso), checkpoint_every=ce, s_label=s_label)
+    tgt = torch.tensor(target, device="cuda").long().unsqueeze(0)
+    L = -torch.log(torch.gather(u.double(), 0, tgt)).sum()
+    L.backward()
+    return D.grad.double().cpu().numpy(), S.grad.double().cpu().numpy(), float(L)
+
+
+def oracle_loss(prob, D, S, iters, s_label, aniso, target):
+    u, q = oracle.potts_init(D.shape[1:], D.shape[0])
+    oracle.potts_iterate(D, u, q, iters, prob.c, prob.tau, S_field=S, s_node=s_label, norm=int(aniso))
+    return float(-np.log(np.take_along_axis(u, target[None], 0)).sum())
+
+
+def relerr(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+@pytest.mark.parametrize("shape,aniso", [((10, 12, 16), False), ((21, 17), True), ((9, 11, 14), True)],
+                         ids=["3d_iso", "2d_aniso", "3d_aniso"])
+def test_adjoint_matches_fp64_autograd(shape, aniso):
+    prob = synth.random_problem(5100, shape, nl=4, s_kind="field", s_scale=0.3)
+    s_label = np.array([1.0, 0.7, 1.3, 0.9], dtype=np.float32)
+    target = np.random.default_rng(5101).integers(0, 4, size=shape)
+    iters = 24
+    gD_ref, gS_ref, L_ref = reference_grads(prob, iters, s_label, aniso, target)
+    gD, gS, L = gpu_grads(prob, iters, s_label, aniso, target, ce=5)
+    assert abs(L - L_ref) <= 1e-5 * abs(L_ref)
+    assert relerr(gD, gD_ref) <= 1e-3, relerr(gD, gD_ref)
+    assert relerr(gS, gS_ref) <= 1e-3, relerr(gS, gS_ref)
+
+
+def test_checkpoint_interval_does_not_change_gradients():
+    prob = synth.random_problem(5200, (8, 10, 12), nl=3, s_kind="field", s_scale=0.3)
+    s_label = np.ones(3, dtype=np.float32)
+    target = np.random.default_rng(5201).integers(0, 3, size=(8, 10, 12))
+    g1 = gpu_grads(prob, 15, s_label, False, target, ce=1)
+    g5 = gpu_grads(prob, 15, s_label, False, target, ce=5)
+    g15 = gpu_grads(prob, 15, s_label, False, target, ce=15)
+    for a, b in ((g1, g5), (g1, g15)):
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def test_adjoint_matches_finite_differences_of_oracle():
+    """Central differences (h = 1e-3) of the FP64 oracle's loss on random
+    entries of D and S, against the GPU adjoint."""
+    prob = synth.random_problem(5300, (7, 9, 11), nl=4, s_kind="field", s_scale=0.3)
+    s_label = np.ones(4, dtype=np.float32)
+    target = np.random.default_rng(5301).integers(0, 4, size=(7, 9, 11))
+    iters = 20
+    gD, gS, _ = gpu_grads(prob, iters, s_label, False, target, ce=5)
+    D0 = prob.D.astype(np.float64)
+    S0 = prob.S_field.astype(np.float64)
+    rng = np.random.default_rng(5302)
+    h = 1e-3
+    checked = 0
+    for _ in range(24):
+        which = rng.integers(0, 2)
+        if which == 0:
+            idx = tuple(int(rng.integers(0, s)) for s in D0.shape)
+            Dp, Dm = D0.copy(), D0.copy()
+            Dp[idx] += h
+            Dm[idx] -= h
+            fd = (oracle_loss(prob, Dp, S0, iters, s_label, False, target) -
+                  oracle_loss(prob, Dm, S0, iters, s_label, False, target)) / (2 * h)
+            g = gD[idx]
+        else:
+            idx = tuple(int(rng.integers(0, s)) for s in S0.shape)
+            if S0[idx] < 2 * h:
+                continue
+            Sp, Sm = S0.copy(), S0.copy()
+            Sp[idx] += h
+            Sm[idx] -= h
+            fd = (oracle_loss(prob, D0, Sp, iters, s_label, False, target) -
+                  oracle_loss(prob, D0, Sm, iters, s_label, False, target)) / (2 * h)
+            g = gS[idx]
+        assert abs(g - fd) <= 1e-2 * abs(fd) + 2e-3, (which, idx, g, fd)
+        checked += 1
+    assert checked >= 16

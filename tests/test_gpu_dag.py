@@ -57,3 +57,21 @@ def test_dag_zero_capacity_closed_form():
     with gpu_problem(prob) as gp:
         gp.iterate(k)
         assert np.abs(gp.labels().cpu().numpy() - ref).max() <= 2e-5
+
+
+@pytest.mark.parametrize("nlev,spatial", [(4, (14, 17, 40)), (7, (33, 64))], ids=["3d_5labels", "2d_8labels"])
+def test_ishikawa_chain_matches_algorithm3(nlev, spatial):
+    """Ishikawa (Alg. 3) runs as the DAG chain with flow-free labels; the GPU
+    result is compared with the oracle's literal Alg. 3."""
+    import oracle
+    prob = synth.ishikawa_problem(5600 + nlev, spatial, nlev=nlev)
+    D = prob.D.astype(np.float64)
+    u3, q3 = oracle.ishikawa_init(prob.spatial, nlev)
+    oracle.ishikawa_iterate(D, u3, q3, 40, prob.c, prob.tau, s_level=prob.s_node[:nlev].astype(np.float64))
+    with gpu_problem(prob) as gp:
+        gp.iterate(40)
+        u = gp.labels().cpu().numpy()
+        q = gp.flows().cpu().numpy()
+    assert np.abs(u - u3).max() <= 1e-3
+    assert np.abs(q[:nlev] - q3).max() <= 1e-3 and np.all(q[nlev:] == 0)
+    assert np.mean(np.argmax(u, 0) == np.argmax(u3, 0)) >= 0.999

@@ -384,3 +384,37 @@ def test_chain_reduction_to_potts(orc):
     E, P = orc.dag_energy(dag, D, u, q, s_node=sn)
     _, _, (E2, P2) = _converge_potts(orc, D, None, np.array([0.3, 0.25, 0.15]), orc.ISO, iters=30000)
     assert abs(E - E2) <= 1e-8 * abs(E2) and (E - P) <= 1e-8 * abs(E)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_algorithm3_equals_algorithm2_on_the_ishikawa_chain(orc, mode):
+    """Section 3.4: Ishikawa is the DAGMF model on a chain (Alg. 3 is Alg. 2
+    specialised): the level flows are the inner-node flows, the labels carry
+    none."""
+    N = 4
+    prob = synth.ishikawa_problem(5400, (6, 7, 9), nlev=N)
+    D = prob.D.astype(np.float64)
+    s_level = prob.s_node[:N].astype(np.float64)
+    u3, q3 = orc.ishikawa_init(prob.spatial, N)
+    orc.ishikawa_iterate(D, u3, q3, 25, 0.5, 0.11, s_level=s_level, grad_source=mode)
+    dag = orc.Dag(prob.n_nodes, prob.edges)
+    u2, q2 = orc.dag_init(prob.spatial, dag)
+    orc.dag_iterate(dag, D, u2, q2, 25, 0.5, 0.11, s_node=prob.s_node.astype(np.float64), grad_source=mode)
+    assert np.abs(u3 - u2).max() <= 1e-12
+    assert np.abs(q3 - q2[:N]).max() <= 1e-12 and np.all(q2[N:] == 0)
+
+
+def test_ishikawa_converges_to_lp_optimum(orc):
+    """Ishikawa energy (Section 1): data on the labels, TV on the cumulative
+    labels u_{A_i} = sum_{j >= i} u_{L_j}; relaxed optimum by LP (ANISO)."""
+    N = 3
+    prob = synth.ishikawa_problem(5500, (5, 6), nlev=N)
+    D = prob.D.astype(np.float64)
+    dag = orc.Dag(prob.n_nodes, prob.edges)
+    s_level = prob.s_node[:N].astype(np.float64)
+    u, q = orc.ishikawa_init(prob.spatial, N)
+    orc.ishikawa_iterate(D, u, q, 30000, 1.0, 0.15, s_level=s_level, norm=orc.ANISO)
+    qd = np.concatenate([q, np.zeros((N + 1,) + q.shape[1:])])
+    E, P = orc.dag_energy(dag, D, u, qd, s_node=prob.s_node.astype(np.float64), norm=orc.ANISO)
+    lp = _lp_optimum(D, dag.path_weights(), dag.leaves(), None, prob.s_node.astype(np.float64))
+    assert abs(E - lp) <= 1e-7 * abs(lp) and abs(P - lp) <= 1e-7 * abs(lp)
