@@ -71,7 +71,8 @@ template <> __device__ __forceinline__ void stv<__nv_bfloat16>(__nv_bfloat16* p,
     *p = __float2bfloat16_rn(v);
 }
 
-// Projection onto {|y| <= s}: Euclidean ball (ISO) or box (ANISO).
+// Projection onto {|y| <= s}: Euclidean ball (ISO) or box (ANISO).  A zero
+// capacity maps every y to exactly 0 (|y|^2 of a tiny y may underflow).
 template <int DIM>
 __device__ __forceinline__ void project(float (&y)[DIM], float s, int aniso) {
     if (aniso) {
@@ -81,8 +82,8 @@ __device__ __forceinline__ void project(float (&y)[DIM], float s, int aniso) {
         float r2 = 0.f;
 #pragma unroll
         for (int k = 0; k < DIM; ++k) r2 = fmaf(y[k], y[k], r2);
-        if (r2 > s * s) {
-            const float f = s * rsqrtf(r2);
+        if (r2 > s * s || s <= 0.f) {
+            const float f = s > 0.f ? s * rsqrtf(r2) : 0.f;
 #pragma unroll
             for (int k = 0; k < DIM; ++k) y[k] *= f;
         }

@@ -94,8 +94,8 @@ __global__ void set_flows_kernel(const float* src, int nn, int ndim, int nx, int
         const float slack = sizeof(T) == 4 ? 1.000001f : 1.02f;
         float r2 = 0.f;
         for (int k = 0; k < ndim; ++k) r2 = fmaf(yv[k], yv[k], r2);
-        if (r2 > s * s * slack) {
-            const float f = s * rsqrtf(r2);
+        if (r2 > s * s * slack || s <= 0.f) {
+            const float f = s > 0.f ? s * rsqrtf(r2) : 0.f;
             for (int k = 0; k < ndim; ++k) yv[k] *= f;
         }
     }

@@ -116,8 +116,12 @@ def test_checkpoint_interval_does_not_change_gradients():
 
 
 def test_adjoint_matches_finite_differences_of_oracle():
-    """Central differences (h = 1e-3) of the FP64 oracle's loss on random
-    entries of D and S, against the GPU adjoint."""
+    """Central differences of the FP64 oracle's loss on random entries of D
+    and S, against the GPU adjoint.  The loss is only piecewise smooth (the
+    capacity projection has a kink at |y| = S), so the step must stay inside
+    one smooth piece: h = 1e-3 crosses kinks on some entries of this problem
+    (a sign flip was seen at one entry), h = 1e-5 on the FP64 forward does
+    not and still resolves the difference quotient to ~1e-8."""
     prob = synth.random_problem(5300, (7, 9, 11), nl=4, s_kind="field", s_scale=0.3)
     s_label = np.ones(4, dtype=np.float32)
     target = np.random.default_rng(5301).integers(0, 4, size=(7, 9, 11))
@@ -126,7 +130,7 @@ def test_adjoint_matches_finite_differences_of_oracle():
     D0 = prob.D.astype(np.float64)
     S0 = prob.S_field.astype(np.float64)
     rng = np.random.default_rng(5302)
-    h = 1e-3
+    h = 1e-5
     checked = 0
     for _ in range(24):
         which = rng.integers(0, 2)
