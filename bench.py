@@ -55,6 +55,26 @@ def parse():
     return ap.parse_args()
 
 
+def rank_seed(rank):
+    """Each rank solves its own seeded volume (weak scaling, no exchange)."""
+    return 2000 + rank
+
+
+def reduce_max(value, dist, device):
+    """Max of a per-rank scalar over all ranks (the slowest rank's time)."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def throughput(world, steps, units_per_step, seconds):
+    """Whole-job units per second: every rank processed steps * units_per_step."""
+    return world * steps * units_per_step / seconds
+
+
 def make_problem(cfg, seed, shape=None):
     import synth
     shape0, nl, gen, _, _ = CONFIGS[cfg]
@@ -287,7 +307,7 @@ def main():
     shape, nl, gen, schedule, storage = CONFIGS[cfg]
     if args.dims:
         shape = (args.dims,) * 3
-    prob = make_problem(cfg, seed=2000 + rank, shape=shape)
+    prob = make_problem(cfg, seed=rank_seed(rank), shape=shape)
     D = torch.from_numpy(prob.D).cuda()
     S = None if prob.S_field is None else torch.from_numpy(prob.S_field).cuda()
     stream = torch.cuda.current_stream()
@@ -329,11 +349,8 @@ def main():
     launches = gp.launches - launches0
     elapsed = t_start.elapsed_time(t_end) / 1e3
     kern_ms = sum(a.elapsed_time(b) for a, b in ev) / (args.steps * (ITERS_PER_STEP - 1))  # per iteration
-    if dist is not None:
-        t = torch.tensor([elapsed], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
-    value = world * args.steps * vlu_step / elapsed
+    elapsed = reduce_max(elapsed, dist, "cuda")
+    value = throughput(world, args.steps, vlu_step, elapsed)
 
     # end to end through the C ABI with pinned host buffers: upload D and S,
     # iterate, energy, read the thresholded labelling back, every step
@@ -358,11 +375,8 @@ def main():
         e1.record(stream)
         barrier()
         te = e0.elapsed_time(e1) / 1e3
-        if dist is not None:
-            t = torch.tensor([te], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            te = float(t.item())
-        e2e = {"value": world * args.steps * vlu_step / te, "unit": "VLU/s",
+        te = reduce_max(te, dist, "cuda")
+        e2e = {"value": throughput(world, args.steps, vlu_step, te), "unit": "VLU/s",
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
     peaks = {}
