@@ -37,6 +37,8 @@ CONFIGS = {
     "hmf": ((192, 192, 192), 12, "hmf", 0, 0),
     "hmf_bf16": ((192, 192, 192), 12, "hmf", 0, 1),
     "dagmf_batched": (None, 10, "dagmf_batch", 0, 0),
+    "ishikawa": ((256, 256, 256), 8, "ishikawa", 0, 0),
+    "continuation": ((128, 128, 128), 8, "potts3d", 0, 0),
 }
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_1501_07844_gb300", "csrc", f) for f in ("pfm_device.cuh", "pfm_tma.cuh")]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic.json")
@@ -81,6 +83,8 @@ def make_problem(cfg, seed, shape=None):
     shape = shape or shape0
     if gen == "potts3d":
         return synth.potts3d_problem(seed=seed, nl=nl, shape=shape)
+    if gen == "ishikawa":
+        return synth.ishikawa_problem(seed=seed, spatial=shape, nlev=nl - 1)
     return synth.hmf_problem(seed=seed, shape=shape)
 
 
@@ -282,6 +286,36 @@ def run_batched(args, rank, world):
     b.close()
 
 
+def run_continuation(args):
+    """Iterations to a relative primal-dual gap of 1e-4 on the 3-D Potts
+    phantom (128^3 x 8): fixed c = 0.5 against schedules that lower c by
+    half every 100 iterations down to a floor (continuation toward the
+    c -> 0 limit), and against a larger fixed c."""
+    import torch
+    import paper_1501_07844_gb300 as pfm
+    prob = make_problem("continuation", seed=2000)
+    D = torch.from_numpy(prob.D).cuda()
+    S = torch.from_numpy(prob.S_field).cuda()
+    out = {}
+    for name, c0, floor in (("fixed_c0.5", 0.5, 0.5), ("fixed_c1.0", 1.0, 1.0), ("cont_1.0_to_0.25", 1.0, 0.25),
+                            ("cont_2.0_to_0.5", 2.0, 0.5)):
+        gp = pfm.Problem(D, S_field=S, c=c0, tau=0.11, check_every=10)
+        c, done, gap = c0, 0, float("inf")
+        t0 = time.perf_counter()
+        while done < 20000 and gap > 1e-4:
+            if done and done % 100 == 0 and c > floor:
+                c = max(floor, c / 2)
+                gp.set_step(c, 0.11)
+            E, P = gp.iterate_energy(10)
+            done += 10
+            gap = (E - P) / abs(E)
+        torch.cuda.synchronize()
+        out[name] = {"iters_to_gap_1e-4": done, "final_gap": gap, "seconds": time.perf_counter() - t0, "final_c": c}
+        gp.close()
+    print(json.dumps({"metric": "iterations to relative gap 1e-4 (continuation)", "config": {"workload": "potts3d 128^3 x 8"},
+                      "results": out}), flush=True)
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -292,6 +326,9 @@ def main():
         return
     if args.config == "dagmf_batched":
         run_batched(args, rank, world)
+        return
+    if args.config == "continuation":
+        run_continuation(args)
         return
 
     import torch

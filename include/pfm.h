@@ -156,6 +156,14 @@ PFM_API pfm_status pfm_set_data(pfm_problem* pb, const float* D, const float* S_
 /* u_L = 1/#leaves, q = 0, iteration counter = 0.  Asynchronous. */
 PFM_API pfm_status pfm_reset(pfm_problem* pb);
 
+/* Sets the entropic weight c and the step tau used by the following
+ * iterations (c > 0, tau > 0; the applied flow step is c*tau).  Lowering c
+ * between blocks of iterations is the continuation toward the c -> 0 limit
+ * of Section 3.2, where the label update tends to the per-voxel argmin of
+ * the excess and the smoothed objective to the pseudo-flow dual.  Problems
+ * in a batch keep the batch's parameters. */
+PFM_API pfm_status pfm_set_step(pfm_problem* pb, double c, double tau);
+
 /* Queues n_iters >= 0 iterations (Algorithm 1 / Algorithm 2 loop body) on
  * the problem's stream.  Asynchronous; errors of the launches are reported
  * here, device-side non-finite values by the next pfm_energy. */

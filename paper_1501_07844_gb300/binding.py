@@ -54,6 +54,7 @@ _SIGS = {
     "pfm_set_data": (C.c_int, [_P, _P, _P]),
     "pfm_reset": (C.c_int, [_P]),
     "pfm_iterate": (C.c_int, [_P, C.c_int]),
+    "pfm_set_step": (C.c_int, [_P, C.c_double, C.c_double]),
     "pfm_energy": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "pfm_run_to_gap": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
     "pfm_iterate_energy": (C.c_int, [_P, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
@@ -242,6 +243,10 @@ class Problem:
 
     def iterate(self, n):
         check(lib().pfm_iterate(self._h, int(n)))
+
+    def set_step(self, c, tau):
+        """Entropic weight c and step tau for the following iterations."""
+        check(lib().pfm_set_step(self._h, float(c), float(tau)))
 
     def energy(self):
         E, P = C.c_double(), C.c_double()

@@ -467,6 +467,15 @@ pfm_status pfm_reset(pfm_problem* pb) {
     return PFM_OK;
 }
 
+pfm_status pfm_set_step(pfm_problem* pb, double c, double tau) {
+    if (!pb) return fail(PFM_EINVAL, "NULL problem");
+    if (!(c > 0) || !isfinite(c) || !(tau > 0) || !isfinite(tau)) return fail(PFM_EINVAL, "c and tau must be > 0");
+    pb->prm.c = c;
+    pb->prm.tau = tau;
+    pb->solver->set_step((float)c, (float)tau);
+    return PFM_OK;
+}
+
 pfm_status pfm_iterate(pfm_problem* pb, int n_iters) {
     if (!pb) return fail(PFM_EINVAL, "NULL problem");
     if (n_iters < 0) return fail(PFM_EINVAL, "n_iters must be >= 0");

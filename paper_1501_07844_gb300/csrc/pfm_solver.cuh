@@ -60,6 +60,8 @@ struct SolverBase {
     virtual const char* variant(bool fused) const = 0;
     // True if step() with a partials buffer evaluates the energy of its input.
     virtual bool fuses_energy(bool fused) const { return false; }
+    // New entropic weight c and step tau for the following iterations.
+    virtual void set_step(float c, float tau) = 0;
 };
 
 template <int MAXL, int MAXN, int DIM, bool IS_DAG, typename T>
@@ -188,6 +190,11 @@ struct Solver final : SolverBase {
     }
 
     bool fuses_energy(bool fused) const override { return fused && kTmaCapable && tma_ready && use_tma; }
+
+    void set_step(float c, float tau) override {
+        base.inv_c = 1.0f / c;
+        base.ctau = c * tau;
+    }
 
     const char* variant(bool fused) const override {
         if (!fused) return "inplace";

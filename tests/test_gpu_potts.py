@@ -236,3 +236,22 @@ def test_iterate_energy_reports_input_of_last_iteration(sched, storage):
     if storage == 0:
         _, _, E_o, P_o = oracle_run(prob, 6)
         assert abs(E - E_o) <= 1e-5 * abs(E_o) and abs(P - P_o) <= 1e-5 * abs(P_o)
+
+
+@pytest.mark.parametrize("sched", [0, 1, 2], ids=["fused_tma", "inplace", "fused_plain"])
+def test_continuation_schedule_matches_oracle(sched):
+    """c lowered between blocks (continuation toward c -> 0): GPU and oracle
+    follow the same schedule."""
+    import oracle
+    prob = synth.potts3d_problem(seed=2500, nl=8, shape=(17, 25, 40))
+    D, S = prob.D.astype(np.float64), prob.S_field.astype(np.float64)
+    u, q = oracle.potts_init(prob.spatial, 8)
+    with gpu_problem(prob, schedule=sched, c=1.0) as gp:
+        for c in (1.0, 0.5, 0.25):
+            gp.set_step(c, 0.11)
+            gp.iterate(15)
+            oracle.potts_iterate(D, u, q, 15, c, 0.11, S_field=S)
+        assert np.abs(gp.labels().cpu().numpy() - u).max() <= 1e-3
+        E, P = gp.energy()
+        E_o, _ = oracle.potts_energy(D, u, q, S_field=S)
+        assert abs(E - E_o) <= 1e-5 * abs(E_o)
