@@ -267,6 +267,28 @@ PFM_API pfm_status pfm_batch_energy(pfm_batch* b, double* primal, double* dual);
 PFM_API pfm_status pfm_batch_tune(pfm_batch* b, int trial_iters, int* zc_out, int* grid_out);
 PFM_API int64_t pfm_batch_launch_count(const pfm_batch* b);
 
+/* ---- Explicit-flow ("full-flow") solver, the comparison path ----
+ * The augmented-Lagrangian continuous max-flow of the Potts model with every
+ * flow stored (source flow p_S, sink flows p_L, spatial flows q_L, labels as
+ * multipliers u_L): the primal of Section 3.2 and the formulation the
+ * pseudo-flow method replaces.  One iteration: f_L = u_L - gamma G_L with
+ * G_L = div q_L - p_S + p_L; q_L <- Proj(q_L - step grad f_L);
+ * p_L <- min(D_L, p_S - div q_L + u_L/gamma);
+ * p_S <- (sum_L (div q_L + p_L - u_L/gamma) + 1/gamma)/#L;
+ * u_L <- u_L - gamma G_L.  Potts problems (flat label set), FP32.  Kept to
+ * measure the paper's memory and time claims on the same GPU.
+ * pfm_alm_energy reports E(u) and P(q) as pfm_energy does for the current
+ * (u, q), and flow = sum_x p_S, the primal objective. */
+typedef struct pfm_alm pfm_alm;
+PFM_API pfm_status pfm_alm_footprint(const pfm_desc* desc, size_t* device_bytes, int64_t* n_grid_buffers);
+PFM_API pfm_status pfm_alm_create(const pfm_desc* desc, double gamma, double step, int norm, void* stream,
+                                  pfm_alm** out);
+PFM_API void pfm_alm_destroy(pfm_alm* m);
+PFM_API pfm_status pfm_alm_iterate(pfm_alm* m, int n_iters);
+PFM_API pfm_status pfm_alm_energy(pfm_alm* m, double* primal, double* dual, double* flow);
+PFM_API pfm_status pfm_alm_get_labels(pfm_alm* m, float* dst);
+PFM_API int64_t pfm_alm_iterations_done(const pfm_alm* m);
+
 /* Allocation-free energy evaluation.  The paper has no counterpart: this is
  * a service for callers that cannot call cudaMalloc -- code whose device
  * memory belongs to an outer allocator that has already claimed the budget

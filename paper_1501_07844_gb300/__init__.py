@@ -10,6 +10,7 @@ binding raises if the library cannot be loaded.
 """
 from .binding import (  # noqa: F401
     ANISO,
+    AlmProblem,
     BF16,
     Batch,
     F32,

@@ -77,6 +77,13 @@ _SIGS = {
     "pfm_batch_energy": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "pfm_batch_tune": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "pfm_batch_launch_count": (C.c_int64, [_P]),
+    "pfm_alm_footprint": (C.c_int, [C.POINTER(pfm_desc), C.POINTER(C.c_size_t), C.POINTER(C.c_int64)]),
+    "pfm_alm_create": (C.c_int, [C.POINTER(pfm_desc), C.c_double, C.c_double, C.c_int, _P, C.POINTER(_P)]),
+    "pfm_alm_destroy": (None, [_P]),
+    "pfm_alm_iterate": (C.c_int, [_P, C.c_int]),
+    "pfm_alm_energy": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "pfm_alm_get_labels": (C.c_int, [_P, _P]),
+    "pfm_alm_iterations_done": (C.c_int64, [_P]),
     "pfm_potts_energy_noalloc": (C.c_int, [C.c_int, C.POINTER(C.c_int64), C.c_int, _P, _P, _P, _P,
                                            C.POINTER(C.c_float), C.c_int, _P, _P]),
 }
@@ -404,3 +411,63 @@ class Batch:
     @property
     def launches(self):
         return lib().pfm_batch_launch_count(self._h)
+
+
+def alm_footprint(spatial, nl, has_S_field=True):
+    """(device bytes, full-grid buffers) of the explicit-flow solver (host-only)."""
+    dummy = C.c_void_p(1)
+    d = _Desc(spatial, nl, [(-1, L, 1.0) for L in range(nl)], dummy, dummy if has_S_field else None, None)
+    nb, nbuf = C.c_size_t(), C.c_int64()
+    check(lib().pfm_alm_footprint(C.byref(d.c), C.byref(nb), C.byref(nbuf)))
+    return nb.value, nbuf.value
+
+
+class AlmProblem:
+    """Explicit-flow augmented-Lagrangian max-flow of a Potts problem (pfm_alm_*)."""
+
+    def __init__(self, D, S_field=None, s_node=None, gamma=0.3, step=0.2, norm=ISO, stream=None):
+        D = _as_f32(D)
+        S_field = _as_f32(S_field)
+        nl = D.shape[0]
+        self.spatial = tuple(D.shape[1:])
+        self.n_leaf = nl
+        self._desc = _Desc(self.spatial, nl, [(-1, L, 1.0) for L in range(nl)], _ptr(D), _ptr(S_field), s_node)
+        h = C.c_void_p()
+        check(lib().pfm_alm_create(C.byref(self._desc.c), float(gamma), float(step), int(norm),
+                                   _stream_handle(stream), C.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().pfm_alm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def iterate(self, n):
+        check(lib().pfm_alm_iterate(self._h, int(n)))
+
+    def energy(self):
+        """(E(u), P(q), sum p_S)."""
+        E, P, F = C.c_double(), C.c_double(), C.c_double()
+        st = lib().pfm_alm_energy(self._h, C.byref(E), C.byref(P), C.byref(F))
+        if st not in (0, 5):
+            check(st)
+        return E.value, P.value, F.value
+
+    def labels(self, out=None):
+        import torch
+        out = out if out is not None else torch.empty((self.n_leaf,) + self.spatial, dtype=torch.float32,
+                                                      device="cuda")
+        check(lib().pfm_alm_get_labels(self._h, _ptr(out)))
+        return out

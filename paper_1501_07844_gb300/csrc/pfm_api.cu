@@ -988,4 +988,152 @@ pfm_status pfm_batch_tune(pfm_batch* b, int trial_iters, int* zc_out, int* grid_
 
 int64_t pfm_batch_launch_count(const pfm_batch* b) { return b ? b->launches : -1; }
 
+// ---------------------------------------------------------------------------
+// Explicit-flow ("full-flow") augmented-Lagrangian solver (comparison path).
+// ---------------------------------------------------------------------------
+}  // extern "C"
+
+struct pfm_alm {
+    pfm_problem* pb = nullptr;  // u = pb->u[0], q = pb->q[0], D, S, capacities, energy
+    float* pL = nullptr;
+    float* pS = nullptr;
+    float* f = nullptr;
+    double gamma = 0.3, step = 0.2;
+    int64_t iters = 0;
+};
+
+namespace {
+
+pfm::AlmArgs alm_args(const pfm_alm* m) {
+    const pfm_problem* pb = m->pb;
+    pfm::AlmArgs a{};
+    a.u = (float*)pb->u[0];
+    a.q = (float*)pb->q[0];
+    a.pL = m->pL;
+    a.pS = m->pS;
+    a.f = m->f;
+    a.D = pb->D;
+    a.S = pb->S;
+    a.nx = pb->nx;
+    a.ny = pb->ny;
+    a.nz = pb->nz;
+    a.nl = pb->nl;
+    a.n = pb->n;
+    a.gamma = (float)m->gamma;
+    a.step = (float)m->step;
+    a.aniso = pb->prm.norm == PFM_NORM_ANISO;
+    for (int j = 0; j < 16; ++j) a.s_node[j] = j < pb->nl ? pb->s_node[j] : 0.f;
+    return a;
+}
+
+void alm_free(pfm_alm* m) {
+    if (m->pb) cudaStreamSynchronize(m->pb->stream);
+    if (m->pL) cudaFree(m->pL);
+    if (m->pS) cudaFree(m->pS);
+    if (m->f) cudaFree(m->f);
+    cudaGetLastError();
+    pfm_destroy(m->pb);
+    delete m;
+}
+
+}  // namespace
+
+extern "C" {
+
+pfm_status pfm_alm_footprint(const pfm_desc* desc, size_t* device_bytes, int64_t* n_grid_buffers) {
+    pfm_params p;
+    pfm_params_default(&p);
+    p.schedule = PFM_SCHEDULE_INPLACE;
+    size_t b = 0;
+    int64_t nb = 0;
+    int nl = 0;
+    pfm_status st = pfm_footprint(desc, &p, &b, &nb, &nl);
+    if (st != PFM_OK) return st;
+    const long long n = (long long)desc->dims[0] * desc->dims[1] * desc->dims[2];
+    // + sink flows p_L, source flow p_S and the work field f
+    if (device_bytes) *device_bytes = b + (size_t)(2 * nl + 1) * n * 4;
+    if (n_grid_buffers) *n_grid_buffers = nb + 2 * nl + 1;
+    return PFM_OK;
+}
+
+pfm_status pfm_alm_create(const pfm_desc* desc, double gamma, double step, int norm, void* stream, pfm_alm** out) {
+    if (!out) return fail(PFM_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!(gamma > 0) || !(step > 0) || !isfinite(gamma) || !isfinite(step))
+        return fail(PFM_EINVAL, "gamma and step must be finite and > 0");
+    pfm_params p;
+    pfm_params_default(&p);
+    p.schedule = PFM_SCHEDULE_INPLACE;
+    p.norm = norm;
+    pfm_alm* m = new pfm_alm();
+    m->gamma = gamma;
+    m->step = step;
+    pfm_status st = pfm_create(desc, &p, stream, &m->pb);
+    if (st != PFM_OK) {
+        delete m;
+        return st;
+    }
+    if (!m->pb->flat || m->pb->nl > 16) {
+        alm_free(m);
+        return fail(PFM_EUNSUPPORTED, "the explicit-flow solver covers Potts problems with at most 16 labels");
+    }
+    const size_t n = (size_t)m->pb->n, nl = (size_t)m->pb->nl;
+    cudaError_t e;
+    if ((e = cudaMalloc(&m->pL, nl * n * 4)) != cudaSuccess || (e = cudaMalloc(&m->pS, n * 4)) != cudaSuccess ||
+        (e = cudaMalloc(&m->f, nl * n * 4)) != cudaSuccess) {
+        alm_free(m);
+        return cuda_fail(e, "alloc");
+    }
+    e = pfm::launch_alm_init(alm_args(m), m->pb->stream);
+    if (e != cudaSuccess) {
+        alm_free(m);
+        return cuda_fail(e, "alm init");
+    }
+    m->pb->launches++;
+    *out = m;
+    return PFM_OK;
+}
+
+void pfm_alm_destroy(pfm_alm* m) {
+    if (m) alm_free(m);
+}
+
+pfm_status pfm_alm_iterate(pfm_alm* m, int n_iters) {
+    if (!m) return fail(PFM_EINVAL, "NULL solver");
+    if (n_iters < 0) return fail(PFM_EINVAL, "n_iters must be >= 0");
+    const pfm::AlmArgs a = alm_args(m);
+    for (int k = 0; k < n_iters; ++k) {
+        PFM_CUDA(pfm::launch_alm_iteration(a, m->pb->ndim, m->pb->stream), "alm iterate");
+        m->pb->launches += 3;
+    }
+    m->iters += n_iters;
+    return PFM_OK;
+}
+
+pfm_status pfm_alm_energy(pfm_alm* m, double* primal, double* dual, double* flow) {
+    if (!m) return fail(PFM_EINVAL, "NULL solver");
+    pfm_problem* pb = m->pb;
+    double E = 0.0, P = 0.0;
+    pfm_status st = pfm_energy(pb, &E, &P);
+    if (st != PFM_OK && st != PFM_ENONFINITE) return st;
+    const int blocks = (int)std::min<long long>((pb->n + 255) / 256, pb->energy_blocks);
+    PFM_CUDA(pfm::launch_sum(m->pS, pb->n, pb->partial, blocks, pb->stream), "sum");
+    PFM_CUDA(pfm::launch_energy_final(pb->partial, blocks, pb->result, pb->flags, pb->stream), "sum");
+    pb->launches += 2;
+    double h[2];
+    PFM_CUDA(cudaMemcpyAsync(h, pb->result, sizeof h, cudaMemcpyDeviceToHost, pb->stream), "read");
+    PFM_CUDA(cudaStreamSynchronize(pb->stream), "sync");
+    if (primal) *primal = E;
+    if (dual) *dual = P;
+    if (flow) *flow = h[0];
+    return st;
+}
+
+pfm_status pfm_alm_get_labels(pfm_alm* m, float* dst) {
+    if (!m) return fail(PFM_EINVAL, "NULL solver");
+    return pfm_get_labels(m->pb, dst);
+}
+
+int64_t pfm_alm_iterations_done(const pfm_alm* m) { return m ? m->iters : -1; }
+
 }  // extern "C"

@@ -378,6 +378,25 @@ struct AdjLaunch {
 };
 cudaError_t launch_adjoint(const AdjLaunch& a, int ndim, cudaStream_t s);
 
+// Explicit-flow augmented-Lagrangian solver (pfm_alm.cu).
+struct AlmArgs {
+    float* u;      // [nl][n] multipliers (the labelling)
+    float* q;      // [nl][dim][n]
+    float* pL;     // [nl][n] sink flows
+    float* pS;     // [n] source flow
+    float* f;      // [nl][n] work
+    const float* D;
+    const float* S;
+    int nx, ny, nz, nl;
+    long long n;
+    float gamma, step;
+    int aniso;
+    float s_node[16];
+};
+cudaError_t launch_alm_init(const AlmArgs& a, cudaStream_t s);
+cudaError_t launch_alm_iteration(const AlmArgs& a, int ndim, cudaStream_t s);
+cudaError_t launch_sum(const float* v, long long n, double* partial, int blocks, cudaStream_t s);
+
 // Auxiliary kernels (pfm_misc.cu).
 cudaError_t launch_init_labels(void* u, int storage, int nl, long long n, cudaStream_t s);
 cudaError_t launch_argmax(const void* u, int storage, int nl, long long n, int* out, cudaStream_t s);

@@ -1,0 +1,56 @@
+"""Explicit-flow ("full-flow") augmented-Lagrangian solver on the GPU
+(pfm_alm_*): parity with the oracle's explicit-flow ALM, and the same
+optimum as the pseudo-flow solver (the equivalence chain of Section 3.2)."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("spatial,step,norm", [((40, 52), 0.25, 0), ((12, 14, 20), 0.2, 0), ((11, 13, 17), 0.2, 1)],
+                         ids=["2d_iso", "3d_iso", "3d_aniso"])
+def test_alm_matches_oracle_alm(spatial, step, norm):
+    import paper_1501_07844_gb300 as pfm
+    prob = synth.random_problem(5700, spatial, nl=4, s_kind="field", s_scale=0.3)
+    D, S = prob.D.astype(np.float64), prob.S_field.astype(np.float64)
+    iters = 300
+    flow_o, (u_o, q_o, pS_o, pL_o) = oracle.alm_potts(D, iters, 0.3, step, S_field=S, norm=norm)
+    with pfm.AlmProblem(prob.D, S_field=prob.S_field, gamma=0.3, step=step, norm=norm) as a:
+        a.iterate(iters)
+        _, _, flow = a.energy()
+        u = a.labels().cpu().numpy()
+    assert np.abs(u - u_o).max() <= 1e-3
+    assert abs(flow - flow_o) <= 1e-5 * abs(flow_o)
+
+
+@pytest.mark.gpu
+def test_alm_and_pseudo_flow_reach_the_same_optimum():
+    import paper_1501_07844_gb300 as pfm
+    from helpers import gpu_problem
+    prob = synth.random_problem(5800, (24, 30), nl=3, s_kind="field", s_scale=0.3)
+    with gpu_problem(prob, c=1.0, tau=0.25) as gp:
+        gp.iterate(20000)
+        E, P = gp.energy()
+    assert (E - P) <= 1e-6 * abs(E)
+    with pfm.AlmProblem(prob.D, S_field=prob.S_field, gamma=0.3, step=0.25) as a:
+        a.iterate(20000)
+        _, _, flow = a.energy()
+    assert abs(flow - E) <= 1e-5 * abs(E)
+
+
+@pytest.mark.parametrize("dummy", [0])
+def test_footprints_against_the_paper_claim(dummy):
+    """Abstract: pseudo-flow needs about 20 % less memory than full flow for
+    Potts.  Counted as full-grid buffers of the in-place pseudo-flow solver
+    against the explicit-flow solver (with and without its work field)."""
+    from paper_1501_07844_gb300.binding import alm_footprint, footprint
+    import paper_1501_07844_gb300 as pfm
+    nl = 8
+    _, pf, _ = footprint((64, 64, 64), nl, [(-1, L, 1.0) for L in range(nl)], has_S_field=True,
+                         schedule=pfm.INPLACE)
+    _, ff = alm_footprint((64, 64, 64), nl)
+    assert pf == 5 * nl + 1 and ff == 7 * nl + 2
+    assert 0.15 <= 1 - pf / (ff - nl) <= 0.25      # without the work field: 6 per label + 2
