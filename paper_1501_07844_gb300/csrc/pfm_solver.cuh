@@ -12,6 +12,7 @@
 
 #include "pfm_device.cuh"
 #include "pfm_tma.cuh"
+#include "pfm_tma_dag.cuh"
 
 namespace pfm {
 
@@ -69,9 +70,12 @@ struct Solver final : SolverBase {
     StepArgs<MAXL, MAXN> base{};
     size_t fused_smem = 0;
     static constexpr bool kTmaCapable = !IS_DAG && MAXL <= 8;
+    static constexpr bool kDagTmaCapable = IS_DAG && MAXL == DMAX && MAXN == DMAX;
     bool tma_ready = false;
     const void* tma_u[2] = {nullptr, nullptr};
     TmaMaps tma_maps[2];
+    bool dag_tma_ready = false;
+    DagLists lists{};
 
     explicit Solver(const ProblemView& v) {
         base.D = v.D;
@@ -133,6 +137,20 @@ struct Solver final : SolverBase {
                 return e;
             }
         }
+        if constexpr (kDagTmaCapable) {
+            if (fused && dag_tma_ready && use_tma) {
+                const int k = (u_in == tma_u[0]) ? 0 : 1;
+                a.zc = zc < 1 ? 1 : zc;
+                const DagTmaLayout lay(a.nl, a.nn, DIM, (int)sizeof(T));
+                cudaError_t e = cudaFuncSetAttribute(fused_dag_tma_kernel<DIM, T>,
+                                                     cudaFuncAttributeMaxDynamicSharedMemorySize, lay.total);
+                if (e != cudaSuccess) return e;
+                dim3 grid((a.nx + FTX - 1) / FTX, (a.ny + DTY - 1) / DTY, (a.nz + a.zc - 1) / a.zc);
+                fused_dag_tma_kernel<DIM, T><<<grid, DAG_TMA_NT, lay.total, s>>>(a, tma_maps[k], lists);
+                *launches = 1;
+                return cudaGetLastError();
+            }
+        }
         if (fused) {
             if (fused_smem > 48 * 1024) {
                 cudaError_t e = cudaFuncSetAttribute(fused_step_kernel<MAXL, MAXN, DIM, IS_DAG, T>,
@@ -156,7 +174,47 @@ struct Solver final : SolverBase {
     }
 
     bool prepare_tma(void* const* u, void* const* q, const float* D, const float* S) override {
-        if constexpr (!kTmaCapable) {
+        if constexpr (kDagTmaCapable) {
+            const int es = (int)sizeof(T);
+            if ((base.nx * es) % 16 != 0 || (base.nx * 4) % 16 != 0) return false;
+            const DagTmaLayout lay(base.nl, base.nn, DIM, es);
+            if (lay.total > 227 * 1024) return false;
+            // sparse path-weight lists: ancestors of each end-label, end-labels below each node
+            for (int j = 0; j < DMAX; ++j) lists.anc_n[j] = 0;
+            for (int A = 0; A < DMAX; ++A) lists.desc_n[A] = 0;
+            for (int A = 0; A < base.nn; ++A)
+                for (int j = 0; j < base.nl; ++j)
+                    if (base.W[A][j] != 0.f) {
+                        lists.anc[j][lists.anc_n[j]] = (unsigned char)A;
+                        lists.anc_w[j][lists.anc_n[j]++] = base.W[A][j];
+                        lists.desc[A][lists.desc_n[A]] = (unsigned char)j;
+                        lists.desc_w[A][lists.desc_n[A]++] = base.W[A][j];
+                    }
+            const int qbx = FTX + 2 * (16 / es);
+            const unsigned long long nx = base.nx, ny = base.ny, nz = base.nz;
+            const unsigned long long dims_u[4] = {nx, ny, nz, (unsigned long long)base.nl};
+            const unsigned long long dims_q[4] = {nx, ny, nz, (unsigned long long)DIM * base.nn};
+            const unsigned long long st_t[3] = {nx * es, nx * ny * es, nx * ny * nz * es};
+            const unsigned long long st_f[3] = {nx * 4, nx * ny * 4, nx * ny * nz * 4};
+            const unsigned box_u[4] = {(unsigned)TMA_BX, (unsigned)DAG_UY, 1u, (unsigned)base.nl};
+            const unsigned box_q[4] = {(unsigned)qbx, (unsigned)DAG_QY, 1u, (unsigned)(DIM * base.nn)};
+            const unsigned long long dims_s[3] = {nx, ny, nz};
+            const unsigned box_s[3] = {(unsigned)FTX, (unsigned)DTY, 1u};
+            for (int k = 0; k < 2; ++k) {
+                TmaMaps& m = tma_maps[k];
+                if (!encode_tiled_map(&m.u, u[k], es, 4, dims_u, st_t, box_u)) return false;
+                if (!encode_tiled_map(&m.q, q[k], es, 4, dims_q, st_t, box_q)) return false;
+                if (!encode_tiled_map(&m.D, D, 4, 4, dims_u, st_f, box_u)) return false;
+                if (S) {
+                    if (!encode_tiled_map(&m.S, S, 4, 3, dims_s, st_f, box_s)) return false;
+                } else {
+                    m.S = m.D;
+                }
+                tma_u[k] = u[k];
+            }
+            dag_tma_ready = true;
+            return false;  // the energy reduction keeps its own (non-TMA) kernel
+        } else if constexpr (!kTmaCapable) {
             return false;
         } else {
             using Lay = TmaLayout<MAXL, DIM, T>;
@@ -199,6 +257,7 @@ struct Solver final : SolverBase {
     const char* variant(bool fused) const override {
         if (!fused) return "inplace";
         if (kTmaCapable && tma_ready && use_tma) return "fused_tma";
+        if (kDagTmaCapable && dag_tma_ready && use_tma) return "fused_tma_dag";
         return "fused";
     }
 

@@ -326,10 +326,12 @@ fused_tma_kernel(const StepArgs<MAXL, MAXL> a, const __grid_constant__ TmaMaps m
             const int qi = (my + 1) * Lay::QBX + (mx + Lay::QOFF);
             const float sf = has_S ? sP[my * FTX + mx] : 1.0f;
             const long long i0 = (long long)pm * plane + (long long)ym * a.nx + xm;
-            // forward differences are zero at the last index: fold that into the step
-            const float cx = xm < a.nx - 1 ? a.ctau : 0.f;
-            const float cy = ym < a.ny - 1 ? a.ctau : 0.f;
-            const float cz = pm < a.nz - 1 ? a.ctau : 0.f;
+            // forward differences are zero at the last index; the neighbour's g
+            // slot beyond the grid is never written, so select, never multiply
+            const bool vx = xm < a.nx - 1, vy = ym < a.ny - 1, vz = pm < a.nz - 1;
+            const float cx = vx ? a.ctau : 0.f;
+            const float cy = vy ? a.ctau : 0.f;
+            const float cz = vz ? a.ctau : 0.f;
             float eloc = 0.f;
 #pragma unroll
             for (int i = 0; i < HL; ++i) {
@@ -338,11 +340,11 @@ fused_tma_kernel(const StepArgs<MAXL, MAXL> a, const __grid_constant__ TmaMaps m
                     const float* gj = gP + j * ustride;
                     const float g0 = gj[ui];
                     float yv[DIM];
-                    yv[0] = lds<T>(qP + (j * DIM + 0) * qstride + qi) - cx * (gj[ui + 1] - g0);
-                    yv[1] = lds<T>(qP + (j * DIM + 1) * qstride + qi) - cy * (gj[ui + TMA_BX] - g0);
+                    yv[0] = lds<T>(qP + (j * DIM + 0) * qstride + qi) - a.ctau * (vx ? gj[ui + 1] - g0 : 0.f);
+                    yv[1] = lds<T>(qP + (j * DIM + 1) * qstride + qi) - a.ctau * (vy ? gj[ui + TMA_BX] - g0 : 0.f);
                     if constexpr (DIM == 3)
                         yv[2] = lds<T>(qP + (j * DIM + 2) * qstride + qi) -
-                                cz * ((cz != 0.f ? gC[j * ustride + ui] : g0) - g0);
+                                a.ctau * (vz ? gC[j * ustride + ui] - g0 : 0.f);
                     const float sj = cap[i] * sf;
                     if constexpr (WITH_E) {
                         // E of plane p-1 on the input labelling (staged u of planes p-1 and p)

@@ -1,0 +1,271 @@
+// pfm_tma_dag.cuh -- TMA-pipelined fused iteration for DAG / HMF problems
+// (Algorithm 2, path-weight form).
+//
+// Same plane pipeline as the Potts kernel (three-stage cp.async.bulk.tensor
+// ring, label prox of plane p on the halo-extended tile, flow step of plane
+// p-1), with a 32 x 4 tile so that three stages of every node's flow fit in
+// shared memory, and four threads per voxel:
+//   prox:  thread h of voxel v computes e_A = div q_A for nodes A = h, h+4, ...
+//          into a per-voxel shared row, then d_j = D_j + sum_A W_(A,j) e_A for
+//          end-labels j = h, h+4, ... from the sparse ancestor list of j;
+//          the per-voxel minimum and normaliser are combined over the four
+//          lanes with two shuffles each;
+//   flow:  thread h of an owned voxel updates the flows of nodes A = h, h+4,
+//          ..., with grad g_A = sum_j W_(A,j) grad g_j over the sparse list of
+//          end-labels below A.
+// The lists hold every nonzero path weight W_(A,j) (W_(j,j) = 1), so the sums
+// equal the ordered top-down / bottom-up loops of Algorithm 2.
+#pragma once
+
+#include "pfm_tma.cuh"
+
+namespace pfm {
+
+constexpr int DTY = 4;                         // tile rows
+constexpr int DEY = DTY + 1;                   // halo-extended rows (5)
+constexpr int DNE = FEX * DEY;                 // 165 halo-extended voxels
+constexpr int DAG_TMA_NT = ((4 * DNE + 31) / 32) * 32;  // 672 threads
+constexpr int DAG_UY = DEY;                    // u / D box rows
+constexpr int DAG_QY = DEY + 1;                // flow box rows (y0-1 .. y0+4)
+constexpr int DMAX = 16;                       // max end-labels / nodes
+
+struct DagLists {
+    unsigned char anc_n[DMAX];          // ancestors of end-label j (incl. its own node)
+    unsigned char anc[DMAX][DMAX];      // node ids
+    float anc_w[DMAX][DMAX];            // W_(A,j)
+    unsigned char desc_n[DMAX];         // end-labels below node A (incl. A itself if A is one)
+    unsigned char desc[DMAX][DMAX];     // end-label indices
+    float desc_w[DMAX][DMAX];           // W_(A,j)
+};
+
+// Shared-memory layout, sized by the runtime label / node counts.
+struct DagTmaLayout {
+    int u_off, d_off, q_off, s_off, stage_bytes, g_off, e_off, bar_off, total;
+    __host__ __device__ static int a128(int b) { return (b + 127) / 128 * 128; }
+    __host__ __device__ DagTmaLayout(int nl, int nn, int dim, int es) {
+        const int qbx = FTX + 2 * (16 / es);
+        u_off = 0;
+        d_off = a128(nl * DAG_UY * TMA_BX * es);
+        q_off = d_off + a128(nl * DAG_UY * TMA_BX * 4);
+        s_off = q_off + a128(dim * nn * DAG_QY * qbx * es);
+        stage_bytes = s_off + a128(FTX * DTY * 4);
+        g_off = TMA_STAGES * stage_bytes;
+        e_off = g_off + a128(2 * nl * DAG_UY * TMA_BX * 4);
+        bar_off = e_off + a128(DNE * nn * 4);
+        total = bar_off + 64 + 128;
+    }
+};
+
+template <int DIM, typename T>
+__global__ void __launch_bounds__(DAG_TMA_NT, 1)
+fused_dag_tma_kernel(const StepArgs<DMAX, DMAX> a, const __grid_constant__ TmaMaps maps,
+                     const __grid_constant__ DagLists lists) {
+    constexpr int QOFF = 16 / (int)sizeof(T);
+    constexpr int QBX = FTX + 2 * QOFF;
+    constexpr int qstride = DAG_QY * QBX;
+    constexpr int ustride = DAG_UY * TMA_BX;
+    constexpr int PER = DMAX / 4;  // labels / nodes per thread at most
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ int s_abort;
+    unsigned char* smem = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
+    const int nl = a.nl, nn = a.nn;
+    const DagTmaLayout lay(nl, nn, DIM, (int)sizeof(T));
+    const int t = threadIdx.x;
+    const int h = t & 3;
+    const int v = t >> 2;
+    const int x0 = blockIdx.x * FTX, y0 = blockIdx.y * DTY;
+    const int z0 = blockIdx.z * a.zc;
+    const int z1 = min(z0 + a.zc, a.nz);
+    const long long n = a.n;
+    const long long plane = (long long)a.nx * a.ny;
+    T* __restrict__ uout = static_cast<T*>(a.u_out);
+    T* __restrict__ qout = static_cast<T*>(a.q_out);
+    const int has_S = a.S != nullptr;
+    const unsigned bytes_u = (unsigned)(nl * ustride * sizeof(T));
+    const unsigned bytes_d = (unsigned)(nl * ustride * 4);
+    const unsigned bytes_q = (unsigned)(DIM * nn * qstride * sizeof(T));
+    const unsigned bytes_s = has_S ? (unsigned)(FTX * DTY * 4) : 0u;
+    const unsigned bar0 = smem_addr(smem + lay.bar_off);
+    const float kexp = -a.inv_c * 1.4426950408889634f;
+    float* gbuf = reinterpret_cast<float*>(smem + lay.g_off);
+    float* ebuf = reinterpret_cast<float*>(smem + lay.e_off);
+    const int g_elems = nl * ustride;
+
+    auto stage_ptr = [&](int k) { return smem + k * lay.stage_bytes; };
+    auto issue = [&](int p, int k, bool flows_only) {
+        const unsigned bar = bar0 + 8 * k;
+        unsigned char* st = stage_ptr(k);
+        mbar_expect_tx(bar, flows_only ? bytes_q : bytes_u + bytes_d + bytes_q + bytes_s);
+        tma_load_4d(smem_addr(st + lay.q_off), &maps.q, x0 - QOFF, y0 - 1, p, 0, bar);
+        if (!flows_only) {
+            tma_load_4d(smem_addr(st + lay.u_off), &maps.u, x0, y0, p, 0, bar);
+            tma_load_4d(smem_addr(st + lay.d_off), &maps.D, x0, y0, p, 0, bar);
+            if (has_S) tma_load_3d(smem_addr(st + lay.s_off), &maps.S, x0, y0, p, bar);
+        }
+    };
+
+    if (t == 0) {
+        for (int k = 0; k < TMA_STAGES; ++k) mbar_init(bar0 + 8 * k, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_abort = 0;
+        issue(z0 - 1, 0, true);
+        issue(z0, 1, false);
+    }
+    __syncthreads();
+
+    const bool inE = v < DNE;
+    const int ex = v % FEX, ey = v / FEX;
+    const int xe = x0 + ex, ye = y0 + ey;
+    const bool validE = inE && xe < a.nx && ye < a.ny;
+    const bool ownerE = validE && ex < FTX && ey < DTY;
+    const bool inM = v < FTX * DTY;
+    const int mx = v % FTX, my = v / FTX;
+    const int xm = x0 + mx, ym = y0 + my;
+    const bool validM = inM && xm < a.nx && ym < a.ny;
+    float* erow = ebuf + (inE ? v : 0) * nn;
+
+    bool bad = false;
+    int inflight_hi = z0;
+    for (int p = z0; p <= z1; ++p) {
+        const int s = p - z0 + 1;
+        const int cs = s % 3, ps = (s + 2) % 3, ns = (s + 1) % 3;
+        if (t == 0 && p + 1 <= z1 && p + 1 < a.nz) {
+            issue(p + 1, ns, false);
+            inflight_hi = p + 1;
+        }
+        unsigned char* cst = stage_ptr(cs);
+        unsigned char* pst = stage_ptr(ps);
+        float* gC = gbuf + (p & 1) * g_elems;
+        const float* gP = gbuf + ((p + 1) & 1) * g_elems;
+        bool ok = true;
+        if (p == z0) ok = mbar_wait_bounded(bar0 + 8 * ps, 0u);
+        if (p < a.nz && ok) ok = mbar_wait_bounded(bar0 + 8 * cs, (unsigned)((s / 3) & 1));
+        if (!ok) {
+            atomicOr(a.flags, FLAG_TIMEOUT);
+            s_abort = 1;
+        }
+        __syncthreads();
+        if (s_abort) break;
+
+        if (p < a.nz) {
+            const T* uS = reinterpret_cast<const T*>(cst + lay.u_off);
+            const float* dS = reinterpret_cast<const float*>(cst + lay.d_off);
+            const T* qS = reinterpret_cast<const T*>(cst + lay.q_off);
+            const T* qP = reinterpret_cast<const T*>(pst + lay.q_off);
+            const int ui = ey * TMA_BX + ex;
+            const int qi = (ey + 1) * QBX + (ex + QOFF);
+            // divergence of this thread's nodes (no boundary tests: the last-index
+            // normal flow is an invariant zero, the box is zero-filled outside)
+            if (validE) {
+#pragma unroll
+                for (int i = 0; i < PER; ++i) {
+                    const int A = h + 4 * i;
+                    if (A < nn) {
+                        const T* qx = qS + (A * DIM + 0) * qstride + qi;
+                        const T* qy = qS + (A * DIM + 1) * qstride + qi;
+                        float dv = (lds<T>(qx) - lds<T>(qx - 1)) + (lds<T>(qy) - lds<T>(qy - QBX));
+                        if constexpr (DIM == 3)
+                            dv += lds<T>(qS + (A * DIM + 2) * qstride + qi) - lds<T>(qP + (A * DIM + 2) * qstride + qi);
+                        erow[A] = dv;
+                    }
+                }
+            }
+            __syncwarp();
+            float u[PER], d[PER];
+            float mloc = 3.0e38f;
+#pragma unroll
+            for (int i = 0; i < PER; ++i) {
+                const int j = h + 4 * i;
+                u[i] = 0.f;
+                d[i] = 0.f;
+                if (validE && j < nl) {
+                    u[i] = lds<T>(uS + j * ustride + ui);
+                    float dj = dS[j * ustride + ui];
+                    const int na = lists.anc_n[j];
+                    for (int k = 0; k < na; ++k) dj = fmaf(lists.anc_w[j][k], erow[lists.anc[j][k]], dj);
+                    d[i] = dj;
+                    mloc = fminf(mloc, dj);
+                }
+            }
+            float m = fminf(mloc, __shfl_xor_sync(0xffffffffu, mloc, 1));
+            m = fminf(m, __shfl_xor_sync(0xffffffffu, m, 2));
+            if (a.literal) m = 0.f;
+            float sloc = 0.f;
+#pragma unroll
+            for (int i = 0; i < PER; ++i) {
+                const int j = h + 4 * i;
+                if (validE && j < nl) {
+                    u[i] *= ex2_approx((d[i] - m) * kexp);
+                    sloc += u[i];
+                }
+            }
+            float sum = sloc + __shfl_xor_sync(0xffffffffu, sloc, 1);
+            sum += __shfl_xor_sync(0xffffffffu, sum, 2);
+            if (validE) {
+                if (!((sum > 0.f) && (sum <= 3.0e38f))) bad = true;
+                const float inv = 1.0f / sum;
+                const long long i0 = (long long)p * plane + (long long)ye * a.nx + xe;
+#pragma unroll
+                for (int i = 0; i < PER; ++i) {
+                    const int j = h + 4 * i;
+                    if (j < nl) {
+                        const float un = u[i] * inv;
+                        gC[j * ustride + ui] = a.literal ? u[i] : un;
+                        if (ownerE && p < z1) stv<T>(uout + (long long)j * n + i0, un);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+
+        const int pm = p - 1;
+        if (pm >= z0 && validM) {
+            const T* qP = reinterpret_cast<const T*>(pst + lay.q_off);
+            const float* sP = reinterpret_cast<const float*>(pst + lay.s_off);
+            const int ui = my * TMA_BX + mx;
+            const int qi = (my + 1) * QBX + (mx + QOFF);
+            const float sf = has_S ? sP[my * FTX + mx] : 1.0f;
+            const long long i0 = (long long)pm * plane + (long long)ym * a.nx + xm;
+            // the neighbour's g slot beyond the grid is never written: select
+            const bool vx = xm < a.nx - 1, vy = ym < a.ny - 1, vz = pm < a.nz - 1;
+#pragma unroll
+            for (int i = 0; i < PER; ++i) {
+                const int A = h + 4 * i;
+                if (A < nn) {
+                    float gr[DIM];
+#pragma unroll
+                    for (int k = 0; k < DIM; ++k) gr[k] = 0.f;
+                    const int nd = lists.desc_n[A];
+                    for (int k = 0; k < nd; ++k) {
+                        const int j = lists.desc[A][k];
+                        const float w = lists.desc_w[A][k];
+                        const float* gj = gP + j * ustride + ui;
+                        const float g0 = gj[0];
+                        gr[0] = fmaf(w, vx ? gj[1] - g0 : 0.f, gr[0]);
+                        gr[1] = fmaf(w, vy ? gj[TMA_BX] - g0 : 0.f, gr[1]);
+                        if constexpr (DIM == 3) gr[2] = fmaf(w, vz ? gC[j * ustride + ui] - g0 : 0.f, gr[2]);
+                    }
+                    float yv[DIM];
+                    yv[0] = lds<T>(qP + (A * DIM + 0) * qstride + qi) - a.ctau * gr[0];
+                    yv[1] = lds<T>(qP + (A * DIM + 1) * qstride + qi) - a.ctau * gr[1];
+                    if constexpr (DIM == 3) yv[2] = lds<T>(qP + (A * DIM + 2) * qstride + qi) - a.ctau * gr[2];
+                    project_nb<DIM>(yv, a.s_node[A] * sf, a.aniso);
+                    T* qa = qout + (long long)A * DIM * n + i0;
+#pragma unroll
+                    for (int k = 0; k < DIM; ++k) stv<T>(qa + k * n, yv[k]);
+                }
+            }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+    }
+    if (bad) atomicOr(a.flags, FLAG_NONFINITE);
+    if (s_abort && t == 0) {
+        for (int p = z0 - 1; p <= inflight_hi; ++p) {
+            const int s = p - z0 + 1;
+            mbar_wait_bounded(bar0 + 8 * (s % 3), (unsigned)((s / 3) & 1));
+        }
+    }
+}
+
+}  // namespace pfm

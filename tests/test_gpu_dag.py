@@ -75,3 +75,32 @@ def test_ishikawa_chain_matches_algorithm3(nlev, spatial):
     assert np.abs(u - u3).max() <= 1e-3
     assert np.abs(q[:nlev] - q3).max() <= 1e-3 and np.all(q[nlev:] == 0)
     assert np.mean(np.argmax(u, 0) == np.argmax(u3, 0)) >= 0.999
+
+
+@pytest.mark.parametrize("kind", ["hmf", "dagmf", "ishikawa8"])
+@pytest.mark.parametrize("storage", [0, 1], ids=["f32", "bf16"])
+def test_tma_dag_kernel_parity(kind, storage):
+    """A 16-byte row pitch selects the TMA-staged DAG kernel (32 x 4 tiles,
+    four threads per voxel, sparse path-weight lists); it matches the oracle
+    (FP32) and the register-staged kernel (both storages)."""
+    import paper_1501_07844_gb300 as pfm
+    shape = (23, 19, 48)
+    if kind == "hmf":
+        prob = synth.hmf_problem(seed=3400, shape=shape, iters=40)
+    elif kind == "dagmf":
+        prob = synth.dagmf_problem(4400, shape, iters=40)
+    else:
+        prob = synth.ishikawa_problem(5650, shape, nlev=7)
+    with gpu_problem(prob, storage=storage) as gp:
+        assert gp.variant == "fused_tma_dag"
+        if storage == 0:
+            compare(prob, gp, 40)
+        else:
+            gp.iterate(40)
+        u_t, q_t = gp.labels().cpu().numpy(), gp.flows().cpu().numpy()
+    with gpu_problem(prob, storage=storage, schedule=pfm.FUSED_PLAIN) as gp:
+        assert gp.variant == "fused"
+        gp.iterate(40)
+        tol = 1e-6 if storage == 0 else 2e-2
+        assert np.abs(gp.labels().cpu().numpy() - u_t).max() <= tol
+        assert np.abs(gp.flows().cpu().numpy() - q_t).max() <= tol
