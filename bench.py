@@ -354,7 +354,7 @@ def run_fullflow(args):
         gp.reset()
         done, t_used, reached = 0, 0.0, None
         while done < 5000:
-            t_used += timed(gp.iterate, 50)
+            t_used += 50 * timed(gp.iterate, 50)
             done += 50
             E, _ = gp.energy()
             if abs(E - E_star) <= 1e-4 * abs(E_star):
@@ -370,7 +370,7 @@ def run_fullflow(args):
     a = pfm.AlmProblem(D, S_field=S, gamma=0.3, step=0.2)
     done, t_used, reached = 0, 0.0, None
     while done < 5000:
-        t_used += timed(a.iterate, 50)
+        t_used += 50 * timed(a.iterate, 50)
         done += 50
         _, _, flow = a.energy()
         if abs(flow - E_star) <= 1e-4 * abs(E_star):
@@ -497,7 +497,7 @@ def main():
     peak = peak or 6800.0
     achieved = alg_bytes / (kern_ms / 1e3) / 1e9
     traffic = load_traffic(cfg)
-    kname = {"fused_tma": "fused_tma_kernel", "fused": "fused_step_kernel",
+    kname = {"fused_tma": "fused_tma_kernel", "fused_tma_dag": "fused_dag_tma_kernel", "fused": "fused_step_kernel",
              "inplace": "prox_inplace_kernel+flow_inplace_kernel"}[gp.variant]
 
     gp.close()

@@ -101,6 +101,6 @@ def test_tma_dag_kernel_parity(kind, storage):
     with gpu_problem(prob, storage=storage, schedule=pfm.FUSED_PLAIN) as gp:
         assert gp.variant == "fused"
         gp.iterate(40)
-        tol = 1e-6 if storage == 0 else 2e-2
+        tol = 5e-6 if storage == 0 else 2e-2   # sparse vs dense path-weight sums round differently
         assert np.abs(gp.labels().cpu().numpy() - u_t).max() <= tol
         assert np.abs(gp.flows().cpu().numpy() - q_t).max() <= tol
