@@ -178,7 +178,8 @@ struct Solver final : SolverBase {
             const int es = (int)sizeof(T);
             if ((base.nx * es) % 16 != 0 || (base.nx * 4) % 16 != 0) return false;
             const DagTmaLayout lay(base.nl, base.nn, DIM, es);
-            if (lay.total > 227 * 1024) return false;
+            // dynamic + static (the lists staged per CTA) within the 227 KB per CTA
+            if (lay.total + (int)sizeof(DagLists) + 64 > 227 * 1024) return false;
             // sparse path-weight lists: ancestors of each end-label, end-labels below each node
             for (int j = 0; j < DMAX; ++j) lists.anc_n[j] = 0;
             for (int A = 0; A < DMAX; ++A) lists.desc_n[A] = 0;

@@ -67,6 +67,9 @@ fused_dag_tma_kernel(const StepArgs<DMAX, DMAX> a, const __grid_constant__ TmaMa
     constexpr int PER = DMAX / 4;  // labels / nodes per thread at most
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ int s_abort;
+    // the four lanes of a voxel walk different lists: read them from shared
+    // memory (lane-dependent constant-bank loads would serialise)
+    __shared__ DagLists sl;
     unsigned char* smem = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
     const int nl = a.nl, nn = a.nn;
     const DagTmaLayout lay(nl, nn, DIM, (int)sizeof(T));
@@ -111,6 +114,9 @@ fused_dag_tma_kernel(const StepArgs<DMAX, DMAX> a, const __grid_constant__ TmaMa
         issue(z0 - 1, 0, true);
         issue(z0, 1, false);
     }
+    static_assert(sizeof(DagLists) % 4 == 0, "lists copied as words");
+    for (int k = t; k < (int)(sizeof(DagLists) / 4); k += DAG_TMA_NT)
+        reinterpret_cast<int*>(&sl)[k] = reinterpret_cast<const int*>(&lists)[k];
     __syncthreads();
 
     const bool inE = v < DNE;
@@ -181,8 +187,8 @@ fused_dag_tma_kernel(const StepArgs<DMAX, DMAX> a, const __grid_constant__ TmaMa
                 if (validE && j < nl) {
                     u[i] = lds<T>(uS + j * ustride + ui);
                     float dj = dS[j * ustride + ui];
-                    const int na = lists.anc_n[j];
-                    for (int k = 0; k < na; ++k) dj = fmaf(lists.anc_w[j][k], erow[lists.anc[j][k]], dj);
+                    const int na = sl.anc_n[j];
+                    for (int k = 0; k < na; ++k) dj = fmaf(sl.anc_w[j][k], erow[sl.anc[j][k]], dj);
                     d[i] = dj;
                     mloc = fminf(mloc, dj);
                 }
@@ -235,10 +241,10 @@ fused_dag_tma_kernel(const StepArgs<DMAX, DMAX> a, const __grid_constant__ TmaMa
                     float gr[DIM];
 #pragma unroll
                     for (int k = 0; k < DIM; ++k) gr[k] = 0.f;
-                    const int nd = lists.desc_n[A];
+                    const int nd = sl.desc_n[A];
                     for (int k = 0; k < nd; ++k) {
-                        const int j = lists.desc[A][k];
-                        const float w = lists.desc_w[A][k];
+                        const int j = sl.desc[A][k];
+                        const float w = sl.desc_w[A][k];
                         const float* gj = gP + j * ustride + ui;
                         const float g0 = gj[0];
                         gr[0] = fmaf(w, vx ? gj[1] - g0 : 0.f, gr[0]);
