@@ -40,6 +40,8 @@ CONFIGS = {
     "ishikawa": ((256, 256, 256), 8, "ishikawa", 0, 0),
     "continuation": ((128, 128, 128), 8, "potts3d", 0, 0),
     "fullflow": ((256, 256, 256), 8, "potts3d", 1, 0),
+    "diff": ((128, 128, 128), 6, "potts3d", 0, 0),
+    "capacity": ((512, 512, 512), 8, "potts3d", 1, 0),
 }
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_1501_07844_gb300", "csrc", f) for f in ("pfm_device.cuh", "pfm_tma.cuh")]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic.json")
@@ -384,6 +386,85 @@ def run_fullflow(args):
                       "config": {"workload": "potts3d 256^3 x 8", "voxels": n}, "results": out}), flush=True)
 
 
+def run_diff(args):
+    """Differentiable Potts: 128^3 x 6 labels, 100 unrolled iterations,
+    checkpoint every 10; loss = -sum log u_target.  Times the plain forward
+    (100 iterations), the differentiable forward (with checkpoints) and the
+    backward (segment recomputation + adjoint kernels)."""
+    import torch
+    import synth
+    import paper_1501_07844_gb300 as pfm
+    from paper_1501_07844_gb300.autograd import potts_solve
+    prob = synth.diff_problem(seed=5000)
+    D = torch.tensor(prob.D, device="cuda", requires_grad=True)
+    S = torch.tensor(prob.S_field, device="cuda", requires_grad=True)
+    tgt = torch.from_numpy(prob.truth.astype(np.int64)).cuda().unsqueeze(0)
+
+    def ev():
+        return torch.cuda.Event(enable_timing=True)
+    res = {}
+    for rep in range(2):  # first round warms up
+        gp = pfm.Problem(D.detach(), S_field=S.detach())
+        e0, e1 = ev(), ev()
+        e0.record()
+        gp.iterate(100)
+        e1.record()
+        torch.cuda.synchronize()
+        plain = e0.elapsed_time(e1)
+        gp.close()
+        e0, e1, e2 = ev(), ev(), ev()
+        e0.record()
+        u = potts_solve(D, S, iters=100, checkpoint_every=10)
+        L = -torch.log(torch.gather(u.double(), 0, tgt)).sum()
+        e1.record()
+        D.grad = None
+        S.grad = None
+        L.backward()
+        e2.record()
+        torch.cuda.synchronize()
+        res = {"plain_forward_ms": plain, "diff_forward_ms": e0.elapsed_time(e1), "backward_ms": e1.elapsed_time(e2),
+               "loss": float(L), "grad_D_norm": float(D.grad.norm()), "grad_S_norm": float(S.grad.norm())}
+    print(json.dumps({"metric": "differentiable Potts 128^3 x 6, 100 iterations, checkpoint 10 (ms)",
+                      "config": {"workload": "diff"}, "results": res}), flush=True)
+
+
+def run_capacity(args):
+    """Largest cube per model and storage that fits the GPU (from the
+    library's own footprint), and one measured in-place iteration on a
+    512^3 x 8 Potts volume (21 GB in place)."""
+    import torch
+    import paper_1501_07844_gb300 as pfm
+    from paper_1501_07844_gb300.binding import footprint
+    import synth
+    free, total = torch.cuda.mem_get_info()
+    budget = free * 0.95
+    out = {"device_bytes_free": free}
+    models = {"potts8": (8, [(-1, L, 1.0) for L in range(8)], True), "hmf12": (15, synth.hmf_tree(3, 4)[1], False)}
+    for mname, (nn, edges, field) in models.items():
+        for sname, sched, stor in (("inplace_f32", pfm.INPLACE, pfm.F32), ("inplace_bf16", pfm.INPLACE, pfm.BF16),
+                                   ("fused_f32", pfm.FUSED, pfm.F32), ("fused_bf16", pfm.FUSED, pfm.BF16)):
+            b, nbuf, _ = footprint((64, 64, 64), nn, edges, has_S_field=field, schedule=sched, storage=stor)
+            per_voxel = b / 64 ** 3
+            edge = int((budget / per_voxel) ** (1 / 3))
+            out["%s_%s" % (mname, sname)] = {"bytes_per_voxel": per_voxel, "max_cube_edge": edge}
+    prob = synth.potts3d_problem(seed=2000, nl=8, shape=(512, 512, 512))
+    gp = pfm.Problem(prob.D, S_field=prob.S_field, schedule=pfm.INPLACE)
+    del prob
+    gp.iterate(2)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    gp.iterate(5)
+    e1.record()
+    torch.cuda.synchronize()
+    E, P = gp.energy()
+    out["run_512_inplace_f32"] = {"ms_per_iter": e0.elapsed_time(e1) / 5, "E": E, "P": P,
+                                  "device_bytes": footprint((512, 512, 512), 8, [(-1, L, 1.0) for L in range(8)],
+                                                            has_S_field=True, schedule=pfm.INPLACE)[0]}
+    gp.close()
+    print(json.dumps({"metric": "largest volume per model in HBM (from pfm_footprint) + 512^3 in-place run",
+                      "config": {"workload": "capacity"}, "results": out}), flush=True)
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -400,6 +481,12 @@ def main():
         return
     if args.config == "fullflow":
         run_fullflow(args)
+        return
+    if args.config == "diff":
+        run_diff(args)
+        return
+    if args.config == "capacity":
+        run_capacity(args)
         return
 
     import torch
