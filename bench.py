@@ -93,11 +93,14 @@ def make_problem(cfg, seed, shape=None):
 
 def algorithmic_bytes_per_iter(prob, storage, schedule):
     """Minimum bytes one fused iteration must move: read u, D, q; write u, q
-    (d and the normaliser stay on chip), plus the S field once per voxel."""
+    (d and the normaliser stay on chip), plus the S field once per voxel.
+    Only nodes with nonzero capacity carry flow (a zero-capacity node's flow
+    is identically zero: the Ishikawa chain's end-labels)."""
     n = int(np.prod(prob.spatial))
     ts = 4 if storage == 0 else 2
     ndim = len(prob.spatial)
-    b = n * (prob.n_leaf * (2 * ts + 4) + prob.n_nodes * ndim * 2 * ts)
+    n_flow = prob.n_nodes if prob.s_node is None else int(np.count_nonzero(np.asarray(prob.s_node) > 0))
+    b = n * (prob.n_leaf * (2 * ts + 4) + n_flow * ndim * 2 * ts)
     if prob.S_field is not None:
         b += 4 * n
     return b

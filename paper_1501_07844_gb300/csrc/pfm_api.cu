@@ -462,7 +462,9 @@ pfm_status pfm_reset(pfm_problem* pb) {
     pb->cur = 0;
     PFM_CUDA(pfm::launch_init_labels(pb->u[0], pb->prm.storage, pb->nl, pb->n, pb->stream), "init u");
     pb->launches++;
-    PFM_CUDA(cudaMemsetAsync(pb->q[0], 0, (size_t)pb->nn * pb->ndim * pb->n * ts, pb->stream), "init q");
+    // both flow buffers: kernels that skip zero-capacity nodes leave their zeros in place
+    for (int k = 0; k < (pb->q[1] != pb->q[0] ? 2 : 1); ++k)
+        PFM_CUDA(cudaMemsetAsync(pb->q[k], 0, (size_t)pb->nn * pb->ndim * pb->n * ts, pb->stream), "init q");
     pb->iters = 0;
     return PFM_OK;
 }

@@ -141,7 +141,7 @@ struct Solver final : SolverBase {
             if (fused && dag_tma_ready && use_tma) {
                 const int k = (u_in == tma_u[0]) ? 0 : 1;
                 a.zc = zc < 1 ? 1 : zc;
-                const DagTmaLayout lay(a.nl, a.nn, DIM, (int)sizeof(T));
+                const DagTmaLayout lay(a.nl, lists.nf, DIM, (int)sizeof(T));
                 cudaError_t e = cudaFuncSetAttribute(fused_dag_tma_kernel<DIM, T>,
                                                      cudaFuncAttributeMaxDynamicSharedMemorySize, lay.total);
                 if (e != cudaSuccess) return e;
@@ -177,13 +177,19 @@ struct Solver final : SolverBase {
         if constexpr (kDagTmaCapable) {
             const int es = (int)sizeof(T);
             if ((base.nx * es) % 16 != 0 || (base.nx * 4) % 16 != 0) return false;
-            const DagTmaLayout lay(base.nl, base.nn, DIM, es);
+            // nodes from nf on have zero capacity: their flow is identically zero
+            int nf = 1;
+            for (int A = 0; A < base.nn; ++A)
+                if (base.s_node[A] > 0.f) nf = A + 1;
+            const DagTmaLayout lay(base.nl, nf, DIM, es);
             // dynamic + static (the lists staged per CTA) within the 227 KB per CTA
             if (lay.total + (int)sizeof(DagLists) + 64 > 227 * 1024) return false;
-            // sparse path-weight lists: ancestors of each end-label, end-labels below each node
+            // sparse path-weight lists over the flow-carrying nodes: ancestors of
+            // each end-label, end-labels below each node (e_A = 0 beyond nf)
+            lists.nf = nf;
             for (int j = 0; j < DMAX; ++j) lists.anc_n[j] = 0;
             for (int A = 0; A < DMAX; ++A) lists.desc_n[A] = 0;
-            for (int A = 0; A < base.nn; ++A)
+            for (int A = 0; A < nf; ++A)
                 for (int j = 0; j < base.nl; ++j)
                     if (base.W[A][j] != 0.f) {
                         lists.anc[j][lists.anc_n[j]] = (unsigned char)A;
@@ -198,7 +204,7 @@ struct Solver final : SolverBase {
             const unsigned long long st_t[3] = {nx * es, nx * ny * es, nx * ny * nz * es};
             const unsigned long long st_f[3] = {nx * 4, nx * ny * 4, nx * ny * nz * 4};
             const unsigned box_u[4] = {(unsigned)TMA_BX, (unsigned)DAG_UY, 1u, (unsigned)base.nl};
-            const unsigned box_q[4] = {(unsigned)qbx, (unsigned)DAG_QY, 1u, (unsigned)(DIM * base.nn)};
+            const unsigned box_q[4] = {(unsigned)qbx, (unsigned)DAG_QY, 1u, (unsigned)(DIM * nf)};
             const unsigned long long dims_s[3] = {nx, ny, nz};
             const unsigned box_s[3] = {(unsigned)FTX, (unsigned)DTY, 1u};
             for (int k = 0; k < 2; ++k) {

@@ -9,12 +9,17 @@
 //          into a per-voxel shared row, then d_j = D_j + sum_A W_(A,j) e_A for
 //          end-labels j = h, h+4, ... from the sparse ancestor list of j;
 //          the per-voxel minimum and normaliser are combined over the four
-//          lanes with two shuffles each;
+//          lanes with two shuffles each; the voxel's g_j then replace e in
+//          the row and thread h forms g_A = sum_j W_(A,j) g_j for its nodes;
 //   flow:  thread h of an owned voxel updates the flows of nodes A = h, h+4,
-//          ..., with grad g_A = sum_j W_(A,j) grad g_j over the sparse list of
-//          end-labels below A.
+//          ..., from the forward differences of g_A.
 // The lists hold every nonzero path weight W_(A,j) (W_(j,j) = 1), so the sums
-// equal the ordered top-down / bottom-up loops of Algorithm 2.
+// equal the ordered top-down / bottom-up loops of Algorithm 2; the gradient is
+// linear, so differencing the accumulated g_A equals accumulating the
+// end-labels' gradients.  Nodes whose capacity is zero carry no flow: the
+// nodes from `nf` on (a suffix of zero-capacity nodes, e.g. the end-labels of
+// the Ishikawa chain) are neither loaded, differentiated nor stored, and their
+// flow buffers keep the zeros every initialisation and import leaves there.
 #pragma once
 
 #include "pfm_tma.cuh"
@@ -36,22 +41,26 @@ struct DagLists {
     unsigned char desc_n[DMAX];         // end-labels below node A (incl. A itself if A is one)
     unsigned char desc[DMAX][DMAX];     // end-label indices
     float desc_w[DMAX][DMAX];           // W_(A,j)
+    int nf;                             // nodes 0 .. nf-1 carry flow (1 <= nf <= nn)
 };
 
-// Shared-memory layout, sized by the runtime label / node counts.
+// Shared-memory layout, sized by the runtime end-label count nl and the
+// count nf of flow-carrying nodes: per stage u, D, the nf nodes' flows and S;
+// two planes of g_A (nf nodes); one row of max(nl, nf) floats per voxel.
 struct DagTmaLayout {
-    int u_off, d_off, q_off, s_off, stage_bytes, g_off, e_off, bar_off, total;
+    int u_off, d_off, q_off, s_off, stage_bytes, g_off, e_off, row, bar_off, total;
     __host__ __device__ static int a128(int b) { return (b + 127) / 128 * 128; }
-    __host__ __device__ DagTmaLayout(int nl, int nn, int dim, int es) {
+    __host__ __device__ DagTmaLayout(int nl, int nf, int dim, int es) {
         const int qbx = FTX + 2 * (16 / es);
         u_off = 0;
         d_off = a128(nl * DAG_UY * TMA_BX * es);
         q_off = d_off + a128(nl * DAG_UY * TMA_BX * 4);
-        s_off = q_off + a128(dim * nn * DAG_QY * qbx * es);
+        s_off = q_off + a128(dim * nf * DAG_QY * qbx * es);
         stage_bytes = s_off + a128(FTX * DTY * 4);
         g_off = TMA_STAGES * stage_bytes;
-        e_off = g_off + a128(2 * nl * DAG_UY * TMA_BX * 4);
-        bar_off = e_off + a128(DNE * nn * 4);
+        e_off = g_off + a128(2 * nf * DAG_UY * TMA_BX * 4);
+        row = nl > nf ? nl : nf;
+        bar_off = e_off + a128(DNE * row * 4);
         total = bar_off + 64 + 128;
     }
 };
@@ -71,8 +80,8 @@ fused_dag_tma_kernel(const StepArgs<DMAX, DMAX> a, const __grid_constant__ TmaMa
     // memory (lane-dependent constant-bank loads would serialise)
     __shared__ DagLists sl;
     unsigned char* smem = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
-    const int nl = a.nl, nn = a.nn;
-    const DagTmaLayout lay(nl, nn, DIM, (int)sizeof(T));
+    const int nl = a.nl, nf = lists.nf;
+    const DagTmaLayout lay(nl, nf, DIM, (int)sizeof(T));
     const int t = threadIdx.x;
     const int h = t & 3;
     const int v = t >> 2;
@@ -86,13 +95,13 @@ fused_dag_tma_kernel(const StepArgs<DMAX, DMAX> a, const __grid_constant__ TmaMa
     const int has_S = a.S != nullptr;
     const unsigned bytes_u = (unsigned)(nl * ustride * sizeof(T));
     const unsigned bytes_d = (unsigned)(nl * ustride * 4);
-    const unsigned bytes_q = (unsigned)(DIM * nn * qstride * sizeof(T));
+    const unsigned bytes_q = (unsigned)(DIM * nf * qstride * sizeof(T));
     const unsigned bytes_s = has_S ? (unsigned)(FTX * DTY * 4) : 0u;
     const unsigned bar0 = smem_addr(smem + lay.bar_off);
     const float kexp = -a.inv_c * 1.4426950408889634f;
     float* gbuf = reinterpret_cast<float*>(smem + lay.g_off);
     float* ebuf = reinterpret_cast<float*>(smem + lay.e_off);
-    const int g_elems = nl * ustride;
+    const int g_elems = nf * ustride;
 
     auto stage_ptr = [&](int k) { return smem + k * lay.stage_bytes; };
     auto issue = [&](int p, int k, bool flows_only) {
@@ -128,7 +137,7 @@ fused_dag_tma_kernel(const StepArgs<DMAX, DMAX> a, const __grid_constant__ TmaMa
     const int mx = v % FTX, my = v / FTX;
     const int xm = x0 + mx, ym = y0 + my;
     const bool validM = inM && xm < a.nx && ym < a.ny;
-    float* erow = ebuf + (inE ? v : 0) * nn;
+    float* erow = ebuf + (inE ? v : 0) * lay.row;
 
     bool bad = false;
     int inflight_hi = z0;
@@ -166,7 +175,7 @@ fused_dag_tma_kernel(const StepArgs<DMAX, DMAX> a, const __grid_constant__ TmaMa
 #pragma unroll
                 for (int i = 0; i < PER; ++i) {
                     const int A = h + 4 * i;
-                    if (A < nn) {
+                    if (A < nf) {
                         const T* qx = qS + (A * DIM + 0) * qstride + qi;
                         const T* qy = qS + (A * DIM + 1) * qstride + qi;
                         float dv = (lds<T>(qx) - lds<T>(qx - 1)) + (lds<T>(qy) - lds<T>(qy - QBX));
@@ -207,6 +216,8 @@ fused_dag_tma_kernel(const StepArgs<DMAX, DMAX> a, const __grid_constant__ TmaMa
             }
             float sum = sloc + __shfl_xor_sync(0xffffffffu, sloc, 1);
             sum += __shfl_xor_sync(0xffffffffu, sum, 2);
+            // every lane has read its ancestors' e: the row now takes g_j
+            __syncwarp();
             if (validE) {
                 if (!((sum > 0.f) && (sum <= 3.0e38f))) bad = true;
                 const float inv = 1.0f / sum;
@@ -216,8 +227,22 @@ fused_dag_tma_kernel(const StepArgs<DMAX, DMAX> a, const __grid_constant__ TmaMa
                     const int j = h + 4 * i;
                     if (j < nl) {
                         const float un = u[i] * inv;
-                        gC[j * ustride + ui] = a.literal ? u[i] : un;
+                        erow[j] = a.literal ? u[i] : un;
                         if (ownerE && p < z1) stv<T>(uout + (long long)j * n + i0, un);
+                    }
+                }
+            }
+            __syncwarp();
+            // bottom-up accumulation g_A = sum_j W_(A,j) g_j (Algorithm 2)
+            if (validE) {
+#pragma unroll
+                for (int i = 0; i < PER; ++i) {
+                    const int A = h + 4 * i;
+                    if (A < nf) {
+                        const int nd = sl.desc_n[A];
+                        float g = 0.f;
+                        for (int k = 0; k < nd; ++k) g = fmaf(sl.desc_w[A][k], erow[sl.desc[A][k]], g);
+                        gC[A * ustride + ui] = g;
                     }
                 }
             }
@@ -237,20 +262,13 @@ fused_dag_tma_kernel(const StepArgs<DMAX, DMAX> a, const __grid_constant__ TmaMa
 #pragma unroll
             for (int i = 0; i < PER; ++i) {
                 const int A = h + 4 * i;
-                if (A < nn) {
+                if (A < nf) {
+                    const float* gA = gP + A * ustride + ui;
+                    const float g0 = gA[0];
                     float gr[DIM];
-#pragma unroll
-                    for (int k = 0; k < DIM; ++k) gr[k] = 0.f;
-                    const int nd = sl.desc_n[A];
-                    for (int k = 0; k < nd; ++k) {
-                        const int j = sl.desc[A][k];
-                        const float w = sl.desc_w[A][k];
-                        const float* gj = gP + j * ustride + ui;
-                        const float g0 = gj[0];
-                        gr[0] = fmaf(w, vx ? gj[1] - g0 : 0.f, gr[0]);
-                        gr[1] = fmaf(w, vy ? gj[TMA_BX] - g0 : 0.f, gr[1]);
-                        if constexpr (DIM == 3) gr[2] = fmaf(w, vz ? gC[j * ustride + ui] - g0 : 0.f, gr[2]);
-                    }
+                    gr[0] = vx ? gA[1] - g0 : 0.f;
+                    gr[1] = vy ? gA[TMA_BX] - g0 : 0.f;
+                    if constexpr (DIM == 3) gr[2] = vz ? gC[A * ustride + ui] - g0 : 0.f;
                     float yv[DIM];
                     yv[0] = lds<T>(qP + (A * DIM + 0) * qstride + qi) - a.ctau * gr[0];
                     yv[1] = lds<T>(qP + (A * DIM + 1) * qstride + qi) - a.ctau * gr[1];
