@@ -106,9 +106,9 @@ def algorithmic_bytes_per_iter(prob, storage, schedule):
     return b
 
 
-def kernel_sha():
+def kernel_sha(sources=None):
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
+    for f in sources or KERNEL_SOURCES:
         h.update(open(f, "rb").read())
     return h.hexdigest()[:16]
 
@@ -121,7 +121,10 @@ def load_traffic(cfg):
     except (OSError, ValueError):
         return None
     e = t.get(cfg)
-    if not e or e.get("kernel_source_sha") != kernel_sha():
+    if not e:
+        return None
+    src = [os.path.join(ROOT, "paper_1501_07844_gb300", "csrc", f) for f in e.get("sources", [])]
+    if e.get("kernel_source_sha") != kernel_sha(src or None):
         return None
     return e.get("dram_bytes_per_launch")
 
