@@ -135,6 +135,26 @@ __device__ __forceinline__ float ex2_approx(float x) {
     return y;
 }
 
+// 1/x by the hardware approximation (at most 1 ulp from the rounded
+// quotient) for normal x; subnormal, zero and NaN x take the IEEE division.
+__device__ __forceinline__ float rcp_fast(float x) {
+    if (x >= 1.17549435e-38f) {
+        float y;
+        asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+        return y;
+    }
+    return 1.0f / x;
+}
+
+// 1/sqrt(x) by the hardware approximation (relative error below 2^-22);
+// a subnormal x counts as 0 and gives +inf, which the projection maps to
+// the unscaled vector (its length is far below any positive capacity).
+__device__ __forceinline__ float rsqrt_approx(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // Branch-free projection onto {|y| <= s} (s >= 0): scale min(1, s/|y|), with
 // s = 0 mapping every y to 0.
 template <int DIM>
@@ -146,7 +166,7 @@ __device__ __forceinline__ void project_nb(float (&y)[DIM], float s, int aniso) 
         float r2 = 0.f;
 #pragma unroll
         for (int k = 0; k < DIM; ++k) r2 = fmaf(y[k], y[k], r2);
-        const float f = s > 0.f ? fminf(1.0f, s * rsqrtf(r2)) : 0.f;
+        const float f = s > 0.f ? fminf(1.0f, s * rsqrt_approx(r2)) : 0.f;
 #pragma unroll
         for (int k = 0; k < DIM; ++k) y[k] *= f;
     }
@@ -214,44 +234,54 @@ fused_tma_kernel(const StepArgs<MAXL, MAXL> a, const __grid_constant__ TmaMaps m
     }
     __syncthreads();
 
-    // prox-phase voxel of this thread pair (halo-extended tile, row-major 33 x 9)
+    // Voxel of this thread pair on the halo-extended 33 x 9 tile, owned voxels
+    // first (v < 256: the 32 x 8 tile, row-major), then the y-halo row (ey = 8)
+    // and the x-halo column (ex = 32).  The same pair runs the prox of plane p
+    // and the flow step of plane p-1 at its voxel, so the field g at its own
+    // voxel (both planes) stays in registers and only the x+1 / y+1
+    // neighbours' g goes through shared memory: one barrier per plane.
     const bool inE = v < FNE;
-    const int ex = v % FEX, ey = v / FEX;
+    const int ex = v < FTX * FTY ? (v & (FTX - 1)) : v < FTX * FTY + FTX ? v - FTX * FTY : FTX;
+    const int ey = v < FTX * FTY ? v / FTX : v < FTX * FTY + FTX ? FTY : v - (FTX * FTY + FTX);
     const int xe = x0 + ex, ye = y0 + ey;
     const bool validE = inE && xe < a.nx && ye < a.ny;
-    const bool ownerE = validE && ex < FTX && ey < FTY;
-    // flow-phase voxel (owned 32 x 8 tile, row-major)
-    const bool inM = v < FTX * FTY;
-    const int mx = v % FTX, my = v / FTX;
-    const int xm = x0 + mx, ym = y0 + my;
-    const bool validM = inM && xm < a.nx && ym < a.ny;
+    const bool ownerE = validE && v < FTX * FTY;
+    const int ui = ey * TMA_BX + ex;
+    const int qi = (ey + 1) * Lay::QBX + (ex + Lay::QOFF);
+    // forward differences are zero at the last index: zero steps there (the
+    // g slots outside the grid hold zeros, so a zero step never meets a NaN)
+    const float cx = xe < a.nx - 1 ? a.ctau : 0.f;
+    const float cy = ye < a.ny - 1 ? a.ctau : 0.f;
 
+    for (int k = t; k < 2 * Lay::g_elems; k += TMA_NT) gbuf[k] = 0.f;
     float cap[HL];  // per-label capacity factors of this thread's label half
 #pragma unroll
     for (int i = 0; i < HL; ++i) cap[i] = a.s_node[half_label(h, i)];
+    float gprev[HL], gcur[HL];  // g at this voxel, planes p-1 and p
+#pragma unroll
+    for (int i = 0; i < HL; ++i) gprev[i] = gcur[i] = 0.f;
+    __syncthreads();
     bool bad = false;
     double accE = 0.0, accP = 0.0;
     int inflight_hi = z0;  // highest plane issued
     for (int p = z0; p <= z1; ++p) {
         const int s = p - z0 + 1;
         const int cs = s % 3, ps = (s + 2) % 3, ns = (s + 1) % 3;
+        // stage ns held plane p-2, last read before the previous barrier
         if (t == 0 && p + 1 <= z1 && p + 1 < a.nz) {
             issue(p + 1, ns, false);
             inflight_hi = p + 1;
         }
         unsigned char* cst = stage_ptr(cs);
         unsigned char* pst = stage_ptr(ps);
-        float* gC = gbuf + (p & 1) * Lay::g_elems;        // g of plane p (written now)
-        const float* gP = gbuf + ((p + 1) & 1) * Lay::g_elems;  // g of plane p-1
+        float* gC = gbuf + (p & 1) * Lay::g_elems;              // g of plane p (written now)
+        const float* gP = gbuf + ((p + 1) & 1) * Lay::g_elems;  // g of plane p-1 (neighbours)
+        // each thread waits for the stages itself; a timeout is raised to the
+        // whole CTA at the end-of-plane barrier
         bool ok = true;
         if (p == z0) ok = mbar_wait_bounded(bar0 + 8 * ps, 0u);
         if (p < a.nz && ok) ok = mbar_wait_bounded(bar0 + 8 * cs, (unsigned)((s / 3) & 1));
-        if (!ok) {
-            atomicOr(a.flags, FLAG_TIMEOUT);
-            s_abort = 1;
-        }
-        __syncthreads();
-        if (s_abort) break;
+        if (!ok) atomicOr(a.flags, FLAG_TIMEOUT);
 
         // ---- label prox of plane p on the halo-extended tile (uniform branch)
         if (p < a.nz) {
@@ -259,8 +289,6 @@ fused_tma_kernel(const StepArgs<MAXL, MAXL> a, const __grid_constant__ TmaMaps m
             const float* dS = reinterpret_cast<const float*>(cst + Lay::d_off);
             const T* qS = reinterpret_cast<const T*>(cst + Lay::q_off);
             const T* qP = reinterpret_cast<const T*>(pst + Lay::q_off);
-            const int ui = ey * TMA_BX + ex;
-            const int qi = (ey + 1) * Lay::QBX + (ex + Lay::QOFF);
             // Divergence without boundary tests: the normal flow component at
             // the last index of each axis is an invariant zero of the stored
             // state (zero at initialisation, kept by the flow step, enforced by
@@ -302,49 +330,43 @@ fused_tma_kernel(const StepArgs<MAXL, MAXL> a, const __grid_constant__ TmaMaps m
             const float sum = sloc + __shfl_xor_sync(0xffffffffu, sloc, 1);
             if (validE) {
                 if (!((sum > 0.f) && (sum <= 3.0e38f))) bad = true;
-                const float inv = 1.0f / sum;
+                const float inv = rcp_fast(sum);
                 const long long i0 = (long long)p * plane + (long long)ye * a.nx + xe;
 #pragma unroll
                 for (int i = 0; i < HL; ++i) {
                     const int j = half_label(h, i);
                     if (EXACT || j < nl) {
                         const float un = u[i] * inv;
-                        gC[j * ustride + ui] = a.literal ? u[i] : un;
+                        gcur[i] = a.literal ? u[i] : un;
+                        gC[j * ustride + ui] = gcur[i];
                         if (ownerE && p < z1) stv<T>(uout + (long long)j * n + i0, un);
                     }
                 }
             }
         }
-        __syncthreads();
 
-        // ---- flow step of plane p-1 (one label half per thread)
+        // ---- flow step of plane p-1 at the owned voxel (one label half per
+        // thread): g of plane p-1 at x+1 and y+1 from the previous plane's
+        // prox (visible since the last barrier), own g of planes p-1 and p
+        // from registers
         const int pm = p - 1;
-        if (pm >= z0 && validM) {
+        if (pm >= z0 && ownerE) {
             const T* qP = reinterpret_cast<const T*>(pst + Lay::q_off);
             const float* sP = reinterpret_cast<const float*>(pst + Lay::s_off);
-            const int ui = my * TMA_BX + mx;
-            const int qi = (my + 1) * Lay::QBX + (mx + Lay::QOFF);
-            const float sf = has_S ? sP[my * FTX + mx] : 1.0f;
-            const long long i0 = (long long)pm * plane + (long long)ym * a.nx + xm;
-            // forward differences are zero at the last index; the neighbour's g
-            // slot beyond the grid is never written, so select, never multiply
-            const bool vx = xm < a.nx - 1, vy = ym < a.ny - 1, vz = pm < a.nz - 1;
-            const float cx = vx ? a.ctau : 0.f;
-            const float cy = vy ? a.ctau : 0.f;
-            const float cz = vz ? a.ctau : 0.f;
+            const float sf = has_S ? sP[ey * FTX + ex] : 1.0f;
+            const long long i0 = (long long)pm * plane + (long long)ye * a.nx + xe;
+            const float cz = pm < a.nz - 1 ? a.ctau : 0.f;
             float eloc = 0.f;
 #pragma unroll
             for (int i = 0; i < HL; ++i) {
                 const int j = half_label(h, i);
                 if (EXACT || j < nl) {
                     const float* gj = gP + j * ustride;
-                    const float g0 = gj[ui];
+                    const float g0 = gprev[i];
                     float yv[DIM];
-                    yv[0] = lds<T>(qP + (j * DIM + 0) * qstride + qi) - a.ctau * (vx ? gj[ui + 1] - g0 : 0.f);
-                    yv[1] = lds<T>(qP + (j * DIM + 1) * qstride + qi) - a.ctau * (vy ? gj[ui + TMA_BX] - g0 : 0.f);
-                    if constexpr (DIM == 3)
-                        yv[2] = lds<T>(qP + (j * DIM + 2) * qstride + qi) -
-                                a.ctau * (vz ? gC[j * ustride + ui] - g0 : 0.f);
+                    yv[0] = lds<T>(qP + (j * DIM + 0) * qstride + qi) - cx * (gj[ui + 1] - g0);
+                    yv[1] = lds<T>(qP + (j * DIM + 1) * qstride + qi) - cy * (gj[ui + TMA_BX] - g0);
+                    if constexpr (DIM == 3) yv[2] = lds<T>(qP + (j * DIM + 2) * qstride + qi) - cz * (gcur[i] - g0);
                     const float sj = cap[i] * sf;
                     if constexpr (WITH_E) {
                         // E of plane p-1 on the input labelling (staged u of planes p-1 and p)
@@ -379,10 +401,16 @@ fused_tma_kernel(const StepArgs<MAXL, MAXL> a, const __grid_constant__ TmaMaps m
             }
             if constexpr (WITH_E) accE += (double)eloc;
         }
+#pragma unroll
+        for (int i = 0; i < HL; ++i) gprev[i] = gcur[i];
         // order this plane's shared-memory accesses before the TMA that
-        // refills stage ps at the next step
+        // refills a stage at the next step; one barrier per plane, which also
+        // carries a timed-out wait of any thread to the whole CTA
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
+        if (__syncthreads_or(!ok)) {
+            if (t == 0) s_abort = 1;
+            break;
+        }
     }
     if (bad) atomicOr(a.flags, FLAG_NONFINITE);
     if (s_abort && t == 0) {

@@ -128,22 +128,41 @@ fused_dag_tma_kernel(const StepArgs<DMAX, DMAX> a, const __grid_constant__ TmaMa
         reinterpret_cast<int*>(&sl)[k] = reinterpret_cast<const int*>(&lists)[k];
     __syncthreads();
 
+    // Voxel of this thread quad on the halo-extended 33 x 5 tile, owned voxels
+    // first (v < 128: the 32 x 4 tile), then the y-halo row (ey = 4) and the
+    // x-halo column (ex = 32).  The quad runs the prox of plane p and the flow
+    // step of plane p-1 at its voxel, so g_A at its own voxel (both planes)
+    // stays in registers and only the x+1 / y+1 neighbours' g_A goes through
+    // shared memory: one barrier per plane.
     const bool inE = v < DNE;
-    const int ex = v % FEX, ey = v / FEX;
+    const int ex = v < FTX * DTY ? (v & (FTX - 1)) : v < FTX * DTY + FTX ? v - FTX * DTY : FTX;
+    const int ey = v < FTX * DTY ? v / FTX : v < FTX * DTY + FTX ? DTY : v - (FTX * DTY + FTX);
     const int xe = x0 + ex, ye = y0 + ey;
     const bool validE = inE && xe < a.nx && ye < a.ny;
-    const bool ownerE = validE && ex < FTX && ey < DTY;
-    const bool inM = v < FTX * DTY;
-    const int mx = v % FTX, my = v / FTX;
-    const int xm = x0 + mx, ym = y0 + my;
-    const bool validM = inM && xm < a.nx && ym < a.ny;
+    const bool ownerE = validE && v < FTX * DTY;
     float* erow = ebuf + (inE ? v : 0) * lay.row;
+    const int ui = ey * TMA_BX + ex;
+    const int qi = (ey + 1) * QBX + (ex + QOFF);
+    // zero steps at the last index (the g slots outside the grid hold zeros)
+    const float cx = xe < a.nx - 1 ? a.ctau : 0.f;
+    const float cy = ye < a.ny - 1 ? a.ctau : 0.f;
 
+    for (int k = t; k < 2 * g_elems; k += DAG_TMA_NT) gbuf[k] = 0.f;
+    // capacities of this thread's nodes, read once (lane-dependent parameter
+    // reads serialise)
+    float cap[PER], gprev[PER], gcur[PER];
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+        cap[i] = (h + 4 * i < nf) ? a.s_node[h + 4 * i] : 0.f;
+        gprev[i] = gcur[i] = 0.f;
+    }
+    __syncthreads();
     bool bad = false;
     int inflight_hi = z0;
     for (int p = z0; p <= z1; ++p) {
         const int s = p - z0 + 1;
         const int cs = s % 3, ps = (s + 2) % 3, ns = (s + 1) % 3;
+        // stage ns held plane p-2, last read before the previous barrier
         if (t == 0 && p + 1 <= z1 && p + 1 < a.nz) {
             issue(p + 1, ns, false);
             inflight_hi = p + 1;
@@ -152,23 +171,17 @@ fused_dag_tma_kernel(const StepArgs<DMAX, DMAX> a, const __grid_constant__ TmaMa
         unsigned char* pst = stage_ptr(ps);
         float* gC = gbuf + (p & 1) * g_elems;
         const float* gP = gbuf + ((p + 1) & 1) * g_elems;
+        // each thread waits itself; a timeout reaches the CTA at the barrier
         bool ok = true;
         if (p == z0) ok = mbar_wait_bounded(bar0 + 8 * ps, 0u);
         if (p < a.nz && ok) ok = mbar_wait_bounded(bar0 + 8 * cs, (unsigned)((s / 3) & 1));
-        if (!ok) {
-            atomicOr(a.flags, FLAG_TIMEOUT);
-            s_abort = 1;
-        }
-        __syncthreads();
-        if (s_abort) break;
+        if (!ok) atomicOr(a.flags, FLAG_TIMEOUT);
 
         if (p < a.nz) {
             const T* uS = reinterpret_cast<const T*>(cst + lay.u_off);
             const float* dS = reinterpret_cast<const float*>(cst + lay.d_off);
             const T* qS = reinterpret_cast<const T*>(cst + lay.q_off);
             const T* qP = reinterpret_cast<const T*>(pst + lay.q_off);
-            const int ui = ey * TMA_BX + ex;
-            const int qi = (ey + 1) * QBX + (ex + QOFF);
             // divergence of this thread's nodes (no boundary tests: the last-index
             // normal flow is an invariant zero, the box is zero-filled outside)
             if (validE) {
@@ -220,7 +233,7 @@ fused_dag_tma_kernel(const StepArgs<DMAX, DMAX> a, const __grid_constant__ TmaMa
             __syncwarp();
             if (validE) {
                 if (!((sum > 0.f) && (sum <= 3.0e38f))) bad = true;
-                const float inv = 1.0f / sum;
+                const float inv = rcp_fast(sum);
                 const long long i0 = (long long)p * plane + (long long)ye * a.nx + xe;
 #pragma unroll
                 for (int i = 0; i < PER; ++i) {
@@ -242,46 +255,47 @@ fused_dag_tma_kernel(const StepArgs<DMAX, DMAX> a, const __grid_constant__ TmaMa
                         const int nd = sl.desc_n[A];
                         float g = 0.f;
                         for (int k = 0; k < nd; ++k) g = fmaf(sl.desc_w[A][k], erow[sl.desc[A][k]], g);
+                        gcur[i] = g;
                         gC[A * ustride + ui] = g;
                     }
                 }
             }
         }
-        __syncthreads();
 
+        // flow step of plane p-1 at the owned voxel: neighbours' g_A of plane
+        // p-1 from shared memory (visible since the last barrier), own g_A of
+        // planes p-1 and p from registers
         const int pm = p - 1;
-        if (pm >= z0 && validM) {
+        if (pm >= z0 && ownerE) {
             const T* qP = reinterpret_cast<const T*>(pst + lay.q_off);
             const float* sP = reinterpret_cast<const float*>(pst + lay.s_off);
-            const int ui = my * TMA_BX + mx;
-            const int qi = (my + 1) * QBX + (mx + QOFF);
-            const float sf = has_S ? sP[my * FTX + mx] : 1.0f;
-            const long long i0 = (long long)pm * plane + (long long)ym * a.nx + xm;
-            // the neighbour's g slot beyond the grid is never written: select
-            const bool vx = xm < a.nx - 1, vy = ym < a.ny - 1, vz = pm < a.nz - 1;
+            const float sf = has_S ? sP[ey * FTX + ex] : 1.0f;
+            const long long i0 = (long long)pm * plane + (long long)ye * a.nx + xe;
+            const float cz = pm < a.nz - 1 ? a.ctau : 0.f;
 #pragma unroll
             for (int i = 0; i < PER; ++i) {
                 const int A = h + 4 * i;
                 if (A < nf) {
                     const float* gA = gP + A * ustride + ui;
-                    const float g0 = gA[0];
-                    float gr[DIM];
-                    gr[0] = vx ? gA[1] - g0 : 0.f;
-                    gr[1] = vy ? gA[TMA_BX] - g0 : 0.f;
-                    if constexpr (DIM == 3) gr[2] = vz ? gC[A * ustride + ui] - g0 : 0.f;
+                    const float g0 = gprev[i];
                     float yv[DIM];
-                    yv[0] = lds<T>(qP + (A * DIM + 0) * qstride + qi) - a.ctau * gr[0];
-                    yv[1] = lds<T>(qP + (A * DIM + 1) * qstride + qi) - a.ctau * gr[1];
-                    if constexpr (DIM == 3) yv[2] = lds<T>(qP + (A * DIM + 2) * qstride + qi) - a.ctau * gr[2];
-                    project_nb<DIM>(yv, a.s_node[A] * sf, a.aniso);
+                    yv[0] = lds<T>(qP + (A * DIM + 0) * qstride + qi) - cx * (gA[1] - g0);
+                    yv[1] = lds<T>(qP + (A * DIM + 1) * qstride + qi) - cy * (gA[TMA_BX] - g0);
+                    if constexpr (DIM == 3) yv[2] = lds<T>(qP + (A * DIM + 2) * qstride + qi) - cz * (gcur[i] - g0);
+                    project_nb<DIM>(yv, cap[i] * sf, a.aniso);
                     T* qa = qout + (long long)A * DIM * n + i0;
 #pragma unroll
                     for (int k = 0; k < DIM; ++k) stv<T>(qa + k * n, yv[k]);
                 }
             }
         }
+#pragma unroll
+        for (int i = 0; i < PER; ++i) gprev[i] = gcur[i];
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
+        if (__syncthreads_or(!ok)) {
+            if (t == 0) s_abort = 1;
+            break;
+        }
     }
     if (bad) atomicOr(a.flags, FLAG_NONFINITE);
     if (s_abort && t == 0) {
