@@ -225,12 +225,22 @@ fused_tma_kernel(const StepArgs<MAXL, MAXL> a, const __grid_constant__ TmaMaps m
         }
     };
 
+    // Without the energy pass an iteration reads only the stage of its own
+    // plane (the voxel's flows and S of the previous plane are kept in
+    // registers), so the ring runs two planes ahead; the energy variant also
+    // reads the previous plane's staged u and D and runs one plane ahead.
+    constexpr bool kDeep = !WITH_E;
+    int inflight_hi = z0;  // highest plane issued
     if (t == 0) {
         for (int k = 0; k < TMA_STAGES; ++k) mbar_init(bar0 + 8 * k, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         s_abort = 0;
         issue(z0 - 1, 0, true);   // flows of plane z0-1 (zero-filled when z0 = 0)
         issue(z0, 1, false);
+        if (kDeep && z0 + 1 <= z1 && z0 + 1 < a.nz) {
+            issue(z0 + 1, 2, false);
+            inflight_hi = z0 + 1;
+        }
     }
     __syncthreads();
 
@@ -257,38 +267,64 @@ fused_tma_kernel(const StepArgs<MAXL, MAXL> a, const __grid_constant__ TmaMaps m
     float cap[HL];  // per-label capacity factors of this thread's label half
 #pragma unroll
     for (int i = 0; i < HL; ++i) cap[i] = a.s_node[half_label(h, i)];
-    float gprev[HL], gcur[HL];  // g at this voxel, planes p-1 and p
+    // this voxel's state carried from plane p-1 to plane p: g, the three flow
+    // components (the z one also closes the divergence of plane p) and S
+    float gprev[HL], gcur[HL], qxp[HL], qyp[HL], qzp[HL];
+    float sprev = 1.0f;
 #pragma unroll
-    for (int i = 0; i < HL; ++i) gprev[i] = gcur[i] = 0.f;
-    __syncthreads();
+    for (int i = 0; i < HL; ++i) gprev[i] = gcur[i] = qxp[i] = qyp[i] = qzp[i] = 0.f;
+    // flows of plane z0-1 (z component only: its x / y flow steps belong to
+    // the previous z-chunk)
+    bool ok = mbar_wait_bounded(bar0, 0u);
+    if constexpr (DIM == 3) {
+        if (ok && validE) {
+            const T* q0 = reinterpret_cast<const T*>(stage_ptr(0) + Lay::q_off);
+#pragma unroll
+            for (int i = 0; i < HL; ++i) {
+                const int j = half_label(h, i);
+                if (EXACT || j < nl) qzp[i] = lds<T>(q0 + (j * DIM + 2) * qstride + qi);
+            }
+        }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    if (__syncthreads_or(!ok)) {
+        if (t == 0) atomicOr(a.flags, FLAG_TIMEOUT);
+        s_abort = 1;
+    }
     bool bad = false;
     double accE = 0.0, accP = 0.0;
-    int inflight_hi = z0;  // highest plane issued
-    for (int p = z0; p <= z1; ++p) {
+    int p_stop = z0 - 1;  // first plane whose stage may still be in flight at an abort
+    for (int p = z0; p <= z1 && !s_abort; ++p) {
         const int s = p - z0 + 1;
         const int cs = s % 3, ps = (s + 2) % 3, ns = (s + 1) % 3;
-        // stage ns held plane p-2, last read before the previous barrier
-        if (t == 0 && p + 1 <= z1 && p + 1 < a.nz) {
-            issue(p + 1, ns, false);
-            inflight_hi = p + 1;
+        // the stage refilled here was last read before the previous barrier
+        if (t == 0) {
+            const int pf = kDeep ? p + 2 : p + 1;
+            if (pf <= z1 && pf < a.nz) {
+                issue(pf, kDeep ? ps : ns, false);
+                inflight_hi = pf;
+            }
         }
         unsigned char* cst = stage_ptr(cs);
         unsigned char* pst = stage_ptr(ps);
         float* gC = gbuf + (p & 1) * Lay::g_elems;              // g of plane p (written now)
         const float* gP = gbuf + ((p + 1) & 1) * Lay::g_elems;  // g of plane p-1 (neighbours)
-        // each thread waits for the stages itself; a timeout is raised to the
+        // each thread waits for its stage itself; a timeout is raised to the
         // whole CTA at the end-of-plane barrier
-        bool ok = true;
-        if (p == z0) ok = mbar_wait_bounded(bar0 + 8 * ps, 0u);
-        if (p < a.nz && ok) ok = mbar_wait_bounded(bar0 + 8 * cs, (unsigned)((s / 3) & 1));
+        ok = true;
+        if (p < a.nz) ok = mbar_wait_bounded(bar0 + 8 * cs, (unsigned)((s / 3) & 1));
         if (!ok) atomicOr(a.flags, FLAG_TIMEOUT);
+        float qxc[HL], qyc[HL], qzc[HL];
+#pragma unroll
+        for (int i = 0; i < HL; ++i) qxc[i] = qyc[i] = qzc[i] = 0.f;
+        float scur = 1.0f;
 
         // ---- label prox of plane p on the halo-extended tile (uniform branch)
         if (p < a.nz) {
             const T* uS = reinterpret_cast<const T*>(cst + Lay::u_off);
             const float* dS = reinterpret_cast<const float*>(cst + Lay::d_off);
             const T* qS = reinterpret_cast<const T*>(cst + Lay::q_off);
-            const T* qP = reinterpret_cast<const T*>(pst + Lay::q_off);
+            if (has_S && ownerE) scur = reinterpret_cast<const float*>(cst + Lay::s_off)[ey * FTX + ex];
             // Divergence without boundary tests: the normal flow component at
             // the last index of each axis is an invariant zero of the stored
             // state (zero at initialisation, kept by the flow step, enforced by
@@ -304,9 +340,13 @@ fused_tma_kernel(const StepArgs<MAXL, MAXL> a, const __grid_constant__ TmaMaps m
                     u[i] = lds<T>(uS + j * ustride + ui);
                     const T* qx = qS + (j * DIM + 0) * qstride + qi;
                     const T* qy = qS + (j * DIM + 1) * qstride + qi;
-                    float dv = (lds<T>(qx) - lds<T>(qx - 1)) + (lds<T>(qy) - lds<T>(qy - Lay::QBX));
-                    if constexpr (DIM == 3)
-                        dv += lds<T>(qS + (j * DIM + 2) * qstride + qi) - lds<T>(qP + (j * DIM + 2) * qstride + qi);
+                    qxc[i] = lds<T>(qx);
+                    qyc[i] = lds<T>(qy);
+                    float dv = (qxc[i] - lds<T>(qx - 1)) + (qyc[i] - lds<T>(qy - Lay::QBX));
+                    if constexpr (DIM == 3) {
+                        qzc[i] = lds<T>(qS + (j * DIM + 2) * qstride + qi);
+                        dv += qzc[i] - qzp[i];
+                    }
                     d[i] = dS[j * ustride + ui] + dv;
                     mloc = fminf(mloc, d[i]);
                 }
@@ -351,9 +391,7 @@ fused_tma_kernel(const StepArgs<MAXL, MAXL> a, const __grid_constant__ TmaMaps m
         // from registers
         const int pm = p - 1;
         if (pm >= z0 && ownerE) {
-            const T* qP = reinterpret_cast<const T*>(pst + Lay::q_off);
-            const float* sP = reinterpret_cast<const float*>(pst + Lay::s_off);
-            const float sf = has_S ? sP[ey * FTX + ex] : 1.0f;
+            const float sf = sprev;
             const long long i0 = (long long)pm * plane + (long long)ye * a.nx + xe;
             const float cz = pm < a.nz - 1 ? a.ctau : 0.f;
             float eloc = 0.f;
@@ -364,9 +402,9 @@ fused_tma_kernel(const StepArgs<MAXL, MAXL> a, const __grid_constant__ TmaMaps m
                     const float* gj = gP + j * ustride;
                     const float g0 = gprev[i];
                     float yv[DIM];
-                    yv[0] = lds<T>(qP + (j * DIM + 0) * qstride + qi) - cx * (gj[ui + 1] - g0);
-                    yv[1] = lds<T>(qP + (j * DIM + 1) * qstride + qi) - cy * (gj[ui + TMA_BX] - g0);
-                    if constexpr (DIM == 3) yv[2] = lds<T>(qP + (j * DIM + 2) * qstride + qi) - cz * (gcur[i] - g0);
+                    yv[0] = qxp[i] - cx * (gj[ui + 1] - g0);
+                    yv[1] = qyp[i] - cy * (gj[ui + TMA_BX] - g0);
+                    if constexpr (DIM == 3) yv[2] = qzp[i] - cz * (gcur[i] - g0);
                     const float sj = cap[i] * sf;
                     if constexpr (WITH_E) {
                         // E of plane p-1 on the input labelling (staged u of planes p-1 and p)
@@ -402,11 +440,18 @@ fused_tma_kernel(const StepArgs<MAXL, MAXL> a, const __grid_constant__ TmaMaps m
             if constexpr (WITH_E) accE += (double)eloc;
         }
 #pragma unroll
-        for (int i = 0; i < HL; ++i) gprev[i] = gcur[i];
+        for (int i = 0; i < HL; ++i) {
+            gprev[i] = gcur[i];
+            qxp[i] = qxc[i];
+            qyp[i] = qyc[i];
+            qzp[i] = qzc[i];
+        }
+        sprev = scur;
         // order this plane's shared-memory accesses before the TMA that
         // refills a stage at the next step; one barrier per plane, which also
         // carries a timed-out wait of any thread to the whole CTA
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        p_stop = p;
         if (__syncthreads_or(!ok)) {
             if (t == 0) s_abort = 1;
             break;
@@ -414,8 +459,10 @@ fused_tma_kernel(const StepArgs<MAXL, MAXL> a, const __grid_constant__ TmaMaps m
     }
     if (bad) atomicOr(a.flags, FLAG_NONFINITE);
     if (s_abort && t == 0) {
-        // bounded drain of this CTA's copies still in flight
-        for (int p = z0 - 1; p <= inflight_hi; ++p) {
+        // bounded drain of this CTA's copies that may still be in flight: the
+        // plane whose wait gave up and every plane issued after it (planes
+        // consumed earlier are complete and their stages may have been refilled)
+        for (int p = p_stop; p <= inflight_hi; ++p) {
             const int s = p - z0 + 1;
             mbar_wait_bounded(bar0 + 8 * (s % 3), (unsigned)((s / 3) & 1));
         }
