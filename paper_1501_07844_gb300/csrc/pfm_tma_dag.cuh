@@ -116,12 +116,20 @@ fused_dag_tma_kernel(const StepArgs<DMAX, DMAX> a, const __grid_constant__ TmaMa
         }
     };
 
+    // an iteration reads only the stage of its own plane (the voxel's flows
+    // and S of the previous plane stay in registers): the ring runs two
+    // planes ahead
+    int inflight_hi = z0;
     if (t == 0) {
         for (int k = 0; k < TMA_STAGES; ++k) mbar_init(bar0 + 8 * k, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         s_abort = 0;
         issue(z0 - 1, 0, true);
         issue(z0, 1, false);
+        if (z0 + 1 <= z1 && z0 + 1 < a.nz) {
+            issue(z0 + 1, 2, false);
+            inflight_hi = z0 + 1;
+        }
     }
     static_assert(sizeof(DagLists) % 4 == 0, "lists copied as words");
     for (int k = t; k < (int)(sizeof(DagLists) / 4); k += DAG_TMA_NT)
@@ -150,38 +158,57 @@ fused_dag_tma_kernel(const StepArgs<DMAX, DMAX> a, const __grid_constant__ TmaMa
     for (int k = t; k < 2 * g_elems; k += DAG_TMA_NT) gbuf[k] = 0.f;
     // capacities of this thread's nodes, read once (lane-dependent parameter
     // reads serialise)
-    float cap[PER], gprev[PER], gcur[PER];
+    // this voxel's state carried from plane p-1 to plane p: g_A, the flow
+    // components of its nodes (the z one also closes the divergence) and S
+    float cap[PER], gprev[PER], gcur[PER], qxp[PER], qyp[PER], qzp[PER];
+    float sprev = 1.0f;
 #pragma unroll
     for (int i = 0; i < PER; ++i) {
         cap[i] = (h + 4 * i < nf) ? a.s_node[h + 4 * i] : 0.f;
-        gprev[i] = gcur[i] = 0.f;
+        gprev[i] = gcur[i] = qxp[i] = qyp[i] = qzp[i] = 0.f;
     }
-    __syncthreads();
+    // z flows of plane z0-1 (its x / y flow steps belong to the previous chunk)
+    bool ok = mbar_wait_bounded(bar0, 0u);
+    if constexpr (DIM == 3) {
+        if (ok && validE) {
+            const T* q0 = reinterpret_cast<const T*>(stage_ptr(0) + lay.q_off);
+#pragma unroll
+            for (int i = 0; i < PER; ++i)
+                if (h + 4 * i < nf) qzp[i] = lds<T>(q0 + ((h + 4 * i) * DIM + 2) * qstride + qi);
+        }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    if (__syncthreads_or(!ok)) {
+        if (t == 0) atomicOr(a.flags, FLAG_TIMEOUT);
+        s_abort = 1;
+    }
     bool bad = false;
-    int inflight_hi = z0;
-    for (int p = z0; p <= z1; ++p) {
+    int p_stop = z0 - 1;  // first plane whose stage may still be in flight at an abort
+    for (int p = z0; p <= z1 && !s_abort; ++p) {
         const int s = p - z0 + 1;
-        const int cs = s % 3, ps = (s + 2) % 3, ns = (s + 1) % 3;
-        // stage ns held plane p-2, last read before the previous barrier
-        if (t == 0 && p + 1 <= z1 && p + 1 < a.nz) {
-            issue(p + 1, ns, false);
-            inflight_hi = p + 1;
+        const int cs = s % 3, ps = (s + 2) % 3;
+        // stage ps held plane p-1, last read before the previous barrier
+        if (t == 0 && p + 2 <= z1 && p + 2 < a.nz) {
+            issue(p + 2, ps, false);
+            inflight_hi = p + 2;
         }
         unsigned char* cst = stage_ptr(cs);
-        unsigned char* pst = stage_ptr(ps);
         float* gC = gbuf + (p & 1) * g_elems;
         const float* gP = gbuf + ((p + 1) & 1) * g_elems;
         // each thread waits itself; a timeout reaches the CTA at the barrier
-        bool ok = true;
-        if (p == z0) ok = mbar_wait_bounded(bar0 + 8 * ps, 0u);
-        if (p < a.nz && ok) ok = mbar_wait_bounded(bar0 + 8 * cs, (unsigned)((s / 3) & 1));
+        ok = true;
+        if (p < a.nz) ok = mbar_wait_bounded(bar0 + 8 * cs, (unsigned)((s / 3) & 1));
         if (!ok) atomicOr(a.flags, FLAG_TIMEOUT);
+        float qxc[PER], qyc[PER], qzc[PER];
+#pragma unroll
+        for (int i = 0; i < PER; ++i) qxc[i] = qyc[i] = qzc[i] = 0.f;
+        float scur = 1.0f;
 
         if (p < a.nz) {
             const T* uS = reinterpret_cast<const T*>(cst + lay.u_off);
             const float* dS = reinterpret_cast<const float*>(cst + lay.d_off);
             const T* qS = reinterpret_cast<const T*>(cst + lay.q_off);
-            const T* qP = reinterpret_cast<const T*>(pst + lay.q_off);
+            if (has_S && ownerE) scur = reinterpret_cast<const float*>(cst + lay.s_off)[ey * FTX + ex];
             // divergence of this thread's nodes (no boundary tests: the last-index
             // normal flow is an invariant zero, the box is zero-filled outside)
             if (validE) {
@@ -191,9 +218,13 @@ fused_dag_tma_kernel(const StepArgs<DMAX, DMAX> a, const __grid_constant__ TmaMa
                     if (A < nf) {
                         const T* qx = qS + (A * DIM + 0) * qstride + qi;
                         const T* qy = qS + (A * DIM + 1) * qstride + qi;
-                        float dv = (lds<T>(qx) - lds<T>(qx - 1)) + (lds<T>(qy) - lds<T>(qy - QBX));
-                        if constexpr (DIM == 3)
-                            dv += lds<T>(qS + (A * DIM + 2) * qstride + qi) - lds<T>(qP + (A * DIM + 2) * qstride + qi);
+                        qxc[i] = lds<T>(qx);
+                        qyc[i] = lds<T>(qy);
+                        float dv = (qxc[i] - lds<T>(qx - 1)) + (qyc[i] - lds<T>(qy - QBX));
+                        if constexpr (DIM == 3) {
+                            qzc[i] = lds<T>(qS + (A * DIM + 2) * qstride + qi);
+                            dv += qzc[i] - qzp[i];
+                        }
                         erow[A] = dv;
                     }
                 }
@@ -267,9 +298,7 @@ fused_dag_tma_kernel(const StepArgs<DMAX, DMAX> a, const __grid_constant__ TmaMa
         // planes p-1 and p from registers
         const int pm = p - 1;
         if (pm >= z0 && ownerE) {
-            const T* qP = reinterpret_cast<const T*>(pst + lay.q_off);
-            const float* sP = reinterpret_cast<const float*>(pst + lay.s_off);
-            const float sf = has_S ? sP[ey * FTX + ex] : 1.0f;
+            const float sf = sprev;
             const long long i0 = (long long)pm * plane + (long long)ye * a.nx + xe;
             const float cz = pm < a.nz - 1 ? a.ctau : 0.f;
 #pragma unroll
@@ -279,9 +308,9 @@ fused_dag_tma_kernel(const StepArgs<DMAX, DMAX> a, const __grid_constant__ TmaMa
                     const float* gA = gP + A * ustride + ui;
                     const float g0 = gprev[i];
                     float yv[DIM];
-                    yv[0] = lds<T>(qP + (A * DIM + 0) * qstride + qi) - cx * (gA[1] - g0);
-                    yv[1] = lds<T>(qP + (A * DIM + 1) * qstride + qi) - cy * (gA[TMA_BX] - g0);
-                    if constexpr (DIM == 3) yv[2] = lds<T>(qP + (A * DIM + 2) * qstride + qi) - cz * (gcur[i] - g0);
+                    yv[0] = qxp[i] - cx * (gA[1] - g0);
+                    yv[1] = qyp[i] - cy * (gA[TMA_BX] - g0);
+                    if constexpr (DIM == 3) yv[2] = qzp[i] - cz * (gcur[i] - g0);
                     project_nb<DIM>(yv, cap[i] * sf, a.aniso);
                     T* qa = qout + (long long)A * DIM * n + i0;
 #pragma unroll
@@ -290,8 +319,15 @@ fused_dag_tma_kernel(const StepArgs<DMAX, DMAX> a, const __grid_constant__ TmaMa
             }
         }
 #pragma unroll
-        for (int i = 0; i < PER; ++i) gprev[i] = gcur[i];
+        for (int i = 0; i < PER; ++i) {
+            gprev[i] = gcur[i];
+            qxp[i] = qxc[i];
+            qyp[i] = qyc[i];
+            qzp[i] = qzc[i];
+        }
+        sprev = scur;
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        p_stop = p;
         if (__syncthreads_or(!ok)) {
             if (t == 0) s_abort = 1;
             break;
@@ -299,7 +335,8 @@ fused_dag_tma_kernel(const StepArgs<DMAX, DMAX> a, const __grid_constant__ TmaMa
     }
     if (bad) atomicOr(a.flags, FLAG_NONFINITE);
     if (s_abort && t == 0) {
-        for (int p = z0 - 1; p <= inflight_hi; ++p) {
+        // bounded drain: the plane whose wait gave up and every plane issued after it
+        for (int p = p_stop; p <= inflight_hi; ++p) {
             const int s = p - z0 + 1;
             mbar_wait_bounded(bar0 + 8 * (s % 3), (unsigned)((s / 3) & 1));
         }
