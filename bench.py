@@ -181,7 +181,7 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_oracle_sample(cfg, min_seconds=8.0, max_iters=20, zslab=64, seed=2000):
+def cpu_oracle_sample(cfg, min_seconds=10.0, max_iters=1000, zslab=64, seed=2000):
     """The FP64 oracle, as it stands, on a z-slab of the same phantom (same
     x-y extent, labels and parameters): iterations until min_seconds passed."""
     import oracle

@@ -437,11 +437,30 @@ flow_inplace_kernel(const StepArgs<MAXL, MAXN> a) {
 }
 
 // ---------------------------------------------------------------------------
-// Primal energy and pseudo-flow dual, FP32 per-voxel terms, FP64
-// accumulation; one (E, P) partial per block, summed in fixed order by
-// energy_final_kernel (deterministic for a fixed grid).
+// Primal energy and pseudo-flow dual, FP32 per-voxel terms, a compensated
+// FP32 partial per thread, FP64 from the warp level up; one (E, P) partial per
+// block, summed in fixed order by energy_final_kernel (deterministic for a
+// fixed grid).
 // ---------------------------------------------------------------------------
 constexpr int ENERGY_NT = 256;
+
+// Compensated (Kahan) FP32 running sum for a thread's share of the energy
+// reduction (one z-column of voxels): GB300's FP64 pipe is narrow, and a
+// double add per voxel and plane costs more than the iteration's own
+// arithmetic, so FP64 starts at the warp / block / grid levels of the
+// reduction.  The compensation keeps the partial within a few FP32 ulps
+// whatever the column length.
+struct SumF {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float x) {
+        const float y = x - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
 
 template <int MAXL, int MAXN, int DIM, bool IS_DAG, typename T>
 __global__ void __launch_bounds__(ENERGY_NT)
@@ -450,7 +469,7 @@ energy_partial_kernel(const StepArgs<MAXL, MAXN> a, double* partial) {
     const long long plane = (long long)a.nx * a.ny;
     const T* u = static_cast<const T*>(a.u_in);
     const T* q = static_cast<const T*>(a.q_in);
-    double accE = 0.0, accP = 0.0;
+    SumF sumE, sumP;
     for (long long i = (long long)blockIdx.x * ENERGY_NT + threadIdx.x; i < n;
          i += (long long)gridDim.x * ENERGY_NT) {
         const int x = (int)(i % a.nx);
@@ -532,10 +551,11 @@ energy_partial_kernel(const StepArgs<MAXL, MAXN> a, double* partial) {
                 dmin = fminf(dmin, dj);
             }
         }
-        accE += (double)eData + (double)tv;
-        accP += (double)dmin;
+        sumE.add(eData + tv);
+        sumP.add(dmin);
     }
     // block reduction in fixed order
+    double accE = sumE.value(), accP = sumP.value();
     __shared__ double sE[ENERGY_NT / 32], sP[ENERGY_NT / 32];
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {

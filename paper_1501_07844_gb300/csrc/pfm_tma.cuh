@@ -225,11 +225,9 @@ fused_tma_kernel(const StepArgs<MAXL, MAXL> a, const __grid_constant__ TmaMaps m
         }
     };
 
-    // Without the energy pass an iteration reads only the stage of its own
-    // plane (the voxel's flows and S of the previous plane are kept in
-    // registers), so the ring runs two planes ahead; the energy variant also
-    // reads the previous plane's staged u and D and runs one plane ahead.
-    constexpr bool kDeep = !WITH_E;
+    // An iteration reads only the stage of its own plane (what the flow step
+    // and the energy of plane p-1 need at the voxel is kept in registers), so
+    // the ring runs two planes ahead.
     int inflight_hi = z0;  // highest plane issued
     if (t == 0) {
         for (int k = 0; k < TMA_STAGES; ++k) mbar_init(bar0 + 8 * k, 1);
@@ -237,7 +235,7 @@ fused_tma_kernel(const StepArgs<MAXL, MAXL> a, const __grid_constant__ TmaMaps m
         s_abort = 0;
         issue(z0 - 1, 0, true);   // flows of plane z0-1 (zero-filled when z0 = 0)
         issue(z0, 1, false);
-        if (kDeep && z0 + 1 <= z1 && z0 + 1 < a.nz) {
+        if (z0 + 1 <= z1 && z0 + 1 < a.nz) {
             issue(z0 + 1, 2, false);
             inflight_hi = z0 + 1;
         }
@@ -291,22 +289,24 @@ fused_tma_kernel(const StepArgs<MAXL, MAXL> a, const __grid_constant__ TmaMaps m
         if (t == 0) atomicOr(a.flags, FLAG_TIMEOUT);
         s_abort = 1;
     }
+    // energy of the input state (WITH_E): the staged u at this voxel and the
+    // x / y part of its gradient norm (|gx|+|gy| or gx^2+gy^2), carried to the
+    // next plane, which supplies the z difference
+    float uin_prev[HL], txy_prev[HL];
+#pragma unroll
+    for (int i = 0; i < HL; ++i) uin_prev[i] = txy_prev[i] = 0.f;
     bool bad = false;
-    double accE = 0.0, accP = 0.0;
+    SumF sumE, sumP;
     int p_stop = z0 - 1;  // first plane whose stage may still be in flight at an abort
     for (int p = z0; p <= z1 && !s_abort; ++p) {
         const int s = p - z0 + 1;
-        const int cs = s % 3, ps = (s + 2) % 3, ns = (s + 1) % 3;
-        // the stage refilled here was last read before the previous barrier
-        if (t == 0) {
-            const int pf = kDeep ? p + 2 : p + 1;
-            if (pf <= z1 && pf < a.nz) {
-                issue(pf, kDeep ? ps : ns, false);
-                inflight_hi = pf;
-            }
+        const int cs = s % 3, ps = (s + 2) % 3;
+        // stage ps held plane p-1, last read before the previous barrier
+        if (t == 0 && p + 2 <= z1 && p + 2 < a.nz) {
+            issue(p + 2, ps, false);
+            inflight_hi = p + 2;
         }
         unsigned char* cst = stage_ptr(cs);
-        unsigned char* pst = stage_ptr(ps);
         float* gC = gbuf + (p & 1) * Lay::g_elems;              // g of plane p (written now)
         const float* gP = gbuf + ((p + 1) & 1) * Lay::g_elems;  // g of plane p-1 (neighbours)
         // each thread waits for its stage itself; a timeout is raised to the
@@ -314,10 +314,11 @@ fused_tma_kernel(const StepArgs<MAXL, MAXL> a, const __grid_constant__ TmaMaps m
         ok = true;
         if (p < a.nz) ok = mbar_wait_bounded(bar0 + 8 * cs, (unsigned)((s / 3) & 1));
         if (!ok) atomicOr(a.flags, FLAG_TIMEOUT);
-        float qxc[HL], qyc[HL], qzc[HL];
+        float qxc[HL], qyc[HL], qzc[HL], uin[HL], txy[HL];
 #pragma unroll
-        for (int i = 0; i < HL; ++i) qxc[i] = qyc[i] = qzc[i] = 0.f;
+        for (int i = 0; i < HL; ++i) qxc[i] = qyc[i] = qzc[i] = uin[i] = txy[i] = 0.f;
         float scur = 1.0f;
+        float eD = 0.f;  // sum of D u over this thread's labels of plane p (WITH_E)
 
         // ---- label prox of plane p on the halo-extended tile (uniform branch)
         if (p < a.nz) {
@@ -347,15 +348,25 @@ fused_tma_kernel(const StepArgs<MAXL, MAXL> a, const __grid_constant__ TmaMaps m
                         qzc[i] = lds<T>(qS + (j * DIM + 2) * qstride + qi);
                         dv += qzc[i] - qzp[i];
                     }
-                    d[i] = dS[j * ustride + ui] + dv;
+                    const float Dv = dS[j * ustride + ui];
+                    d[i] = Dv + dv;
                     mloc = fminf(mloc, d[i]);
+                    if constexpr (WITH_E) {
+                        uin[i] = u[i];
+                        if (ownerE) {
+                            const float gx = cx != 0.f ? lds<T>(uS + j * ustride + ui + 1) - u[i] : 0.f;
+                            const float gy = cy != 0.f ? lds<T>(uS + j * ustride + ui + TMA_BX) - u[i] : 0.f;
+                            txy[i] = a.aniso ? fabsf(gx) + fabsf(gy) : fmaf(gx, gx, gy * gy);
+                            if (p < z1) eD = fmaf(Dv, u[i], eD);
+                        }
+                    }
                 }
             }
             // per-voxel minimum over both halves: the dual term of this voxel,
             // and the exponent shift (NORMALISED only)
             const float dmin = fminf(mloc, __shfl_xor_sync(0xffffffffu, mloc, 1));
             if constexpr (WITH_E) {
-                if (ownerE && p < z1 && h == 0) accP += (double)dmin;
+                if (ownerE && p < z1 && h == 0) sumP.add(dmin);
             }
             const float m = a.literal ? 0.f : dmin;
             float sloc = 0.f;
@@ -407,29 +418,13 @@ fused_tma_kernel(const StepArgs<MAXL, MAXL> a, const __grid_constant__ TmaMaps m
                     if constexpr (DIM == 3) yv[2] = qzp[i] - cz * (gcur[i] - g0);
                     const float sj = cap[i] * sf;
                     if constexpr (WITH_E) {
-                        // E of plane p-1 on the input labelling (staged u of planes p-1 and p)
-                        const T* uj = reinterpret_cast<const T*>(pst + Lay::u_off) + j * ustride;
-                        const float u0 = lds<T>(uj + ui);
-                        float gr[DIM];
-                        gr[0] = cx != 0.f ? lds<T>(uj + ui + 1) - u0 : 0.f;
-                        gr[1] = cy != 0.f ? lds<T>(uj + ui + TMA_BX) - u0 : 0.f;
-                        if constexpr (DIM == 3)
-                            gr[2] = cz != 0.f
-                                        ? lds<T>(reinterpret_cast<const T*>(cst + Lay::u_off) + j * ustride + ui) - u0
-                                        : 0.f;
-                        float nv;
-                        if (a.aniso) {
-                            nv = 0.f;
-#pragma unroll
-                            for (int k = 0; k < DIM; ++k) nv += fabsf(gr[k]);
-                        } else {
-                            float r2 = 0.f;
-#pragma unroll
-                            for (int k = 0; k < DIM; ++k) r2 = fmaf(gr[k], gr[k], r2);
-                            nv = sqrtf(r2);
-                        }
-                        const float Dj = reinterpret_cast<const float*>(pst + Lay::d_off)[j * ustride + ui];
-                        eloc = fmaf(Dj, u0, fmaf(sj, nv, eloc));
+                        // TV term of plane p-1 on the input labelling: x / y part
+                        // from the previous plane, z difference with this plane's
+                        // staged u
+                        float gz = 0.f;
+                        if constexpr (DIM == 3) gz = cz != 0.f ? uin[i] - uin_prev[i] : 0.f;
+                        const float nv = a.aniso ? txy_prev[i] + fabsf(gz) : sqrtf(fmaf(gz, gz, txy_prev[i]));
+                        eloc = fmaf(sj, nv, eloc);
                     }
                     project_nb<DIM>(yv, sj, a.aniso);
                     T* qa = qout + (long long)j * DIM * n + i0;
@@ -437,14 +432,17 @@ fused_tma_kernel(const StepArgs<MAXL, MAXL> a, const __grid_constant__ TmaMaps m
                     for (int k = 0; k < DIM; ++k) stv<T>(qa + k * n, yv[k]);
                 }
             }
-            if constexpr (WITH_E) accE += (double)eloc;
+            if constexpr (WITH_E) sumE.add(eloc);
         }
+        if constexpr (WITH_E) sumE.add(eD);
 #pragma unroll
         for (int i = 0; i < HL; ++i) {
             gprev[i] = gcur[i];
             qxp[i] = qxc[i];
             qyp[i] = qyc[i];
             qzp[i] = qzc[i];
+            uin_prev[i] = uin[i];
+            txy_prev[i] = txy[i];
         }
         sprev = scur;
         // order this plane's shared-memory accesses before the TMA that
@@ -468,6 +466,7 @@ fused_tma_kernel(const StepArgs<MAXL, MAXL> a, const __grid_constant__ TmaMaps m
         }
     }
     if constexpr (WITH_E) {
+        double accE = sumE.value(), accP = sumP.value();
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
             accE += __shfl_down_sync(0xffffffffu, accE, off);
@@ -567,7 +566,8 @@ energy_tma_kernel(const StepArgs<MAXL, MAXL> a, const __grid_constant__ TmaMaps 
             }
         }
     }
-    double accE = 0.0, accP = 0.0;
+    SumF sumE, sumP;
+    int r_stop = z0;  // first plane whose stage may still be in flight at an abort
     for (int r = z0; r < z1; ++r) {
         const int s = r - z0;
         const int cs = s % 3, n1 = (s + 1) % 3, n2 = (s + 2) % 3;
@@ -637,18 +637,22 @@ energy_tma_kernel(const StepArgs<MAXL, MAXL> a, const __grid_constant__ TmaMaps 
         dmin = fminf(dmin, __shfl_xor_sync(0xffffffffu, dmin, 1));
         dmin = fminf(dmin, __shfl_xor_sync(0xffffffffu, dmin, 2));
         if (own) {
-            accE += (double)eData + (double)tv;
-            if (h == 0) accP += (double)dmin;
+            sumE.add(eData + tv);
+            if (h == 0) sumP.add(dmin);
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        r_stop = r + 1;
         __syncthreads();
     }
     if (s_abort && t == 0) {
-        for (int p = z0; p <= issued_hi; ++p) {
+        // planes consumed before the abort are complete (their stages may have
+        // been refilled): drain from the first plane not yet consumed
+        for (int p = r_stop; p <= issued_hi; ++p) {
             const int s = p - z0;
             mbar_wait_bounded(bar0 + 8 * (s % 3), (unsigned)((s / 3) & 1));
         }
     }
+    double accE = sumE.value(), accP = sumP.value();
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
         accE += __shfl_down_sync(0xffffffffu, accE, off);
