@@ -133,8 +133,12 @@ PFM_API const char* pfm_last_error(void);
 PFM_API void pfm_params_default(pfm_params* p);
 
 /* Host-only query (no GPU needed): device bytes and number of full-grid
- * buffers (one value per voxel each) that pfm_create would allocate.
- * n_leaf_out may be NULL.  Returns PFM_EDAG / PFM_EINVAL like pfm_create. */
+ * buffers (one value per voxel each) that pfm_create would allocate.  The
+ * device arrays store rows of nx values at a pitch of nx rounded up to a
+ * multiple of 8 (every row starts on a 16-byte boundary for the TMA
+ * kernels); the bytes include that padding.  Caller-side arrays are always
+ * dense.  n_leaf_out may be NULL.  Returns PFM_EDAG / PFM_EINVAL like
+ * pfm_create. */
 PFM_API pfm_status pfm_footprint(const pfm_desc* desc, const pfm_params* params,
                          size_t* device_bytes, int64_t* n_grid_buffers, int* n_leaf_out);
 

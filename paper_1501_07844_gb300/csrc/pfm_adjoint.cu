@@ -30,6 +30,12 @@ constexpr int NT = 256;
 
 using AdjArgs = AdjLaunch;
 
+// Slot of voxel i (dense index, row coordinate x) in the problem's pitched
+// D and S arrays.
+__device__ __forceinline__ long long pitched(const AdjArgs& a, long long i, int x) {
+    return (i / a.nx) * a.px + x;
+}
+
 __device__ __forceinline__ void coords(long long i, int nx, int ny, int& x, int& y, int& z) {
     x = (int)(i % nx);
     const long long r = i / nx;
@@ -44,7 +50,7 @@ __global__ void __launch_bounds__(NT) adj_proj_kernel(const AdjArgs a) {
     int x, y, z;
     coords(i, a.nx, a.ny, x, y, z);
     const long long n = a.n, plane = (long long)a.nx * a.ny;
-    const float sf = a.S ? a.S[i] : 1.0f;
+    const float sf = a.S ? a.S[pitched(a, i, x)] : 1.0f;
     float sbar = 0.f;
     for (int j = 0; j < a.nl; ++j) {
         const float* u1 = a.u_k1 + (long long)j * n + i;
@@ -99,6 +105,7 @@ __global__ void __launch_bounds__(NT) adj_prox_kernel(const AdjArgs a) {
     int x, y, z;
     coords(i, a.nx, a.ny, x, y, z);
     const long long n = a.n, plane = (long long)a.nx * a.ny;
+    const long long pi = pitched(a, i, x);
     float d[16], ub[16], u1[16];
     float m = 3.0e38f;
     float dot = 0.f;
@@ -108,7 +115,7 @@ __global__ void __launch_bounds__(NT) adj_prox_kernel(const AdjArgs a) {
         float dv = (x < a.nx - 1 ? qa[0] : 0.f) - (x > 0 ? qa[-1] : 0.f);
         dv += (y < a.ny - 1 ? qa[n] : 0.f) - (y > 0 ? qa[n - a.nx] : 0.f);
         if constexpr (DIM == 3) dv += (z < a.nz - 1 ? qa[2 * n] : 0.f) - (z > 0 ? qa[2 * n - plane] : 0.f);
-        d[j] = a.D[(long long)j * n + i] + dv;
+        d[j] = a.D[(long long)j * a.np + pi] + dv;
         m = fminf(m, d[j]);
         // ubar'_j + c tau div ybar_j
         const float* yb = a.ybar + (long long)j * DIM * n + i;

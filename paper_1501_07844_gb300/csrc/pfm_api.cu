@@ -211,7 +211,9 @@ pfm_status set_error(pfm_status st, const char* msg) {
 
 struct pfm_problem {
     int ndim = 0, nx = 0, ny = 0, nz = 0, nl = 0, nn = 0;
-    long long n = 0;
+    int px = 0;         // row pitch (elements) of every device array, >= nx
+    long long n = 0;    // slots per label / component: px*ny*nz
+    long long nv = 0;   // voxels: nx*ny*nz (the caller's dense arrays)
     bool flat = true;
     pfm_params prm{};
     cudaStream_t stream = nullptr;
@@ -239,6 +241,7 @@ pfm::ProblemView view_of(const pfm_problem* pb) {
     pfm::ProblemView v{};
     v.ndim = pb->ndim;
     v.nx = pb->nx;
+    v.px = pb->px;
     v.ny = pb->ny;
     v.nz = pb->nz;
     v.nl = pb->nl;
@@ -305,14 +308,19 @@ void pfm_params_default(pfm_params* p) {
     p->gap_tol = 1e-4;
 }
 
-pfm_status pfm_footprint(const pfm_desc* desc, const pfm_params* params, size_t* device_bytes,
-                         int64_t* n_grid_buffers, int* n_leaf_out) {
+}  // extern "C"
+
+// Device arrays of pfm_create's problems have rows padded to a multiple of
+// 8 elements (16 bytes in FP32 and BF16); the explicit-flow solver's are dense.
+static pfm_status footprint_impl(const pfm_desc* desc, const pfm_params* params, bool dense, size_t* device_bytes,
+                                 int64_t* n_grid_buffers, int* n_leaf_out) {
     DagInfo dag;
     pfm_status st = check_params(params);
     if (st != PFM_OK) return st;
     st = check_desc(desc, &dag);
     if (st != PFM_OK) return st;
-    const long long n = (long long)desc->dims[0] * desc->dims[1] * desc->dims[2];
+    const long long px = dense ? desc->dims[0] : (desc->dims[0] + 7) / 8 * 8;
+    const long long n = px * desc->dims[1] * desc->dims[2];
     const int copies = params->schedule == PFM_SCHEDULE_INPLACE ? 1 : 2;
     const size_t ts = elem_size(params->storage);
     int64_t bufs = 0;
@@ -337,7 +345,37 @@ pfm_status pfm_footprint(const pfm_desc* desc, const pfm_params* params, size_t*
     return PFM_OK;
 }
 
+extern "C" {
+
+pfm_status pfm_footprint(const pfm_desc* desc, const pfm_params* params, size_t* device_bytes,
+                         int64_t* n_grid_buffers, int* n_leaf_out) {
+    return footprint_impl(desc, params, false, device_bytes, n_grid_buffers, n_leaf_out);
+}
+
+// Row pitch of the device arrays: nx rounded up to 8 elements, so that every
+// row of the FP32 and BF16 arrays starts on a 16-byte boundary (the TMA
+// kernels need it); the explicit-flow solver keeps dense rows.
+static int row_pitch(long long nx, bool dense) { return (int)(dense ? nx : (nx + 7) / 8 * 8); }
+
+// Copy rows of nx FP32 values between a dense caller array and a pitched
+// device array (either direction; pitches in elements).
+static cudaError_t copy_rows(void* dst, int dpitch, const void* src, int spitch, int nx, long long rows,
+                             cudaStream_t s) {
+    if (dpitch == nx && spitch == nx)
+        return cudaMemcpyAsync(dst, src, (size_t)rows * nx * 4, cudaMemcpyDefault, s);
+    return cudaMemcpy2DAsync(dst, (size_t)dpitch * 4, src, (size_t)spitch * 4, (size_t)nx * 4, (size_t)rows,
+                             cudaMemcpyDefault, s);
+}
+
+static pfm_status create_impl(const pfm_desc* desc, const pfm_params* params, void* stream, bool dense,
+                              pfm_problem** out);
+
 pfm_status pfm_create(const pfm_desc* desc, const pfm_params* params, void* stream, pfm_problem** out) {
+    return create_impl(desc, params, stream, false, out);
+}
+
+static pfm_status create_impl(const pfm_desc* desc, const pfm_params* params, void* stream, bool dense,
+                              pfm_problem** out) {
     if (!out) return fail(PFM_EINVAL, "out is NULL");
     *out = nullptr;
     DagInfo dag;
@@ -351,7 +389,9 @@ pfm_status pfm_create(const pfm_desc* desc, const pfm_params* params, void* stre
     pb->nx = (int)desc->dims[0];
     pb->ny = (int)desc->dims[1];
     pb->nz = (int)desc->dims[2];
-    pb->n = (long long)pb->nx * pb->ny * pb->nz;
+    pb->px = row_pitch(pb->nx, dense);
+    pb->n = (long long)pb->px * pb->ny * pb->nz;
+    pb->nv = (long long)pb->nx * pb->ny * pb->nz;
     pb->nl = dag.nl;
     pb->nn = dag.nn;
     pb->flat = dag.flat;
@@ -393,9 +433,15 @@ pfm_status pfm_create(const pfm_desc* desc, const pfm_params* params, void* stre
 
     cudaStream_t s = pb->stream;
     if ((e = cudaMemsetAsync(pb->flags, 0, sizeof(unsigned), s)) != cudaSuccess) return bail(cuda_fail(e, "memset"));
-    if ((e = cudaMemcpyAsync(pb->D, desc->D, (size_t)pb->nl * n * 4, cudaMemcpyDefault, s)) != cudaSuccess)
+    // the row padding of D and S holds zeros (finite, never read as a voxel)
+    if (pb->px != pb->nx) {
+        if ((e = cudaMemsetAsync(pb->D, 0, (size_t)pb->nl * n * 4, s)) != cudaSuccess) return bail(cuda_fail(e, "memset"));
+        if (pb->S && (e = cudaMemsetAsync(pb->S, 0, (size_t)n * 4, s)) != cudaSuccess) return bail(cuda_fail(e, "memset"));
+    }
+    const long long rows = (long long)pb->ny * pb->nz;
+    if ((e = copy_rows(pb->D, pb->px, desc->D, pb->nx, pb->nx, pb->nl * rows, s)) != cudaSuccess)
         return bail(cuda_fail(e, "copy D"));
-    if (pb->S && (e = cudaMemcpyAsync(pb->S, desc->S_field, (size_t)n * 4, cudaMemcpyDefault, s)) != cudaSuccess)
+    if (pb->S && (e = copy_rows(pb->S, pb->px, desc->S_field, pb->nx, pb->nx, rows, s)) != cudaSuccess)
         return bail(cuda_fail(e, "copy S"));
     if ((e = cudaMemcpyAsync(pb->snode_dev, pb->s_node.data(), sizeof(float) * pb->nn, cudaMemcpyHostToDevice, s)) !=
         cudaSuccess)
@@ -449,8 +495,9 @@ pfm_status pfm_set_data(pfm_problem* pb, const float* D, const float* S_field) {
     if (!pb || !D) return fail(PFM_EINVAL, "NULL argument");
     if ((S_field != nullptr) != (pb->S != nullptr))
         return fail(PFM_EINVAL, "S_field must be given iff the problem was created with one");
-    PFM_CUDA(cudaMemcpyAsync(pb->D, D, (size_t)pb->nl * pb->n * 4, cudaMemcpyDefault, pb->stream), "copy D");
-    if (S_field) PFM_CUDA(cudaMemcpyAsync(pb->S, S_field, (size_t)pb->n * 4, cudaMemcpyDefault, pb->stream), "copy S");
+    const long long rows = (long long)pb->ny * pb->nz;
+    PFM_CUDA(copy_rows(pb->D, pb->px, D, pb->nx, pb->nx, pb->nl * rows, pb->stream), "copy D");
+    if (S_field) PFM_CUDA(copy_rows(pb->S, pb->px, S_field, pb->nx, pb->nx, rows, pb->stream), "copy S");
     PFM_CUDA(pfm::launch_validate(pb->D, (long long)pb->nl * pb->n, pb->S, pb->n, pb->flags, pb->stream), "validate");
     pb->launches++;
     return PFM_OK;
@@ -574,9 +621,10 @@ pfm_status pfm_run_to_gap(pfm_problem* pb, int max_iters, int* iters_done, doubl
 
 pfm_status pfm_get_labels(pfm_problem* pb, float* dst) {
     if (!pb || !dst) return fail(PFM_EINVAL, "NULL argument");
-    const long long count = (long long)pb->nl * pb->n;
+    const long long rows = (long long)pb->nl * pb->ny * pb->nz;
+    const long long count = (long long)pb->nl * pb->nv;
     if (pb->prm.storage == PFM_STORAGE_F32) {
-        PFM_CUDA(cudaMemcpyAsync(dst, pb->u[pb->cur], count * 4, cudaMemcpyDefault, pb->stream), "copy labels");
+        PFM_CUDA(copy_rows(dst, pb->nx, pb->u[pb->cur], pb->px, pb->nx, rows, pb->stream), "copy labels");
     } else {
         float* tmp = nullptr;
         cudaPointerAttributes at{};
@@ -587,7 +635,7 @@ pfm_status pfm_get_labels(pfm_problem* pb, float* dst) {
         } else {
             PFM_CUDA(cudaMallocAsync((void**)&tmp, count * 4, pb->stream), "alloc staging");
         }
-        cudaError_t e = pfm::launch_to_f32(pb->u[pb->cur], pb->prm.storage, count, tmp, pb->stream);
+        cudaError_t e = pfm::launch_to_f32(pb->u[pb->cur], pb->prm.storage, rows, pb->nx, pb->px, tmp, pb->stream);
         pb->launches++;
         if (e == cudaSuccess && !dev) e = cudaMemcpyAsync(dst, tmp, count * 4, cudaMemcpyDefault, pb->stream);
         if (!dev) cudaFreeAsync(tmp, pb->stream);
@@ -599,9 +647,10 @@ pfm_status pfm_get_labels(pfm_problem* pb, float* dst) {
 
 pfm_status pfm_get_flows(pfm_problem* pb, float* dst) {
     if (!pb || !dst) return fail(PFM_EINVAL, "NULL argument");
-    const long long count = (long long)pb->nn * pb->ndim * pb->n;
+    const long long rows = (long long)pb->nn * pb->ndim * pb->ny * pb->nz;
+    const long long count = (long long)pb->nn * pb->ndim * pb->nv;
     if (pb->prm.storage == PFM_STORAGE_F32) {
-        PFM_CUDA(cudaMemcpyAsync(dst, pb->q[pb->cur], count * 4, cudaMemcpyDefault, pb->stream), "copy flows");
+        PFM_CUDA(copy_rows(dst, pb->nx, pb->q[pb->cur], pb->px, pb->nx, rows, pb->stream), "copy flows");
     } else {
         float* tmp = nullptr;
         cudaPointerAttributes at{};
@@ -612,7 +661,7 @@ pfm_status pfm_get_flows(pfm_problem* pb, float* dst) {
         } else {
             PFM_CUDA(cudaMallocAsync((void**)&tmp, count * 4, pb->stream), "alloc staging");
         }
-        cudaError_t e = pfm::launch_to_f32(pb->q[pb->cur], pb->prm.storage, count, tmp, pb->stream);
+        cudaError_t e = pfm::launch_to_f32(pb->q[pb->cur], pb->prm.storage, rows, pb->nx, pb->px, tmp, pb->stream);
         pb->launches++;
         if (e == cudaSuccess && !dev) e = cudaMemcpyAsync(dst, tmp, count * 4, cudaMemcpyDefault, pb->stream);
         if (!dev) cudaFreeAsync(tmp, pb->stream);
@@ -628,10 +677,11 @@ pfm_status pfm_get_argmax(pfm_problem* pb, int32_t* dst) {
     const bool dev = cudaPointerGetAttributes(&at, dst) == cudaSuccess && at.type == cudaMemoryTypeDevice;
     cudaGetLastError();
     int* tmp = dev ? (int*)dst : nullptr;
-    if (!dev) PFM_CUDA(cudaMallocAsync((void**)&tmp, pb->n * 4, pb->stream), "alloc staging");
-    cudaError_t e = pfm::launch_argmax(pb->u[pb->cur], pb->prm.storage, pb->nl, pb->n, tmp, pb->stream);
+    if (!dev) PFM_CUDA(cudaMallocAsync((void**)&tmp, pb->nv * 4, pb->stream), "alloc staging");
+    cudaError_t e =
+        pfm::launch_argmax(pb->u[pb->cur], pb->prm.storage, pb->nl, pb->n, pb->nx, pb->px, pb->nv, tmp, pb->stream);
     pb->launches++;
-    if (e == cudaSuccess && !dev) e = cudaMemcpyAsync(dst, tmp, pb->n * 4, cudaMemcpyDefault, pb->stream);
+    if (e == cudaSuccess && !dev) e = cudaMemcpyAsync(dst, tmp, pb->nv * 4, cudaMemcpyDefault, pb->stream);
     if (!dev) cudaFreeAsync(tmp, pb->stream);
     if (e != cudaSuccess) return cuda_fail(e, "argmax");
     PFM_CUDA(cudaStreamSynchronize(pb->stream), "stream sync");
@@ -656,10 +706,11 @@ pfm_status pfm_set_labels(pfm_problem* pb, const float* src) {
     if (!pb || !src) return fail(PFM_EINVAL, "NULL argument");
     float* tmp;
     bool owned;
-    pfm_status st = stage_in(pb, src, (long long)pb->nl * pb->n, &tmp, &owned);
+    pfm_status st = stage_in(pb, src, (long long)pb->nl * pb->nv, &tmp, &owned);
     if (st != PFM_OK) return st;
     PFM_CUDA(cudaMemsetAsync(pb->flags, 0, sizeof(unsigned), pb->stream), "memset");
-    cudaError_t e = pfm::launch_set_labels(tmp, pb->prm.storage, pb->nl, pb->n, pb->u[pb->cur], pb->flags, pb->stream);
+    cudaError_t e = pfm::launch_set_labels(tmp, pb->prm.storage, pb->nl, pb->nv, pb->nx, pb->px, pb->n,
+                                           pb->u[pb->cur], pb->flags, pb->stream);
     pb->launches++;
     if (owned) cudaFreeAsync(tmp, pb->stream);
     if (e != cudaSuccess) return cuda_fail(e, "set labels");
@@ -677,9 +728,9 @@ pfm_status pfm_set_flows(pfm_problem* pb, const float* src) {
     if (!pb || !src) return fail(PFM_EINVAL, "NULL argument");
     float* tmp;
     bool owned;
-    pfm_status st = stage_in(pb, src, (long long)pb->nn * pb->ndim * pb->n, &tmp, &owned);
+    pfm_status st = stage_in(pb, src, (long long)pb->nn * pb->ndim * pb->nv, &tmp, &owned);
     if (st != PFM_OK) return st;
-    cudaError_t e = pfm::launch_set_flows(tmp, pb->prm.storage, pb->nn, pb->ndim, pb->nx, pb->ny, pb->nz,
+    cudaError_t e = pfm::launch_set_flows(tmp, pb->prm.storage, pb->nn, pb->ndim, pb->nx, pb->ny, pb->nz, pb->px,
                                           pb->snode_dev, pb->S, pb->prm.norm == PFM_NORM_ANISO, pb->q[pb->cur],
                                           pb->stream);
     pb->launches++;
@@ -728,14 +779,16 @@ pfm_status pfm_adjoint_step(pfm_problem* pb, const float* u_k, const float* q_k,
     L.Dbar = Dbar;
     L.Sbar = pb->S ? Sbar : nullptr;
     L.ybar = work;
-    L.dbar = work + (size_t)pb->nl * pb->ndim * pb->n;
+    L.dbar = work + (size_t)pb->nl * pb->ndim * pb->nv;
     L.D = pb->D;
     L.S = pb->S;
     L.nx = pb->nx;
+    L.px = pb->px;
+    L.np = pb->n;
     L.ny = pb->ny;
     L.nz = pb->nz;
     L.nl = pb->nl;
-    L.n = pb->n;
+    L.n = pb->nv;
     L.c = (float)pb->prm.c;
     L.ctau = (float)(pb->prm.c * pb->prm.tau);
     L.aniso = pb->prm.norm == PFM_NORM_ANISO;
@@ -1049,7 +1102,7 @@ pfm_status pfm_alm_footprint(const pfm_desc* desc, size_t* device_bytes, int64_t
     size_t b = 0;
     int64_t nb = 0;
     int nl = 0;
-    pfm_status st = pfm_footprint(desc, &p, &b, &nb, &nl);
+    pfm_status st = footprint_impl(desc, &p, true, &b, &nb, &nl);
     if (st != PFM_OK) return st;
     const long long n = (long long)desc->dims[0] * desc->dims[1] * desc->dims[2];
     // + sink flows p_L, source flow p_S and the work field f
@@ -1070,7 +1123,7 @@ pfm_status pfm_alm_create(const pfm_desc* desc, double gamma, double step, int n
     pfm_alm* m = new pfm_alm();
     m->gamma = gamma;
     m->step = step;
-    pfm_status st = pfm_create(desc, &p, stream, &m->pb);
+    pfm_status st = create_impl(desc, &p, stream, true, &m->pb);
     if (st != PFM_OK) {
         delete m;
         return st;

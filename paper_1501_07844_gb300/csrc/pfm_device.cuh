@@ -1,7 +1,12 @@
 // pfm_device.cuh -- device-side building blocks of libpfm (sm_103a).
 //
-// Layouts are label-major structure-of-arrays, x fastest, as in pfm.h:
-//   u[leaf][n], D[leaf][n], q[node][comp][n], S[n];  n = nx*ny*nz voxels.
+// Layouts are label-major structure-of-arrays, x fastest, as in pfm.h, with
+// rows padded to a pitch px >= nx (a multiple of 8 elements, so that every
+// row of the FP32 and BF16 arrays starts on a 16-byte boundary, as TMA
+// requires):
+//   u[leaf][n], D[leaf][n], q[node][comp][n], S[n];  n = px*ny*nz slots,
+//   voxel (x, y, z) at (z*ny + y)*px + x; slots x >= nx are padding that no
+//   kernel reads as a voxel.
 // A warp covers consecutive x, so every per-label load or store of a warp
 // is one contiguous 128-byte (FP32) or 64-byte (BF16) segment.
 //
@@ -53,8 +58,9 @@ struct StepArgs {
     float* abuf;          // [n] normaliser of the unshifted product (in-place PAPER_LITERAL)
     unsigned* flags;
     int nx, ny, nz, nl, nn;
+    int px;               // row pitch (elements), >= nx
     int literal, aniso, zc;
-    long long n;
+    long long n;          // slots per label / component: px*ny*nz
     float inv_c, ctau;
     float s_node[MAXN];
     float W[MAXN][MAXL];  // path weights W_(A,j), node A to end-label j (DAG kernels)
@@ -163,7 +169,7 @@ __device__ __forceinline__ void fused_tile(const StepArgs<MAXL, MAXN>& a, int bx
     const int z0 = bz * a.zc;
     const int z1 = min(z0 + a.zc, a.nz);
     const long long n = a.n;
-    const long long plane = (long long)a.nx * a.ny;
+    const long long plane = (long long)a.px * a.ny;
     const T* __restrict__ uin = static_cast<const T*>(a.u_in);
     const T* __restrict__ qin = static_cast<const T*>(a.q_in);
     T* __restrict__ uout = static_cast<T*>(a.u_out);
@@ -179,7 +185,7 @@ __device__ __forceinline__ void fused_tile(const StepArgs<MAXL, MAXN>& a, int bx
     for (int j = 0; j < MAXL; ++j) gprev[j] = 0.f;
     if constexpr (DIM == 3) {
         if (valid && z0 > 0) {
-            const long long i = (long long)(z0 - 1) * plane + (long long)y * a.nx + x;
+            const long long i = (long long)(z0 - 1) * plane + (long long)y * a.px + x;
 #pragma unroll
             for (int A = 0; A < MAXN; ++A)
                 if (A < a.nn) qk[A][2] = ldv<T>(qin + ((long long)A * DIM + 2) * n + i);
@@ -192,7 +198,7 @@ __device__ __forceinline__ void fused_tile(const StepArgs<MAXL, MAXN>& a, int bx
 #pragma unroll
         for (int j = 0; j < MAXL; ++j) gcur[j] = 0.f;
         if (p < a.nz && valid) {
-            const long long i = (long long)p * plane + (long long)y * a.nx + x;
+            const long long i = (long long)p * plane + (long long)y * a.px + x;
             float u[MAXL], e[MAXN], Dv[MAXL];
             float qxm[MAXN], qym[MAXN];
 #pragma unroll
@@ -212,7 +218,7 @@ __device__ __forceinline__ void fused_tile(const StepArgs<MAXL, MAXN>& a, int bx
 #pragma unroll
                     for (int k = 0; k < DIM; ++k) qn[A][k] = ldv<T>(qa + k * n);
                     qxm[A] = x > 0 ? ldv<T>(qa - 1) : 0.f;
-                    qym[A] = y > 0 ? ldv<T>(qa + n - a.nx) : 0.f;
+                    qym[A] = y > 0 ? ldv<T>(qa + n - a.px) : 0.f;
                 } else {
 #pragma unroll
                     for (int k = 0; k < DIM; ++k) qn[A][k] = 0.f;
@@ -245,7 +251,7 @@ __device__ __forceinline__ void fused_tile(const StepArgs<MAXL, MAXN>& a, int bx
         __syncthreads();
         const int pm = p - 1;
         if (pm >= z0 && owner) {
-            const long long i = (long long)pm * plane + (long long)y * a.nx + x;
+            const long long i = (long long)pm * plane + (long long)y * a.px + x;
             const float* sp = sg + (pm % 3) * MAXL * FNE + t;
             float gr[MAXL][DIM];
 #pragma unroll
@@ -343,11 +349,12 @@ prox_inplace_kernel(const StepArgs<MAXL, MAXN> a) {
     const long long n = a.n;
     const long long i = (long long)blockIdx.x * POINT_NT + threadIdx.x;
     if (i >= n) return;
-    const int x = (int)(i % a.nx);
-    const long long r = i / a.nx;
+    const int x = (int)(i % a.px);
+    if (x >= a.nx) return;  // row padding
+    const long long r = i / a.px;
     const int y = (int)(r % a.ny);
     const int z = (int)(r / a.ny);
-    const long long plane = (long long)a.nx * a.ny;
+    const long long plane = (long long)a.px * a.ny;
     T* u = static_cast<T*>(a.u_out);
     const T* q = static_cast<const T*>(a.q_in);
     float uv[MAXL], e[MAXN], g[MAXL], Dv[MAXL];
@@ -362,7 +369,7 @@ prox_inplace_kernel(const StepArgs<MAXL, MAXN> a) {
         if (A < a.nn) {
             const T* qa = q + (long long)A * DIM * n + i;
             dv = (x < a.nx - 1 ? ldv<T>(qa) : 0.f) - (x > 0 ? ldv<T>(qa - 1) : 0.f);
-            dv += (y < a.ny - 1 ? ldv<T>(qa + n) : 0.f) - (y > 0 ? ldv<T>(qa + n - a.nx) : 0.f);
+            dv += (y < a.ny - 1 ? ldv<T>(qa + n) : 0.f) - (y > 0 ? ldv<T>(qa + n - a.px) : 0.f);
             if constexpr (DIM == 3)
                 dv += (z < a.nz - 1 ? ldv<T>(qa + 2 * n) : 0.f) - (z > 0 ? ldv<T>(qa + 2 * n - plane) : 0.f);
         }
@@ -383,17 +390,18 @@ flow_inplace_kernel(const StepArgs<MAXL, MAXN> a) {
     const long long n = a.n;
     const long long i = (long long)blockIdx.x * POINT_NT + threadIdx.x;
     if (i >= n) return;
-    const int x = (int)(i % a.nx);
-    const long long r = i / a.nx;
+    const int x = (int)(i % a.px);
+    if (x >= a.nx) return;  // row padding
+    const long long r = i / a.px;
     const int y = (int)(r % a.ny);
     const int z = (int)(r / a.ny);
-    const long long plane = (long long)a.nx * a.ny;
+    const long long plane = (long long)a.px * a.ny;
     const T* u = static_cast<const T*>(a.u_in);
     T* q = static_cast<T*>(a.q_out);
     // g = u (NORMALISED) or u * a(x) (PAPER_LITERAL: the unnormalised product)
     const float a0 = a.literal ? a.abuf[i] : 1.f;
     const float ax = (a.literal && x < a.nx - 1) ? a.abuf[i + 1] : 1.f;
-    const float ay = (a.literal && y < a.ny - 1) ? a.abuf[i + a.nx] : 1.f;
+    const float ay = (a.literal && y < a.ny - 1) ? a.abuf[i + a.px] : 1.f;
     float az = 1.f;
     if constexpr (DIM == 3) az = (a.literal && z < a.nz - 1) ? a.abuf[i + plane] : 1.f;
     float gr[MAXL][DIM];
@@ -403,7 +411,7 @@ flow_inplace_kernel(const StepArgs<MAXL, MAXN> a) {
             const T* uj = u + (long long)j * n + i;
             const float g0 = ldv<T>(uj) * a0;
             gr[j][0] = x < a.nx - 1 ? ldv<T>(uj + 1) * ax - g0 : 0.f;
-            gr[j][1] = y < a.ny - 1 ? ldv<T>(uj + a.nx) * ay - g0 : 0.f;
+            gr[j][1] = y < a.ny - 1 ? ldv<T>(uj + a.px) * ay - g0 : 0.f;
             if constexpr (DIM == 3) gr[j][2] = z < a.nz - 1 ? ldv<T>(uj + plane) * az - g0 : 0.f;
         } else {
 #pragma unroll
@@ -466,14 +474,15 @@ template <int MAXL, int MAXN, int DIM, bool IS_DAG, typename T>
 __global__ void __launch_bounds__(ENERGY_NT)
 energy_partial_kernel(const StepArgs<MAXL, MAXN> a, double* partial) {
     const long long n = a.n;
-    const long long plane = (long long)a.nx * a.ny;
+    const long long plane = (long long)a.px * a.ny;
     const T* u = static_cast<const T*>(a.u_in);
     const T* q = static_cast<const T*>(a.q_in);
     SumF sumE, sumP;
     for (long long i = (long long)blockIdx.x * ENERGY_NT + threadIdx.x; i < n;
          i += (long long)gridDim.x * ENERGY_NT) {
-        const int x = (int)(i % a.nx);
-        const long long r = i / a.nx;
+        const int x = (int)(i % a.px);
+        if (x >= a.nx) continue;  // row padding
+        const long long r = i / a.px;
         const int y = (int)(r % a.ny);
         const int z = (int)(r / a.ny);
         float uv[MAXL], gr[MAXL][DIM];
@@ -485,7 +494,7 @@ energy_partial_kernel(const StepArgs<MAXL, MAXN> a, double* partial) {
                 uv[j] = ldv<T>(uj);
                 eData = fmaf(__ldg(a.D + (long long)j * n + i), uv[j], eData);
                 gr[j][0] = x < a.nx - 1 ? ldv<T>(uj + 1) - uv[j] : 0.f;
-                gr[j][1] = y < a.ny - 1 ? ldv<T>(uj + a.nx) - uv[j] : 0.f;
+                gr[j][1] = y < a.ny - 1 ? ldv<T>(uj + a.px) - uv[j] : 0.f;
                 if constexpr (DIM == 3) gr[j][2] = z < a.nz - 1 ? ldv<T>(uj + plane) - uv[j] : 0.f;
             } else {
                 uv[j] = 0.f;
@@ -527,7 +536,7 @@ energy_partial_kernel(const StepArgs<MAXL, MAXN> a, double* partial) {
                 tv = fmaf(a.s_node[A] * sf, nv, tv);
                 const T* qa = q + (long long)A * DIM * n + i;
                 float dv = (x < a.nx - 1 ? ldv<T>(qa) : 0.f) - (x > 0 ? ldv<T>(qa - 1) : 0.f);
-                dv += (y < a.ny - 1 ? ldv<T>(qa + n) : 0.f) - (y > 0 ? ldv<T>(qa + n - a.nx) : 0.f);
+                dv += (y < a.ny - 1 ? ldv<T>(qa + n) : 0.f) - (y > 0 ? ldv<T>(qa + n - a.px) : 0.f);
                 if constexpr (DIM == 3)
                     dv += (z < a.nz - 1 ? ldv<T>(qa + 2 * n) : 0.f) - (z > 0 ? ldv<T>(qa + 2 * n - plane) : 0.f);
                 e[A] = dv;

@@ -12,6 +12,9 @@ constexpr int NT = 256;
 
 inline unsigned blocks_for(long long count) { return (unsigned)((count + NT - 1) / NT); }
 
+// Slot of dense element e (rows of nx values) in an array of rows of pitch px.
+__device__ __forceinline__ long long slot(long long e, int nx, int px) { return (e / nx) * px + e % nx; }
+
 // u_L = 1/#leaves (Algorithm 1 and Algorithm 2, first line).
 template <typename T>
 __global__ void init_labels_kernel(T* u, int nl, long long n) {
@@ -21,15 +24,16 @@ __global__ void init_labels_kernel(T* u, int nl, long long n) {
 }
 
 // Thresholding of the relaxed labelling: index of the largest u_L, ties to
-// the lowest index.
+// the lowest index; out is dense (nv voxels).
 template <typename T>
-__global__ void argmax_kernel(const T* u, int nl, long long n, int* out) {
+__global__ void argmax_kernel(const T* u, int nl, long long n, int nx, int px, long long nv, int* out) {
     const long long i = (long long)blockIdx.x * NT + threadIdx.x;
-    if (i >= n) return;
-    float best = ldv<T>(u + i);
+    if (i >= nv) return;
+    const long long pi = slot(i, nx, px);
+    float best = ldv<T>(u + pi);
     int arg = 0;
     for (int j = 1; j < nl; ++j) {
-        const float v = ldv<T>(u + (long long)j * n + i);
+        const float v = ldv<T>(u + (long long)j * n + pi);
         if (v > best) {
             best = v;
             arg = j;
@@ -38,23 +42,25 @@ __global__ void argmax_kernel(const T* u, int nl, long long n, int* out) {
     out[i] = arg;
 }
 
+// Pitched rows -> dense FP32 rows (count = rows * nx).
 template <typename T>
-__global__ void to_f32_kernel(const T* src, long long count, float* dst) {
+__global__ void to_f32_kernel(const T* src, long long count, int nx, int px, float* dst) {
     const long long i = (long long)blockIdx.x * NT + threadIdx.x;
-    if (i < count) dst[i] = ldv<T>(src + i);
+    if (i < count) dst[i] = ldv<T>(src + slot(i, nx, px));
 }
 
 // Checkpoint import of a labelling: entries must be finite and >= 0 with a
 // positive sum per voxel; stored as given (the label update is invariant to
 // a per-voxel scale, so a labelling read back resumes bit for bit).
 template <typename T>
-__global__ void set_labels_kernel(const float* src, int nl, long long n, T* dst, unsigned* flags) {
+__global__ void set_labels_kernel(const float* src, int nl, long long nv, int nx, int px, long long n, T* dst,
+                                  unsigned* flags) {
     const long long i = (long long)blockIdx.x * NT + threadIdx.x;
-    if (i >= n) return;
+    if (i >= nv) return;
     float s = 0.f;
     bool ok = true;
     for (int j = 0; j < nl; ++j) {
-        const float v = src[(long long)j * n + i];
+        const float v = src[(long long)j * nv + i];
         ok = ok && (v >= 0.f) && isfinite(v);
         s += v;
     }
@@ -63,19 +69,22 @@ __global__ void set_labels_kernel(const float* src, int nl, long long n, T* dst,
         atomicOr(flags, FLAG_BAD_LABELS);
         return;
     }
-    for (int j = 0; j < nl; ++j) stv<T>(dst + (long long)j * n + i, src[(long long)j * n + i]);
+    const long long pi = slot(i, nx, px);
+    for (int j = 0; j < nl; ++j) stv<T>(dst + (long long)j * n + pi, src[(long long)j * nv + i]);
 }
 
 // Checkpoint import of flows: zero normal flux at the last index of each
 // axis, then projection onto the capacity set.
 template <typename T>
-__global__ void set_flows_kernel(const float* src, int nn, int ndim, int nx, int ny, int nz,
+__global__ void set_flows_kernel(const float* src, int nn, int ndim, int nx, int ny, int nz, int px,
                                  const float* s_node, const float* S, int aniso, T* dst) {
-    const long long n = (long long)nx * ny * nz;
+    const long long n = (long long)nx * ny * nz;       // dense voxels of src
+    const long long np = (long long)px * ny * nz;      // slots of the pitched S and dst
     const long long gi = (long long)blockIdx.x * NT + threadIdx.x;
     if (gi >= (long long)nn * n) return;
     const int A = (int)(gi / n);
     const long long i = gi % n;
+    const long long pi = slot(i, nx, px);
     const int x = (int)(i % nx);
     const int y = (int)((i / nx) % ny);
     const int z = (int)(i / ((long long)nx * ny));
@@ -84,7 +93,7 @@ __global__ void set_flows_kernel(const float* src, int nn, int ndim, int nx, int
     if (x == nx - 1) yv[0] = 0.f;
     if (y == ny - 1) yv[1] = 0.f;
     if (ndim == 3 && z == nz - 1) yv[2] = 0.f;
-    const float s = s_node[A] * (S ? S[i] : 1.0f);
+    const float s = s_node[A] * (S ? S[pi] : 1.0f);
     if (aniso) {
         for (int k = 0; k < ndim; ++k) yv[k] = fminf(fmaxf(yv[k], -s), s);
     } else {
@@ -99,7 +108,7 @@ __global__ void set_flows_kernel(const float* src, int nn, int ndim, int nx, int
             for (int k = 0; k < ndim; ++k) yv[k] *= f;
         }
     }
-    for (int k = 0; k < ndim; ++k) stv<T>(dst + ((long long)A * ndim + k) * n + i, yv[k]);
+    for (int k = 0; k < ndim; ++k) stv<T>(dst + ((long long)A * ndim + k) * np + pi, yv[k]);
 }
 
 __global__ void validate_kernel(const float* D, long long nD, const float* S, long long nS, unsigned* flags) {
@@ -155,35 +164,39 @@ cudaError_t launch_init_labels(void* u, int storage, int nl, long long n, cudaSt
     return cudaGetLastError();
 }
 
-cudaError_t launch_argmax(const void* u, int storage, int nl, long long n, int* out, cudaStream_t s) {
-    const unsigned b = blocks_for(n);
-    PFM_BY_STORAGE(storage, (argmax_kernel<float><<<b, NT, 0, s>>>((const float*)u, nl, n, out)),
-                   (argmax_kernel<__nv_bfloat16><<<b, NT, 0, s>>>((const __nv_bfloat16*)u, nl, n, out)));
+cudaError_t launch_argmax(const void* u, int storage, int nl, long long n, int nx, int px, long long nv, int* out,
+                          cudaStream_t s) {
+    const unsigned b = blocks_for(nv);
+    PFM_BY_STORAGE(storage, (argmax_kernel<float><<<b, NT, 0, s>>>((const float*)u, nl, n, nx, px, nv, out)),
+                   (argmax_kernel<__nv_bfloat16><<<b, NT, 0, s>>>((const __nv_bfloat16*)u, nl, n, nx, px, nv, out)));
     return cudaGetLastError();
 }
 
-cudaError_t launch_to_f32(const void* src, int storage, long long count, float* dst, cudaStream_t s) {
+cudaError_t launch_to_f32(const void* src, int storage, long long rows, int nx, int px, float* dst, cudaStream_t s) {
+    const long long count = rows * nx;
     const unsigned b = blocks_for(count);
-    PFM_BY_STORAGE(storage, (to_f32_kernel<float><<<b, NT, 0, s>>>((const float*)src, count, dst)),
-                   (to_f32_kernel<__nv_bfloat16><<<b, NT, 0, s>>>((const __nv_bfloat16*)src, count, dst)));
+    PFM_BY_STORAGE(storage, (to_f32_kernel<float><<<b, NT, 0, s>>>((const float*)src, count, nx, px, dst)),
+                   (to_f32_kernel<__nv_bfloat16><<<b, NT, 0, s>>>((const __nv_bfloat16*)src, count, nx, px, dst)));
     return cudaGetLastError();
 }
 
-cudaError_t launch_set_labels(const float* src, int storage, int nl, long long n, void* dst, unsigned* flags,
-                              cudaStream_t s) {
-    const unsigned b = blocks_for(n);
-    PFM_BY_STORAGE(storage, (set_labels_kernel<float><<<b, NT, 0, s>>>(src, nl, n, (float*)dst, flags)),
-                   (set_labels_kernel<__nv_bfloat16><<<b, NT, 0, s>>>(src, nl, n, (__nv_bfloat16*)dst, flags)));
+cudaError_t launch_set_labels(const float* src, int storage, int nl, long long nv, int nx, int px, long long n,
+                              void* dst, unsigned* flags, cudaStream_t s) {
+    const unsigned b = blocks_for(nv);
+    PFM_BY_STORAGE(storage,
+                   (set_labels_kernel<float><<<b, NT, 0, s>>>(src, nl, nv, nx, px, n, (float*)dst, flags)),
+                   (set_labels_kernel<__nv_bfloat16><<<b, NT, 0, s>>>(src, nl, nv, nx, px, n, (__nv_bfloat16*)dst,
+                                                                      flags)));
     return cudaGetLastError();
 }
 
-cudaError_t launch_set_flows(const float* src, int storage, int nn, int ndim, int nx, int ny, int nz,
+cudaError_t launch_set_flows(const float* src, int storage, int nn, int ndim, int nx, int ny, int nz, int px,
                              const float* s_node_dev, const float* S, int aniso, void* dst, cudaStream_t s) {
     const unsigned b = blocks_for((long long)nn * nx * ny * nz);
     PFM_BY_STORAGE(storage,
-                   (set_flows_kernel<float><<<b, NT, 0, s>>>(src, nn, ndim, nx, ny, nz, s_node_dev, S, aniso,
+                   (set_flows_kernel<float><<<b, NT, 0, s>>>(src, nn, ndim, nx, ny, nz, px, s_node_dev, S, aniso,
                                                              (float*)dst)),
-                   (set_flows_kernel<__nv_bfloat16><<<b, NT, 0, s>>>(src, nn, ndim, nx, ny, nz, s_node_dev, S,
+                   (set_flows_kernel<__nv_bfloat16><<<b, NT, 0, s>>>(src, nn, ndim, nx, ny, nz, px, s_node_dev, S,
                                                                      aniso, (__nv_bfloat16*)dst)));
     return cudaGetLastError();
 }

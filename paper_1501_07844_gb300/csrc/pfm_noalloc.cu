@@ -66,6 +66,7 @@ cudaError_t fill_and_launch(int ndim, const int64_t dims[3], int nl, const float
     a.D = D;
     a.S = S;
     a.nx = (int)dims[0];
+    a.px = a.nx;  // the caller's arrays are dense
     a.ny = (int)dims[1];
     a.nz = (int)dims[2];
     a.nl = nl;

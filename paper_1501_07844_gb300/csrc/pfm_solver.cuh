@@ -25,7 +25,8 @@ bool encode_tiled_map(CUtensorMap* map, const void* base, int elem_bytes, int ra
 // What a solver bucket needs from the problem (filled by the C-ABI layer).
 struct ProblemView {
     int ndim, nx, ny, nz, nl, nn;
-    long long n;
+    int px;        // row pitch (elements) of every state / data array
+    long long n;   // slots per label / component: px*ny*nz
     float c, tau;
     int literal, aniso;
     const float* D;
@@ -83,6 +84,7 @@ struct Solver final : SolverBase {
         base.abuf = v.abuf;
         base.flags = v.flags;
         base.nx = v.nx;
+        base.px = v.px;
         base.ny = v.ny;
         base.nz = v.nz;
         base.nl = v.nl;
@@ -176,7 +178,7 @@ struct Solver final : SolverBase {
     bool prepare_tma(void* const* u, void* const* q, const float* D, const float* S) override {
         if constexpr (kDagTmaCapable) {
             const int es = (int)sizeof(T);
-            if ((base.nx * es) % 16 != 0 || (base.nx * 4) % 16 != 0) return false;
+            if ((base.px * es) % 16 != 0 || (base.px * 4) % 16 != 0) return false;
             // nodes from nf on have zero capacity: their flow is identically zero
             int nf = 1;
             for (int A = 0; A < base.nn; ++A)
@@ -198,11 +200,12 @@ struct Solver final : SolverBase {
                         lists.desc_w[A][lists.desc_n[A]++] = base.W[A][j];
                     }
             const int qbx = FTX + 2 * (16 / es);
-            const unsigned long long nx = base.nx, ny = base.ny, nz = base.nz;
+            // logical extents, pitched strides: the padding is outside every box
+            const unsigned long long nx = base.nx, ny = base.ny, nz = base.nz, px = base.px;
             const unsigned long long dims_u[4] = {nx, ny, nz, (unsigned long long)base.nl};
             const unsigned long long dims_q[4] = {nx, ny, nz, (unsigned long long)DIM * base.nn};
-            const unsigned long long st_t[3] = {nx * es, nx * ny * es, nx * ny * nz * es};
-            const unsigned long long st_f[3] = {nx * 4, nx * ny * 4, nx * ny * nz * 4};
+            const unsigned long long st_t[3] = {px * es, px * ny * es, px * ny * nz * es};
+            const unsigned long long st_f[3] = {px * 4, px * ny * 4, px * ny * nz * 4};
             const unsigned box_u[4] = {(unsigned)TMA_BX, (unsigned)DAG_UY, 1u, (unsigned)base.nl};
             const unsigned box_q[4] = {(unsigned)qbx, (unsigned)DAG_QY, 1u, (unsigned)(DIM * nf)};
             const unsigned long long dims_s[3] = {nx, ny, nz};
@@ -227,12 +230,13 @@ struct Solver final : SolverBase {
             using Lay = TmaLayout<MAXL, DIM, T>;
             const int es = (int)sizeof(T);
             // every row pitch must be a multiple of 16 bytes (FP32 D and S too)
-            if ((base.nx * es) % 16 != 0 || (base.nx * 4) % 16 != 0) return false;
-            const unsigned long long nx = base.nx, ny = base.ny, nz = base.nz, nl = base.nl;
+            if ((base.px * es) % 16 != 0 || (base.px * 4) % 16 != 0) return false;
+            // logical extents, pitched strides: the padding is outside every box
+            const unsigned long long nx = base.nx, ny = base.ny, nz = base.nz, nl = base.nl, px = base.px;
             const unsigned long long dims_u[4] = {nx, ny, nz, nl};
             const unsigned long long dims_q[4] = {nx, ny, nz, (unsigned long long)DIM * nl};
-            const unsigned long long st_t[3] = {nx * es, nx * ny * es, nx * ny * nz * es};
-            const unsigned long long st_f[3] = {nx * 4, nx * ny * 4, nx * ny * nz * 4};
+            const unsigned long long st_t[3] = {px * es, px * ny * es, px * ny * nz * es};
+            const unsigned long long st_f[3] = {px * 4, px * ny * 4, px * ny * nz * 4};
             const unsigned box_u[4] = {(unsigned)TMA_BX, (unsigned)TMA_UY, 1u, (unsigned)nl};
             const unsigned box_q[4] = {(unsigned)Lay::QBX, (unsigned)TMA_QY, 1u, (unsigned)(DIM * nl)};
             const unsigned long long dims_s[3] = {nx, ny, nz};
@@ -341,6 +345,7 @@ struct BatchRunner final : BatchBase {
         a.abuf = v.abuf;
         a.flags = v.flags;
         a.nx = v.nx;
+        a.px = v.px;
         a.ny = v.ny;
         a.nz = v.nz;
         a.nl = v.nl;
@@ -434,10 +439,12 @@ struct AdjLaunch {
     float* Sbar;           // [n], accumulated, or nullptr
     float* ybar;           // work [nl][dim][n]
     float* dbar;           // work [nl][n]
-    const float* D;
-    const float* S;
+    const float* D;        // the problem's [nl][np], rows of pitch px
+    const float* S;        // the problem's [np], or nullptr
     int nx, ny, nz, nl;
-    long long n;
+    int px;                // row pitch of D and S
+    long long n;           // dense voxels of the caller's arrays
+    long long np;          // slots per label of D (px*ny*nz)
     float c, ctau;
     int aniso;
     float s_node[16];
@@ -465,11 +472,14 @@ cudaError_t launch_sum(const float* v, long long n, double* partial, int blocks,
 
 // Auxiliary kernels (pfm_misc.cu).
 cudaError_t launch_init_labels(void* u, int storage, int nl, long long n, cudaStream_t s);
-cudaError_t launch_argmax(const void* u, int storage, int nl, long long n, int* out, cudaStream_t s);
-cudaError_t launch_to_f32(const void* src, int storage, long long count, float* dst, cudaStream_t s);
-cudaError_t launch_set_labels(const float* src, int storage, int nl, long long n, void* dst, unsigned* flags,
-                              cudaStream_t s);
-cudaError_t launch_set_flows(const float* src, int storage, int nn, int ndim, int nx, int ny, int nz,
+// Readback and import between the pitched internal arrays (rows of nx
+// values at pitch px, n = px*ny*nz slots per label) and dense caller arrays.
+cudaError_t launch_argmax(const void* u, int storage, int nl, long long n, int nx, int px, long long nv, int* out,
+                          cudaStream_t s);
+cudaError_t launch_to_f32(const void* src, int storage, long long rows, int nx, int px, float* dst, cudaStream_t s);
+cudaError_t launch_set_labels(const float* src, int storage, int nl, long long nv, int nx, int px, long long n,
+                              void* dst, unsigned* flags, cudaStream_t s);
+cudaError_t launch_set_flows(const float* src, int storage, int nn, int ndim, int nx, int ny, int nz, int px,
                              const float* s_node_dev, const float* S, int aniso, void* dst, cudaStream_t s);
 cudaError_t launch_validate(const float* D, long long nD, const float* S, long long nS, unsigned* flags,
                             cudaStream_t s);

@@ -197,7 +197,7 @@ fused_tma_kernel(const StepArgs<MAXL, MAXL> a, const __grid_constant__ TmaMaps m
     const int z0 = blockIdx.z * a.zc;
     const int z1 = min(z0 + a.zc, a.nz);
     const long long n = a.n;
-    const long long plane = (long long)a.nx * a.ny;
+    const long long plane = (long long)a.px * a.ny;
     T* __restrict__ uout = static_cast<T*>(a.u_out);
     T* __restrict__ qout = static_cast<T*>(a.q_out);
     const int has_S = a.S != nullptr;
@@ -382,7 +382,7 @@ fused_tma_kernel(const StepArgs<MAXL, MAXL> a, const __grid_constant__ TmaMaps m
             if (validE) {
                 if (!((sum > 0.f) && (sum <= 3.0e38f))) bad = true;
                 const float inv = rcp_fast(sum);
-                const long long i0 = (long long)p * plane + (long long)ye * a.nx + xe;
+                const long long i0 = (long long)p * plane + (long long)ye * a.px + xe;
 #pragma unroll
                 for (int i = 0; i < HL; ++i) {
                     const int j = half_label(h, i);
@@ -403,7 +403,7 @@ fused_tma_kernel(const StepArgs<MAXL, MAXL> a, const __grid_constant__ TmaMaps m
         const int pm = p - 1;
         if (pm >= z0 && ownerE) {
             const float sf = sprev;
-            const long long i0 = (long long)pm * plane + (long long)ye * a.nx + xe;
+            const long long i0 = (long long)pm * plane + (long long)ye * a.px + xe;
             const float cz = pm < a.nz - 1 ? a.ctau : 0.f;
             float eloc = 0.f;
 #pragma unroll
@@ -519,7 +519,7 @@ energy_tma_kernel(const StepArgs<MAXL, MAXL> a, const __grid_constant__ TmaMaps 
     const int z0 = blockIdx.z * a.zc;
     const int z1 = min(z0 + a.zc, a.nz);
     const long long n = a.n;
-    const long long plane = (long long)a.nx * a.ny;
+    const long long plane = (long long)a.px * a.ny;
     const int has_S = a.S != nullptr;
     const unsigned bytes = (unsigned)(nl * TMA_UY * TMA_BX * sizeof(T)) + (unsigned)(nl * TMA_UY * TMA_BX * 4) +
                            (unsigned)(DIM * nl * TMA_QY * Lay::QBX * sizeof(T)) +
@@ -558,7 +558,7 @@ energy_tma_kernel(const StepArgs<MAXL, MAXL> a, const __grid_constant__ TmaMaps 
     if constexpr (DIM == 3) {
         if (own && z0 > 0) {
             const T* qin = static_cast<const T*>(a.q_in);
-            const long long i0 = (long long)(z0 - 1) * plane + (long long)y * a.nx + x;
+            const long long i0 = (long long)(z0 - 1) * plane + (long long)y * a.px + x;
 #pragma unroll
             for (int i = 0; i < QL; ++i) {
                 const int j = h + 4 * i;

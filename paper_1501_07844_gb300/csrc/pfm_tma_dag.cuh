@@ -89,7 +89,7 @@ fused_dag_tma_kernel(const StepArgs<DMAX, DMAX> a, const __grid_constant__ TmaMa
     const int z0 = blockIdx.z * a.zc;
     const int z1 = min(z0 + a.zc, a.nz);
     const long long n = a.n;
-    const long long plane = (long long)a.nx * a.ny;
+    const long long plane = (long long)a.px * a.ny;
     T* __restrict__ uout = static_cast<T*>(a.u_out);
     T* __restrict__ qout = static_cast<T*>(a.q_out);
     const int has_S = a.S != nullptr;
@@ -265,7 +265,7 @@ fused_dag_tma_kernel(const StepArgs<DMAX, DMAX> a, const __grid_constant__ TmaMa
             if (validE) {
                 if (!((sum > 0.f) && (sum <= 3.0e38f))) bad = true;
                 const float inv = rcp_fast(sum);
-                const long long i0 = (long long)p * plane + (long long)ye * a.nx + xe;
+                const long long i0 = (long long)p * plane + (long long)ye * a.px + xe;
 #pragma unroll
                 for (int i = 0; i < PER; ++i) {
                     const int j = h + 4 * i;
@@ -299,7 +299,7 @@ fused_dag_tma_kernel(const StepArgs<DMAX, DMAX> a, const __grid_constant__ TmaMa
         const int pm = p - 1;
         if (pm >= z0 && ownerE) {
             const float sf = sprev;
-            const long long i0 = (long long)pm * plane + (long long)ye * a.nx + xe;
+            const long long i0 = (long long)pm * plane + (long long)ye * a.px + xe;
             const float cz = pm < a.nz - 1 ? a.ctau : 0.f;
 #pragma unroll
             for (int i = 0; i < PER; ++i) {

@@ -205,15 +205,54 @@ def test_tma_fused_modes(mode, norm):
 
 
 def test_kernel_variant_selection():
+    """Rows are padded to 16 bytes internally, so every width takes the TMA
+    kernel; more than 8 labels and FUSED_PLAIN take the register-staged one."""
     import paper_1501_07844_gb300 as pfm
     p8 = synth.random_problem(95, (5, 6, 32), nl=8, s_kind="field")
     p_odd = synth.random_problem(96, (5, 6, 30), nl=8, s_kind="field")
     p12 = synth.random_problem(97, (5, 6, 32), nl=12, s_kind="field")
     with gpu_problem(p8) as a, gpu_problem(p_odd) as b, gpu_problem(p12) as c, \
             gpu_problem(p8, schedule=pfm.INPLACE) as d, gpu_problem(p8, storage=pfm.BF16) as e, \
-            gpu_problem(p_odd, storage=pfm.BF16) as f:
-        assert (a.variant, b.variant, c.variant, d.variant, e.variant, f.variant) == \
-            ("fused_tma", "fused", "fused", "inplace", "fused_tma", "fused")
+            gpu_problem(p_odd, storage=pfm.BF16) as f, gpu_problem(p_odd, schedule=pfm.FUSED_PLAIN) as g:
+        assert (a.variant, b.variant, c.variant, d.variant, e.variant, f.variant, g.variant) == \
+            ("fused_tma", "fused_tma", "fused", "inplace", "fused_tma", "fused_tma", "fused")
+
+
+@pytest.mark.parametrize("nx", [1, 5, 37, 65])
+@pytest.mark.parametrize("storage", [0, 1], ids=["f32", "bf16"])
+def test_padded_rows_every_schedule(nx, storage):
+    """Widths that are not a multiple of 8: the device rows are padded; every
+    schedule matches the oracle (FP32) or the other schedules (BF16), the
+    energy matches, and labels / flows / argmax read back dense and import
+    back bit for bit."""
+    import paper_1501_07844_gb300 as pfm
+    prob = synth.random_problem(140 + nx, (6, 11, nx), nl=5, s_kind="both", s_scale=0.4)
+    res = {}
+    for sched in (pfm.FUSED, pfm.INPLACE, pfm.FUSED_PLAIN):
+        with gpu_problem(prob, schedule=sched, storage=storage) as gp:
+            if storage == 0:
+                compare(prob, gp, 30)
+            else:
+                gp.iterate(30)
+            res[sched] = (gp.labels().cpu().numpy(), gp.flows().cpu().numpy(), gp.energy(), gp.argmax().cpu().numpy())
+            u, q = gp.labels(), gp.flows()
+            assert tuple(u.shape) == (5, 6, 11, nx) and tuple(q.shape) == (5, 3, 6, 11, nx)
+            gp.set_labels(u)
+            gp.set_flows(q)
+            assert torch_equal(gp.labels(), u) and torch_equal(gp.flows(), q)
+    tol = 1e-6 if storage == 0 else 2e-2
+    for sched in (pfm.INPLACE, pfm.FUSED_PLAIN):
+        assert np.abs(res[sched][0] - res[pfm.FUSED][0]).max() <= tol
+        assert np.abs(res[sched][1] - res[pfm.FUSED][1]).max() <= tol
+        E0, E1 = res[pfm.FUSED][2][0], res[sched][2][0]
+        assert abs(E1 - E0) <= (1e-5 if storage == 0 else 2e-2) * abs(E0)
+    for sched in res:
+        assert np.array_equal(res[sched][3], np.argmax(res[sched][0], axis=0))
+
+
+def torch_equal(a, b):
+    import torch
+    return bool(torch.equal(a, b))
 
 
 @pytest.mark.parametrize("sched", [0, 1, 2], ids=["fused_tma", "inplace", "fused_plain"])
