@@ -286,8 +286,9 @@ def run_batched(args, rank, world):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "dagmf_batched", "volumes": len(vols), "voxels": vox, "labels": 10, "nodes": 14,
                        "iters_per_step": ITERS_PER_STEP, "tuned_zc": zc, "tuned_grid": grid,
+                       "kernel_variant": b.variant,
                        "shapes": [list(p.spatial) for p in vols]},
-            "roofline": {"bound": "hbm", "kernel": "batched_step_kernel", "achieved": achieved, "peak": peak,
+            "roofline": {"bound": "hbm", "kernel": {"batched_tma_dag": "batched_dag_tma_kernel"}.get(b.variant, "batched_step_kernel"), "achieved": achieved, "peak": peak,
                          "unit": "GB/s", "frac": achieved / peak, "algorithmic_bytes_per_launch": alg,
                          "kernel_ms_per_launch": it_ms},
             "gpu_launches": int(b.launches - l0), "clocks": clk.summary()}

@@ -247,8 +247,12 @@ PFM_API pfm_status pfm_adjoint_step(pfm_problem* pb, const float* u_k, const flo
  * DAGs in lockstep: each pfm_batch_iterate iteration is ONE launch of a
  * persistent kernel whose CTAs walk a work list of (member, x tile, y tile,
  * z chunk) items, and runs of 20 iterations are replayed from a captured
- * CUDA graph.  All members share params (the schedule is always the
- * double-buffered one) and ndim; each member is an ordinary pfm_problem
+ * CUDA graph.  All members share params and ndim.  With the default
+ * PFM_SCHEDULE_FUSED, batches with label DAGs run the TMA-staged DAG kernel
+ * when every member fits it (at most 16 end-labels and nodes, three stages
+ * within shared memory), else, and with PFM_SCHEDULE_FUSED_PLAIN, the
+ * register-staged one; Potts-only batches run the register-staged kernel.
+ * The state is always double-buffered.  Each member is an ordinary pfm_problem
  * owned by the batch: read it back with pfm_get_* through
  * pfm_batch_member, but advance it only through pfm_batch_iterate.  stream
  * NULL makes the batch create its own stream (capture needs one other than
@@ -259,6 +263,8 @@ PFM_API pfm_status pfm_batch_create(int n, const pfm_desc* descs, const pfm_para
                                     pfm_batch** out);
 PFM_API void pfm_batch_destroy(pfm_batch* b);
 PFM_API int pfm_batch_size(const pfm_batch* b);
+/* "batched_tma_dag" or "batched": the kernel family of pfm_batch_iterate. */
+PFM_API const char* pfm_batch_kernel_variant(const pfm_batch* b);
 PFM_API pfm_status pfm_batch_member(pfm_batch* b, int index, pfm_problem** out);
 /* n_iters >= 0 iterations of every member (asynchronous). */
 PFM_API pfm_status pfm_batch_iterate(pfm_batch* b, int n_iters);

@@ -72,6 +72,7 @@ _SIGS = {
     "pfm_batch_create": (C.c_int, [C.c_int, C.c_void_p, C.POINTER(pfm_params), _P, C.POINTER(_P)]),
     "pfm_batch_destroy": (None, [_P]),
     "pfm_batch_size": (C.c_int, [_P]),
+    "pfm_batch_kernel_variant": (C.c_char_p, [_P]),
     "pfm_batch_member": (C.c_int, [_P, C.c_int, C.POINTER(_P)]),
     "pfm_batch_iterate": (C.c_int, [_P, C.c_int]),
     "pfm_batch_energy": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
@@ -411,6 +412,11 @@ class Batch:
     @property
     def launches(self):
         return lib().pfm_batch_launch_count(self._h)
+
+    @property
+    def variant(self):
+        """Kernel family of iterate(): "batched_tma_dag" or "batched"."""
+        return lib().pfm_batch_kernel_variant(self._h).decode()
 
 
 def alm_footprint(spatial, nl, has_S_field=True):

@@ -819,6 +819,7 @@ struct pfm_batch {
     int sms = 0;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     int64_t launches = 0;
+    bool tma = false;  // members run the TMA-staged DAG kernel
 };
 
 namespace {
@@ -905,19 +906,6 @@ pfm_status pfm_batch_create(int n, const pfm_desc* descs, const pfm_params* para
         maxn = std::max(maxn, pb->nn);
         any_dag = any_dag || !pb->flat;
     }
-    const bool bf16 = params->storage == PFM_STORAGE_BF16;
-    if (!any_dag) {
-        const int ml = potts_bucket(maxl);
-        b->runner = bf16 ? pfm::make_batch_potts_bf16(ml, ndim) : pfm::make_batch_potts_f32(ml, ndim);
-    } else {
-        int ml, mn;
-        dag_bucket(maxl, maxn, &ml, &mn);
-        if (ml) b->runner = bf16 ? pfm::make_batch_dag_bf16(ml, mn, ndim) : pfm::make_batch_dag_f32(ml, mn, ndim);
-    }
-    if (!b->runner) {
-        batch_free(b);
-        return fail(PFM_EUNSUPPORTED, "no batched kernel bucket for these members");
-    }
     for (pfm_problem* pb : b->probs) {
         pfm::BatchMember m;
         m.view = view_of(pb);
@@ -926,6 +914,26 @@ pfm_status pfm_batch_create(int n, const pfm_desc* descs, const pfm_params* para
             m.q[k] = pb->q[k];
         }
         b->members.push_back(m);
+    }
+    const bool bf16 = params->storage == PFM_STORAGE_BF16;
+    // DAG members on the TMA-staged kernel when every member fits it (the
+    // default schedule); PFM_SCHEDULE_FUSED_PLAIN keeps the register-staged one
+    if (any_dag && params->schedule == PFM_SCHEDULE_FUSED) {
+        b->runner = bf16 ? pfm::make_batch_dag_tma_bf16(b->members.data(), n, ndim)
+                         : pfm::make_batch_dag_tma_f32(b->members.data(), n, ndim);
+        b->tma = b->runner != nullptr;
+    }
+    if (!b->runner && !any_dag) {
+        const int ml = potts_bucket(maxl);
+        b->runner = bf16 ? pfm::make_batch_potts_bf16(ml, ndim) : pfm::make_batch_potts_f32(ml, ndim);
+    } else if (!b->runner) {
+        int ml, mn;
+        dag_bucket(maxl, maxn, &ml, &mn);
+        if (ml) b->runner = bf16 ? pfm::make_batch_dag_bf16(ml, mn, ndim) : pfm::make_batch_dag_f32(ml, mn, ndim);
+    }
+    if (!b->runner) {
+        batch_free(b);
+        return fail(PFM_EUNSUPPORTED, "no batched kernel bucket for these members");
     }
     int dev = 0;
     cudaGetDevice(&dev);
@@ -944,6 +952,11 @@ void pfm_batch_destroy(pfm_batch* b) {
 }
 
 int pfm_batch_size(const pfm_batch* b) { return b ? (int)b->probs.size() : 0; }
+
+const char* pfm_batch_kernel_variant(const pfm_batch* b) {
+    if (!b) return "";
+    return b->tma ? "batched_tma_dag" : "batched";
+}
 
 pfm_status pfm_batch_member(pfm_batch* b, int index, pfm_problem** out) {
     if (!b || !out || index < 0 || index >= (int)b->probs.size()) return fail(PFM_EINVAL, "bad batch member index");

@@ -19,4 +19,10 @@ BatchBase* make_batch_dag_bf16(int maxl, int maxn, int dim) {
     return nullptr;
 }
 
+BatchBase* make_batch_dag_tma_bf16(const BatchMember* m, int n, int dim) {
+    if (dim == 3) return BatchDagTma<3, __nv_bfloat16>::fits(m, n) ? new BatchDagTma<3, __nv_bfloat16>() : nullptr;
+    if (dim == 2) return BatchDagTma<2, __nv_bfloat16>::fits(m, n) ? new BatchDagTma<2, __nv_bfloat16>() : nullptr;
+    return nullptr;
+}
+
 }  // namespace pfm

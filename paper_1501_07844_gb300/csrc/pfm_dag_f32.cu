@@ -19,4 +19,10 @@ BatchBase* make_batch_dag_f32(int maxl, int maxn, int dim) {
     return nullptr;
 }
 
+BatchBase* make_batch_dag_tma_f32(const BatchMember* m, int n, int dim) {
+    if (dim == 3) return BatchDagTma<3, float>::fits(m, n) ? new BatchDagTma<3, float>() : nullptr;
+    if (dim == 2) return BatchDagTma<2, float>::fits(m, n) ? new BatchDagTma<2, float>() : nullptr;
+    return nullptr;
+}
+
 }  // namespace pfm

@@ -37,6 +37,78 @@ struct ProblemView {
     const float* W;        // host [nn][nl] path weights (DAG) or nullptr
 };
 
+// Host side of the TMA DAG kernels.  Sparse path-weight lists over the
+// flow-carrying nodes (nodes from nf on have zero capacity and identically
+// zero flow) and the shared-memory layout; false if three stages do not fit
+// in the 227 KB a CTA may use (dynamic + the lists staged statically).
+inline bool build_dag_lists(const StepArgs<DMAX, DMAX>& a, int dim, int es, DagLists* lists, DagTmaLayout* lay) {
+    if ((a.px * es) % 16 != 0 || (a.px * 4) % 16 != 0) return false;
+    int nf = 1;
+    for (int A = 0; A < a.nn; ++A)
+        if (a.s_node[A] > 0.f) nf = A + 1;
+    *lay = DagTmaLayout(a.nl, nf, dim, es);
+    if (lay->total + (int)sizeof(DagLists) + 64 > 227 * 1024) return false;
+    *lists = DagLists{};
+    lists->nf = nf;
+    for (int A = 0; A < nf; ++A)
+        for (int j = 0; j < a.nl; ++j)
+            if (a.W[A][j] != 0.f) {
+                lists->anc[j][lists->anc_n[j]] = (unsigned char)A;
+                lists->anc_w[j][lists->anc_n[j]++] = a.W[A][j];
+                lists->desc[A][lists->desc_n[A]] = (unsigned char)j;
+                lists->desc_w[A][lists->desc_n[A]++] = a.W[A][j];
+            }
+    return true;
+}
+
+// Tensor maps of one parity of a DAG problem: logical extents, pitched
+// strides; the flow box covers the nf flow-carrying nodes.
+inline bool encode_dag_maps(const StepArgs<DMAX, DMAX>& a, int dim, int es, int nf, const void* u, const void* q,
+                            const float* D, const float* S, TmaMaps* m) {
+    const int qbx = FTX + 2 * (16 / es);
+    const unsigned long long nx = a.nx, ny = a.ny, nz = a.nz, px = a.px;
+    const unsigned long long dims_u[4] = {nx, ny, nz, (unsigned long long)a.nl};
+    const unsigned long long dims_q[4] = {nx, ny, nz, (unsigned long long)dim * a.nn};
+    const unsigned long long st_t[3] = {px * es, px * ny * es, px * ny * nz * es};
+    const unsigned long long st_f[3] = {px * 4, px * ny * 4, px * ny * nz * 4};
+    const unsigned box_u[4] = {(unsigned)TMA_BX, (unsigned)DAG_UY, 1u, (unsigned)a.nl};
+    const unsigned box_q[4] = {(unsigned)qbx, (unsigned)DAG_QY, 1u, (unsigned)(dim * nf)};
+    const unsigned long long dims_s[3] = {nx, ny, nz};
+    const unsigned box_s[3] = {(unsigned)FTX, (unsigned)DTY, 1u};
+    if (!encode_tiled_map(&m->u, u, es, 4, dims_u, st_t, box_u)) return false;
+    if (!encode_tiled_map(&m->q, q, es, 4, dims_q, st_t, box_q)) return false;
+    if (!encode_tiled_map(&m->D, D, 4, 4, dims_u, st_f, box_u)) return false;
+    if (S) return encode_tiled_map(&m->S, S, 4, 3, dims_s, st_f, box_s);
+    m->S = m->D;  // never read: the kernel skips S when the problem has no field
+    return true;
+}
+
+// Kernel arguments of a problem (one parity's buffers filled in by the caller).
+template <int MAXL, int MAXN, bool IS_DAG>
+StepArgs<MAXL, MAXN> make_step_args(const ProblemView& v, int zc) {
+    StepArgs<MAXL, MAXN> a{};
+    a.D = v.D;
+    a.S = v.S;
+    a.abuf = v.abuf;
+    a.flags = v.flags;
+    a.nx = v.nx;
+    a.px = v.px;
+    a.ny = v.ny;
+    a.nz = v.nz;
+    a.nl = v.nl;
+    a.nn = v.nn;
+    a.n = v.n;
+    a.literal = v.literal;
+    a.aniso = v.aniso;
+    a.inv_c = 1.0f / v.c;
+    a.ctau = v.c * v.tau;
+    a.zc = zc;
+    for (int A = 0; A < MAXN; ++A) a.s_node[A] = A < v.nn ? v.s_node[A] : 0.f;
+    for (int A = 0; A < MAXN; ++A)
+        for (int j = 0; j < MAXL; ++j) a.W[A][j] = (IS_DAG && A < v.nn && j < v.nl) ? v.W[A * v.nl + j] : 0.f;
+    return a;
+}
+
 struct SolverBase {
     virtual ~SolverBase() {}
     // One iteration reading (u_in, q_in) and writing (u_out, q_out); for the
@@ -79,25 +151,7 @@ struct Solver final : SolverBase {
     DagLists lists{};
 
     explicit Solver(const ProblemView& v) {
-        base.D = v.D;
-        base.S = v.S;
-        base.abuf = v.abuf;
-        base.flags = v.flags;
-        base.nx = v.nx;
-        base.px = v.px;
-        base.ny = v.ny;
-        base.nz = v.nz;
-        base.nl = v.nl;
-        base.nn = v.nn;
-        base.n = v.n;
-        base.literal = v.literal;
-        base.aniso = v.aniso;
-        base.inv_c = 1.0f / v.c;
-        base.ctau = v.c * v.tau;
-        for (int A = 0; A < MAXN; ++A) base.s_node[A] = A < v.nn ? v.s_node[A] : 0.f;
-        for (int A = 0; A < MAXN; ++A)
-            for (int j = 0; j < MAXL; ++j)
-                base.W[A][j] = (IS_DAG && A < v.nn && j < v.nl) ? v.W[A * v.nl + j] : 0.f;
+        base = make_step_args<MAXL, MAXN, IS_DAG>(v, 0);
         fused_smem = sizeof(float) * 3 * MAXL * FNE;
     }
 
@@ -178,48 +232,10 @@ struct Solver final : SolverBase {
     bool prepare_tma(void* const* u, void* const* q, const float* D, const float* S) override {
         if constexpr (kDagTmaCapable) {
             const int es = (int)sizeof(T);
-            if ((base.px * es) % 16 != 0 || (base.px * 4) % 16 != 0) return false;
-            // nodes from nf on have zero capacity: their flow is identically zero
-            int nf = 1;
-            for (int A = 0; A < base.nn; ++A)
-                if (base.s_node[A] > 0.f) nf = A + 1;
-            const DagTmaLayout lay(base.nl, nf, DIM, es);
-            // dynamic + static (the lists staged per CTA) within the 227 KB per CTA
-            if (lay.total + (int)sizeof(DagLists) + 64 > 227 * 1024) return false;
-            // sparse path-weight lists over the flow-carrying nodes: ancestors of
-            // each end-label, end-labels below each node (e_A = 0 beyond nf)
-            lists.nf = nf;
-            for (int j = 0; j < DMAX; ++j) lists.anc_n[j] = 0;
-            for (int A = 0; A < DMAX; ++A) lists.desc_n[A] = 0;
-            for (int A = 0; A < nf; ++A)
-                for (int j = 0; j < base.nl; ++j)
-                    if (base.W[A][j] != 0.f) {
-                        lists.anc[j][lists.anc_n[j]] = (unsigned char)A;
-                        lists.anc_w[j][lists.anc_n[j]++] = base.W[A][j];
-                        lists.desc[A][lists.desc_n[A]] = (unsigned char)j;
-                        lists.desc_w[A][lists.desc_n[A]++] = base.W[A][j];
-                    }
-            const int qbx = FTX + 2 * (16 / es);
-            // logical extents, pitched strides: the padding is outside every box
-            const unsigned long long nx = base.nx, ny = base.ny, nz = base.nz, px = base.px;
-            const unsigned long long dims_u[4] = {nx, ny, nz, (unsigned long long)base.nl};
-            const unsigned long long dims_q[4] = {nx, ny, nz, (unsigned long long)DIM * base.nn};
-            const unsigned long long st_t[3] = {px * es, px * ny * es, px * ny * nz * es};
-            const unsigned long long st_f[3] = {px * 4, px * ny * 4, px * ny * nz * 4};
-            const unsigned box_u[4] = {(unsigned)TMA_BX, (unsigned)DAG_UY, 1u, (unsigned)base.nl};
-            const unsigned box_q[4] = {(unsigned)qbx, (unsigned)DAG_QY, 1u, (unsigned)(DIM * nf)};
-            const unsigned long long dims_s[3] = {nx, ny, nz};
-            const unsigned box_s[3] = {(unsigned)FTX, (unsigned)DTY, 1u};
+            DagTmaLayout lay(1, 1, DIM, es);
+            if (!build_dag_lists(base, DIM, es, &lists, &lay)) return false;
             for (int k = 0; k < 2; ++k) {
-                TmaMaps& m = tma_maps[k];
-                if (!encode_tiled_map(&m.u, u[k], es, 4, dims_u, st_t, box_u)) return false;
-                if (!encode_tiled_map(&m.q, q[k], es, 4, dims_q, st_t, box_q)) return false;
-                if (!encode_tiled_map(&m.D, D, 4, 4, dims_u, st_f, box_u)) return false;
-                if (S) {
-                    if (!encode_tiled_map(&m.S, S, 4, 3, dims_s, st_f, box_s)) return false;
-                } else {
-                    m.S = m.D;
-                }
+                if (!encode_dag_maps(base, DIM, es, lists.nf, u[k], q[k], D, S, &tma_maps[k])) return false;
                 tma_u[k] = u[k];
             }
             dag_tma_ready = true;
@@ -338,29 +354,7 @@ struct BatchRunner final : BatchBase {
         if (items) cudaFree(items);
     }
 
-    static Args make_args(const ProblemView& v, int zc) {
-        Args a{};
-        a.D = v.D;
-        a.S = v.S;
-        a.abuf = v.abuf;
-        a.flags = v.flags;
-        a.nx = v.nx;
-        a.px = v.px;
-        a.ny = v.ny;
-        a.nz = v.nz;
-        a.nl = v.nl;
-        a.nn = v.nn;
-        a.n = v.n;
-        a.literal = v.literal;
-        a.aniso = v.aniso;
-        a.inv_c = 1.0f / v.c;
-        a.ctau = v.c * v.tau;
-        a.zc = zc;
-        for (int A = 0; A < MAXN; ++A) a.s_node[A] = A < v.nn ? v.s_node[A] : 0.f;
-        for (int A = 0; A < MAXN; ++A)
-            for (int j = 0; j < MAXL; ++j) a.W[A][j] = (IS_DAG && A < v.nn && j < v.nl) ? v.W[A * v.nl + j] : 0.f;
-        return a;
-    }
+    static Args make_args(const ProblemView& v, int zc) { return make_step_args<MAXL, MAXN, IS_DAG>(v, zc); }
 
     cudaError_t setup(const BatchMember* m, int n, int zc) override {
         if (dev) cudaFree(dev);
@@ -416,6 +410,105 @@ struct BatchRunner final : BatchBase {
     }
 };
 
+// Batched DAG iteration on the TMA-staged kernel: one persistent launch per
+// iteration walks (member, x tile, y tile, z chunk) items; per member and
+// parity the arguments and tensor maps sit in device memory, the lists once
+// per member.
+template <int DIM, typename T>
+struct BatchDagTma final : BatchBase {
+    using Args = StepArgs<DMAX, DMAX>;
+    Args* args = nullptr;     // [2][nvol]
+    TmaMaps* maps = nullptr;  // [2][nvol]
+    DagLists* lists = nullptr;
+    int4* items = nullptr;
+    int nvol = 0, nitems = 0, smem = 0, bar_off = 0;
+
+    ~BatchDagTma() override { release(); }
+
+    void release() {
+        if (args) cudaFree(args);
+        if (maps) cudaFree(maps);
+        if (lists) cudaFree(lists);
+        if (items) cudaFree(items);
+        args = nullptr;
+        maps = nullptr;
+        lists = nullptr;
+        items = nullptr;
+    }
+
+    // True if every member can run the TMA DAG kernel.
+    static bool fits(const BatchMember* m, int n) {
+        for (int k = 0; k < n; ++k) {
+            if (m[k].view.nl > DMAX || m[k].view.nn > DMAX) return false;
+            DagLists l;
+            DagTmaLayout lay(1, 1, DIM, (int)sizeof(T));
+            if (!build_dag_lists(make_step_args<DMAX, DMAX, true>(m[k].view, 1), DIM, (int)sizeof(T), &l, &lay))
+                return false;
+        }
+        return true;
+    }
+
+    cudaError_t setup(const BatchMember* m, int n, int zc) override {
+        release();
+        nvol = n;
+        const int es = (int)sizeof(T);
+        std::vector<Args> ha(2 * (size_t)n);
+        std::vector<TmaMaps> hm(2 * (size_t)n);
+        std::vector<DagLists> hl((size_t)n);
+        std::vector<int4> work;
+        smem = 0;
+        bar_off = 0;
+        for (int k = 0; k < n; ++k) {
+            const ProblemView& v = m[k].view;
+            const Args base = make_step_args<DMAX, DMAX, true>(v, zc);
+            DagTmaLayout lay(1, 1, DIM, es);
+            if (!build_dag_lists(base, DIM, es, &hl[k], &lay)) return cudaErrorInvalidValue;
+            smem = std::max(smem, lay.total);
+            bar_off = std::max(bar_off, lay.bar_off);
+            for (int p = 0; p < 2; ++p) {
+                Args a = base;
+                a.u_in = m[k].u[p];
+                a.u_out = m[k].u[1 - p];
+                a.q_in = m[k].q[p];
+                a.q_out = m[k].q[1 - p];
+                ha[(size_t)p * n + k] = a;
+                if (!encode_dag_maps(base, DIM, es, hl[k].nf, m[k].u[p], m[k].q[p], v.D, v.S, &hm[(size_t)p * n + k]))
+                    return cudaErrorInvalidValue;
+            }
+            // x tiles fastest, so the CTAs that run together are neighbours
+            for (int bz = 0; bz < (v.nz + zc - 1) / zc; ++bz)
+                for (int by = 0; by < (v.ny + DTY - 1) / DTY; ++by)
+                    for (int bx = 0; bx < (v.nx + FTX - 1) / FTX; ++bx) work.push_back(make_int4(k, bx, by, bz));
+        }
+        // the barriers sit past every member's buffers; + 64 bytes for them
+        smem = std::max(smem, bar_off + 64 + 128);
+        nitems = (int)work.size();
+        cudaError_t e;
+        if ((e = cudaMalloc(&args, sizeof(Args) * ha.size())) != cudaSuccess) return e;
+        if ((e = cudaMalloc(&maps, sizeof(TmaMaps) * hm.size())) != cudaSuccess) return e;
+        if ((e = cudaMalloc(&lists, sizeof(DagLists) * hl.size())) != cudaSuccess) return e;
+        if ((e = cudaMalloc(&items, sizeof(int4) * work.size())) != cudaSuccess) return e;
+        if ((e = cudaMemcpy(args, ha.data(), sizeof(Args) * ha.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return e;
+        if ((e = cudaMemcpy(maps, hm.data(), sizeof(TmaMaps) * hm.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
+            return e;
+        if ((e = cudaMemcpy(lists, hl.data(), sizeof(DagLists) * hl.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
+            return e;
+        if ((e = cudaMemcpy(items, work.data(), sizeof(int4) * work.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
+            return e;
+        return cudaFuncSetAttribute(batched_dag_tma_kernel<DIM, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    }
+
+    cudaError_t launch(int parity, int grid, cudaStream_t s) override {
+        batched_dag_tma_kernel<DIM, T><<<grid, DAG_TMA_NT, smem, s>>>(args + (size_t)parity * nvol,
+                                                                      maps + (size_t)parity * nvol, lists, items,
+                                                                      nitems, bar_off);
+        return cudaGetLastError();
+    }
+
+    int n_items() const override { return nitems; }
+    int ctas_per_sm() const override { return 1; }
+};
+
 // Factories, one per translation unit (storage x model).
 SolverBase* make_potts_f32(int maxl, int dim, const ProblemView& v);
 SolverBase* make_potts_bf16(int maxl, int dim, const ProblemView& v);
@@ -425,6 +518,9 @@ BatchBase* make_batch_potts_f32(int maxl, int dim);
 BatchBase* make_batch_potts_bf16(int maxl, int dim);
 BatchBase* make_batch_dag_f32(int maxl, int maxn, int dim);
 BatchBase* make_batch_dag_bf16(int maxl, int maxn, int dim);
+// The TMA DAG batch, or nullptr if some member cannot run the TMA DAG kernel.
+BatchBase* make_batch_dag_tma_f32(const BatchMember* m, int n, int dim);
+BatchBase* make_batch_dag_tma_bf16(const BatchMember* m, int n, int dim);
 
 // Adjoint of one Potts iteration (pfm_adjoint.cu).
 struct AdjLaunch {

@@ -65,31 +65,41 @@ struct DagTmaLayout {
     }
 };
 
+// Stage bookkeeping carried across the tiles a CTA processes: bit k of
+// `phase` is the parity of the next completion of stage k's mbarrier (every
+// thread keeps it); bit k of `pending` marks a fill of stage k not yet
+// waited for (thread 0 keeps it, for the drain after a timeout).
+struct DagRing {
+    unsigned phase = 0, pending = 0;
+};
+
+// One tile (bx, by) of z-chunk bz of one problem.  sl is the problem's lists
+// in shared memory; smem the aligned dynamic shared memory; bar0 the three
+// mbarriers (initialised by the caller).  Returns false after a timed-out
+// wait (FLAG_TIMEOUT raised; the caller drains and stops).  Every thread of
+// the CTA calls it; it ends with a CTA barrier.
 template <int DIM, typename T>
-__global__ void __launch_bounds__(DAG_TMA_NT, 1)
-fused_dag_tma_kernel(const StepArgs<DMAX, DMAX> a, const __grid_constant__ TmaMaps maps,
-                     const __grid_constant__ DagLists lists) {
+__device__ __forceinline__ bool dag_tma_tile(const StepArgs<DMAX, DMAX>& a, const TmaMaps& maps, const DagLists& sl,
+                                             int bx, int by, int bz, unsigned char* smem, unsigned bar0,
+                                             DagRing& ring) {
     constexpr int QOFF = 16 / (int)sizeof(T);
     constexpr int QBX = FTX + 2 * QOFF;
     constexpr int qstride = DAG_QY * QBX;
     constexpr int ustride = DAG_UY * TMA_BX;
     constexpr int PER = DMAX / 4;  // labels / nodes per thread at most
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ int s_abort;
-    // the four lanes of a voxel walk different lists: read them from shared
-    // memory (lane-dependent constant-bank loads would serialise)
-    __shared__ DagLists sl;
-    unsigned char* smem = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
-    const int nl = a.nl, nf = lists.nf;
+    // scalars read once (the batched kernel's arguments live in global memory)
+    const int nl = a.nl, nf = sl.nf;
+    const int nx = a.nx, ny = a.ny, nz = a.nz, px = a.px, literal = a.literal, aniso = a.aniso;
+    const float ctau = a.ctau;
     const DagTmaLayout lay(nl, nf, DIM, (int)sizeof(T));
     const int t = threadIdx.x;
     const int h = t & 3;
     const int v = t >> 2;
-    const int x0 = blockIdx.x * FTX, y0 = blockIdx.y * DTY;
-    const int z0 = blockIdx.z * a.zc;
-    const int z1 = min(z0 + a.zc, a.nz);
+    const int x0 = bx * FTX, y0 = by * DTY;
+    const int z0 = bz * a.zc;
+    const int z1 = min(z0 + a.zc, nz);
     const long long n = a.n;
-    const long long plane = (long long)a.px * a.ny;
+    const long long plane = (long long)px * ny;
     T* __restrict__ uout = static_cast<T*>(a.u_out);
     T* __restrict__ qout = static_cast<T*>(a.q_out);
     const int has_S = a.S != nullptr;
@@ -97,7 +107,6 @@ fused_dag_tma_kernel(const StepArgs<DMAX, DMAX> a, const __grid_constant__ TmaMa
     const unsigned bytes_d = (unsigned)(nl * ustride * 4);
     const unsigned bytes_q = (unsigned)(DIM * nf * qstride * sizeof(T));
     const unsigned bytes_s = has_S ? (unsigned)(FTX * DTY * 4) : 0u;
-    const unsigned bar0 = smem_addr(smem + lay.bar_off);
     const float kexp = -a.inv_c * 1.4426950408889634f;
     float* gbuf = reinterpret_cast<float*>(smem + lay.g_off);
     float* ebuf = reinterpret_cast<float*>(smem + lay.e_off);
@@ -106,6 +115,7 @@ fused_dag_tma_kernel(const StepArgs<DMAX, DMAX> a, const __grid_constant__ TmaMa
     auto stage_ptr = [&](int k) { return smem + k * lay.stage_bytes; };
     auto issue = [&](int p, int k, bool flows_only) {
         const unsigned bar = bar0 + 8 * k;
+        ring.pending |= 1u << k;
         unsigned char* st = stage_ptr(k);
         mbar_expect_tx(bar, flows_only ? bytes_q : bytes_u + bytes_d + bytes_q + bytes_s);
         tma_load_4d(smem_addr(st + lay.q_off), &maps.q, x0 - QOFF, y0 - 1, p, 0, bar);
@@ -118,23 +128,20 @@ fused_dag_tma_kernel(const StepArgs<DMAX, DMAX> a, const __grid_constant__ TmaMa
 
     // an iteration reads only the stage of its own plane (the voxel's flows
     // and S of the previous plane stay in registers): the ring runs two
-    // planes ahead
-    int inflight_hi = z0;
+    // planes ahead.  Plane p of the tile lives in stage (p - z0 + 1) % 3.
+    auto wait_stage = [&](int k) {
+        const bool r = mbar_wait_bounded(bar0 + 8 * k, (ring.phase >> k) & 1u);
+        if (r) {
+            ring.phase ^= 1u << k;
+            if (t == 0) ring.pending &= ~(1u << k);
+        }
+        return r;
+    };
     if (t == 0) {
-        for (int k = 0; k < TMA_STAGES; ++k) mbar_init(bar0 + 8 * k, 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        s_abort = 0;
         issue(z0 - 1, 0, true);
         issue(z0, 1, false);
-        if (z0 + 1 <= z1 && z0 + 1 < a.nz) {
-            issue(z0 + 1, 2, false);
-            inflight_hi = z0 + 1;
-        }
+        if (z0 + 1 <= z1 && z0 + 1 < nz) issue(z0 + 1, 2, false);
     }
-    static_assert(sizeof(DagLists) % 4 == 0, "lists copied as words");
-    for (int k = t; k < (int)(sizeof(DagLists) / 4); k += DAG_TMA_NT)
-        reinterpret_cast<int*>(&sl)[k] = reinterpret_cast<const int*>(&lists)[k];
-    __syncthreads();
 
     // Voxel of this thread quad on the halo-extended 33 x 5 tile, owned voxels
     // first (v < 128: the 32 x 4 tile), then the y-halo row (ey = 4) and the
@@ -146,14 +153,14 @@ fused_dag_tma_kernel(const StepArgs<DMAX, DMAX> a, const __grid_constant__ TmaMa
     const int ex = v < FTX * DTY ? (v & (FTX - 1)) : v < FTX * DTY + FTX ? v - FTX * DTY : FTX;
     const int ey = v < FTX * DTY ? v / FTX : v < FTX * DTY + FTX ? DTY : v - (FTX * DTY + FTX);
     const int xe = x0 + ex, ye = y0 + ey;
-    const bool validE = inE && xe < a.nx && ye < a.ny;
+    const bool validE = inE && xe < nx && ye < ny;
     const bool ownerE = validE && v < FTX * DTY;
     float* erow = ebuf + (inE ? v : 0) * lay.row;
     const int ui = ey * TMA_BX + ex;
     const int qi = (ey + 1) * QBX + (ex + QOFF);
     // zero steps at the last index (the g slots outside the grid hold zeros)
-    const float cx = xe < a.nx - 1 ? a.ctau : 0.f;
-    const float cy = ye < a.ny - 1 ? a.ctau : 0.f;
+    const float cx = xe < nx - 1 ? ctau : 0.f;
+    const float cy = ye < ny - 1 ? ctau : 0.f;
 
     for (int k = t; k < 2 * g_elems; k += DAG_TMA_NT) gbuf[k] = 0.f;
     // capacities of this thread's nodes, read once (lane-dependent parameter
@@ -168,7 +175,7 @@ fused_dag_tma_kernel(const StepArgs<DMAX, DMAX> a, const __grid_constant__ TmaMa
         gprev[i] = gcur[i] = qxp[i] = qyp[i] = qzp[i] = 0.f;
     }
     // z flows of plane z0-1 (its x / y flow steps belong to the previous chunk)
-    bool ok = mbar_wait_bounded(bar0, 0u);
+    bool ok = wait_stage(0);
     if constexpr (DIM == 3) {
         if (ok && validE) {
             const T* q0 = reinterpret_cast<const T*>(stage_ptr(0) + lay.q_off);
@@ -180,31 +187,28 @@ fused_dag_tma_kernel(const StepArgs<DMAX, DMAX> a, const __grid_constant__ TmaMa
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     if (__syncthreads_or(!ok)) {
         if (t == 0) atomicOr(a.flags, FLAG_TIMEOUT);
-        s_abort = 1;
+        return false;
     }
     bool bad = false;
-    int p_stop = z0 - 1;  // first plane whose stage may still be in flight at an abort
-    for (int p = z0; p <= z1 && !s_abort; ++p) {
+    bool alive = true;
+    for (int p = z0; p <= z1; ++p) {
         const int s = p - z0 + 1;
         const int cs = s % 3, ps = (s + 2) % 3;
         // stage ps held plane p-1, last read before the previous barrier
-        if (t == 0 && p + 2 <= z1 && p + 2 < a.nz) {
-            issue(p + 2, ps, false);
-            inflight_hi = p + 2;
-        }
+        if (t == 0 && p + 2 <= z1 && p + 2 < nz) issue(p + 2, ps, false);
         unsigned char* cst = stage_ptr(cs);
         float* gC = gbuf + (p & 1) * g_elems;
         const float* gP = gbuf + ((p + 1) & 1) * g_elems;
         // each thread waits itself; a timeout reaches the CTA at the barrier
         ok = true;
-        if (p < a.nz) ok = mbar_wait_bounded(bar0 + 8 * cs, (unsigned)((s / 3) & 1));
+        if (p < nz) ok = wait_stage(cs);
         if (!ok) atomicOr(a.flags, FLAG_TIMEOUT);
         float qxc[PER], qyc[PER], qzc[PER];
 #pragma unroll
         for (int i = 0; i < PER; ++i) qxc[i] = qyc[i] = qzc[i] = 0.f;
         float scur = 1.0f;
 
-        if (p < a.nz) {
+        if (p < nz) {
             const T* uS = reinterpret_cast<const T*>(cst + lay.u_off);
             const float* dS = reinterpret_cast<const float*>(cst + lay.d_off);
             const T* qS = reinterpret_cast<const T*>(cst + lay.q_off);
@@ -248,7 +252,7 @@ fused_dag_tma_kernel(const StepArgs<DMAX, DMAX> a, const __grid_constant__ TmaMa
             }
             float m = fminf(mloc, __shfl_xor_sync(0xffffffffu, mloc, 1));
             m = fminf(m, __shfl_xor_sync(0xffffffffu, m, 2));
-            if (a.literal) m = 0.f;
+            if (literal) m = 0.f;
             float sloc = 0.f;
 #pragma unroll
             for (int i = 0; i < PER; ++i) {
@@ -265,13 +269,13 @@ fused_dag_tma_kernel(const StepArgs<DMAX, DMAX> a, const __grid_constant__ TmaMa
             if (validE) {
                 if (!((sum > 0.f) && (sum <= 3.0e38f))) bad = true;
                 const float inv = rcp_fast(sum);
-                const long long i0 = (long long)p * plane + (long long)ye * a.px + xe;
+                const long long i0 = (long long)p * plane + (long long)ye * px + xe;
 #pragma unroll
                 for (int i = 0; i < PER; ++i) {
                     const int j = h + 4 * i;
                     if (j < nl) {
                         const float un = u[i] * inv;
-                        erow[j] = a.literal ? u[i] : un;
+                        erow[j] = literal ? u[i] : un;
                         if (ownerE && p < z1) stv<T>(uout + (long long)j * n + i0, un);
                     }
                 }
@@ -299,8 +303,8 @@ fused_dag_tma_kernel(const StepArgs<DMAX, DMAX> a, const __grid_constant__ TmaMa
         const int pm = p - 1;
         if (pm >= z0 && ownerE) {
             const float sf = sprev;
-            const long long i0 = (long long)pm * plane + (long long)ye * a.px + xe;
-            const float cz = pm < a.nz - 1 ? a.ctau : 0.f;
+            const long long i0 = (long long)pm * plane + (long long)ye * px + xe;
+            const float cz = pm < nz - 1 ? ctau : 0.f;
 #pragma unroll
             for (int i = 0; i < PER; ++i) {
                 const int A = h + 4 * i;
@@ -311,7 +315,7 @@ fused_dag_tma_kernel(const StepArgs<DMAX, DMAX> a, const __grid_constant__ TmaMa
                     yv[0] = qxp[i] - cx * (gA[1] - g0);
                     yv[1] = qyp[i] - cy * (gA[TMA_BX] - g0);
                     if constexpr (DIM == 3) yv[2] = qzp[i] - cz * (gcur[i] - g0);
-                    project_nb<DIM>(yv, cap[i] * sf, a.aniso);
+                    project_nb<DIM>(yv, cap[i] * sf, aniso);
                     T* qa = qout + (long long)A * DIM * n + i0;
 #pragma unroll
                     for (int k = 0; k < DIM; ++k) stv<T>(qa + k * n, yv[k]);
@@ -327,20 +331,83 @@ fused_dag_tma_kernel(const StepArgs<DMAX, DMAX> a, const __grid_constant__ TmaMa
         }
         sprev = scur;
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        p_stop = p;
         if (__syncthreads_or(!ok)) {
-            if (t == 0) s_abort = 1;
+            alive = false;
             break;
         }
     }
     if (bad) atomicOr(a.flags, FLAG_NONFINITE);
-    if (s_abort && t == 0) {
-        // bounded drain: the plane whose wait gave up and every plane issued after it
-        for (int p = p_stop; p <= inflight_hi; ++p) {
-            const int s = p - z0 + 1;
-            mbar_wait_bounded(bar0 + 8 * (s % 3), (unsigned)((s / 3) & 1));
-        }
+    return alive;
+}
+
+// Bounded drain of the fills still in flight after a timed-out wait (thread 0).
+__device__ __forceinline__ void dag_ring_drain(unsigned bar0, const DagRing& ring) {
+    for (int k = 0; k < TMA_STAGES; ++k)
+        if ((ring.pending >> k) & 1u) mbar_wait_bounded(bar0 + 8 * k, (ring.phase >> k) & 1u);
+}
+
+// Copies a problem's lists into shared memory (the four lanes of a voxel
+// walk different lists; lane-dependent constant-bank reads would serialise).
+__device__ __forceinline__ void dag_stage_lists(DagLists* sl, const DagLists* src) {
+    static_assert(sizeof(DagLists) % 4 == 0, "lists copied as words");
+    for (int k = threadIdx.x; k < (int)(sizeof(DagLists) / 4); k += DAG_TMA_NT)
+        reinterpret_cast<int*>(sl)[k] = reinterpret_cast<const int*>(src)[k];
+}
+
+__device__ __forceinline__ unsigned char* dag_smem_base(unsigned char* raw) {
+    return raw + ((128u - (smem_addr(raw) & 127u)) & 127u);
+}
+
+// One problem: CTA = (x tile, y tile, z chunk).
+template <int DIM, typename T>
+__global__ void __launch_bounds__(DAG_TMA_NT, 1)
+fused_dag_tma_kernel(const StepArgs<DMAX, DMAX> a, const __grid_constant__ TmaMaps maps,
+                     const __grid_constant__ DagLists lists) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ DagLists sl;
+    unsigned char* smem = dag_smem_base(smem_raw);
+    const DagTmaLayout lay(a.nl, lists.nf, DIM, (int)sizeof(T));
+    const unsigned bar0 = smem_addr(smem + lay.bar_off);
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < TMA_STAGES; ++k) mbar_init(bar0 + 8 * k, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    dag_stage_lists(&sl, &lists);
+    __syncthreads();
+    DagRing ring;
+    if (!dag_tma_tile<DIM, T>(a, maps, sl, blockIdx.x, blockIdx.y, blockIdx.z, smem, bar0, ring) &&
+        threadIdx.x == 0)
+        dag_ring_drain(bar0, ring);
+}
+
+// Many problems in one persistent launch: CTAs take (problem, x tile,
+// y tile, z chunk) items round-robin; args, maps and lists are per problem
+// (this launch's parity), the maps in global memory (64-byte aligned,
+// written before the launch).  The mbarrier ring carries over from item to
+// item; dynamic shared memory is sized for the largest problem layout.
+template <int DIM, typename T>
+__global__ void __launch_bounds__(DAG_TMA_NT, 1)
+batched_dag_tma_kernel(const StepArgs<DMAX, DMAX>* __restrict__ args, const TmaMaps* __restrict__ maps,
+                       const DagLists* __restrict__ lists, const int4* __restrict__ items, int n_items,
+                       int bar_off) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ DagLists sl;
+    unsigned char* smem = dag_smem_base(smem_raw);
+    const unsigned bar0 = smem_addr(smem + bar_off);
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < TMA_STAGES; ++k) mbar_init(bar0 + 8 * k, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    DagRing ring;
+    bool alive = true;
+    for (int it = blockIdx.x; it < n_items && alive; it += gridDim.x) {
+        const int4 w = items[it];
+        // the previous item ended with a CTA barrier: sl and the stages are free
+        dag_stage_lists(&sl, lists + w.x);
+        __syncthreads();
+        alive = dag_tma_tile<DIM, T>(args[w.x], maps[w.x], sl, w.y, w.z, w.w, smem, bar0, ring);
+    }
+    if (!alive && threadIdx.x == 0) dag_ring_drain(bar0, ring);
 }
 
 }  // namespace pfm

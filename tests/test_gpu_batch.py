@@ -1,7 +1,9 @@
 """Batched solver (pfm_batch_*): many volumes of uneven sizes and label DAGs
 advanced by one persistent kernel per iteration, replayed from CUDA graphs.
-Every member must equal the same problem solved on its own, bit for bit,
-and match the oracle."""
+Every member must equal the same problem solved on its own with the same
+kernel body, bit for bit (the TMA-staged DAG batch against the TMA DAG
+kernel, the register-staged batch against PFM_SCHEDULE_FUSED_PLAIN), and
+match the oracle."""
 import numpy as np
 import pytest
 
@@ -24,16 +26,19 @@ def dag_volumes(count=5, seed=4500):
     return out
 
 
+@pytest.mark.parametrize("sched", [0, 2], ids=["tma", "register"])
 @pytest.mark.parametrize("iters", [7, 20, 47], ids=["direct", "one_graph", "graphs_and_tail"])
-def test_batch_members_equal_single_problems(iters):
+def test_batch_members_equal_single_problems(iters, sched):
     import paper_1501_07844_gb300 as pfm
     vols = dag_volumes()
-    with pfm.Batch([as_dict(p) for p in vols]) as b:
+    with pfm.Batch([as_dict(p) for p in vols], schedule=sched) as b:
+        assert b.variant == ("batched_tma_dag" if sched == pfm.FUSED else "batched")
         b.iterate(iters)
         E_b, P_b = b.energy()
         for k, p in enumerate(vols):
-            # the batched kernel runs the register-staged tile body
-            with gpu_problem(p, schedule=pfm.FUSED_PLAIN) as single:
+            # the same tile body as the batched kernel
+            with gpu_problem(p, schedule=sched) as single:
+                assert single.variant == ("fused_tma_dag" if sched == pfm.FUSED else "fused")
                 single.iterate(iters)
                 m = b.members[k]
                 assert np.array_equal(m.labels().cpu().numpy(), single.labels().cpu().numpy())
@@ -43,10 +48,11 @@ def test_batch_members_equal_single_problems(iters):
                 assert m.iterations == iters
 
 
-def test_batch_matches_oracle_and_mixes_potts_and_dags():
+@pytest.mark.parametrize("sched", [0, 2], ids=["tma", "register"])
+def test_batch_matches_oracle_and_mixes_potts_and_dags(sched):
     import paper_1501_07844_gb300 as pfm
     vols = dag_volumes(3, seed=4600) + [synth.potts3d_problem(seed=4610, nl=8, shape=(14, 22, 37))]
-    with pfm.Batch([as_dict(p) for p in vols]) as b:
+    with pfm.Batch([as_dict(p) for p in vols], schedule=sched) as b:
         b.iterate(30)
         for k in (0, 3):
             p = vols[k]
@@ -56,16 +62,17 @@ def test_batch_matches_oracle_and_mixes_potts_and_dags():
             assert np.mean(np.argmax(u, 0) == np.argmax(u_o, 0)) >= 0.999
 
 
-def test_batch_tune_resets_and_keeps_results():
+@pytest.mark.parametrize("sched", [0, 2], ids=["tma", "register"])
+def test_batch_tune_resets_and_keeps_results(sched):
     import paper_1501_07844_gb300 as pfm
     vols = dag_volumes(4, seed=4700)
-    with pfm.Batch([as_dict(p) for p in vols]) as b:
+    with pfm.Batch([as_dict(p) for p in vols], schedule=sched) as b:
         b.iterate(5)
         zc, grid = b.tune(trial_iters=2)
         assert zc in (8, 16, 32, 64) and grid >= 1
         assert all(m.iterations == 0 for m in b.members)
         b.iterate(25)
-        with gpu_problem(vols[2], schedule=pfm.FUSED_PLAIN) as single:
+        with gpu_problem(vols[2], schedule=sched) as single:
             single.iterate(25)
             assert np.array_equal(b.members[2].labels().cpu().numpy(), single.labels().cpu().numpy())
 
@@ -74,6 +81,7 @@ def test_batch_bf16_and_2d():
     import paper_1501_07844_gb300 as pfm
     vols = [synth.random_problem(4800 + k, (30 + 7 * k, 41 - 5 * k), nl=5, s_kind="both") for k in range(4)]
     with pfm.Batch([as_dict(p) for p in vols], storage=pfm.BF16) as b:
+        assert b.variant == "batched"  # Potts-only batches keep the register-staged kernel
         b.iterate(21)
         for k, p in enumerate(vols):
             with gpu_problem(p, storage=pfm.BF16, schedule=pfm.FUSED_PLAIN) as single:
@@ -90,3 +98,22 @@ def test_batch_rejects_bad_members():
     flat2d = synth.random_problem(4901, (6, 7), nl=3, s_kind="field")
     with pytest.raises(pfm.PfmError):
         pfm.Batch([as_dict(good), as_dict(flat2d)])
+
+
+@pytest.mark.parametrize("storage", [0, 1], ids=["f32", "bf16"])
+def test_tma_dag_batch_2d_bf16_and_hmf(storage):
+    """The TMA DAG batch on 2-D members and HMF trees, both storages: bit for
+    bit the single-problem TMA DAG kernel."""
+    import paper_1501_07844_gb300 as pfm
+    vols = [synth.hmf_problem(seed=4950 + k, shape=(19 + 5 * k, 37 - 3 * k, 45 + 2 * k), iters=20) for k in range(2)]
+    vols += [synth.dagmf_problem(4960 + k, (53 + 9 * k, 70 - 11 * k), iters=20) for k in range(2)]
+    for group in (vols[:2], vols[2:]):
+        with pfm.Batch([as_dict(p) for p in group], storage=storage) as b:
+            assert b.variant == "batched_tma_dag"
+            b.iterate(23)
+            for k, p in enumerate(group):
+                with gpu_problem(p, storage=storage) as single:
+                    assert single.variant == "fused_tma_dag"
+                    single.iterate(23)
+                    assert np.array_equal(b.members[k].labels().cpu().numpy(), single.labels().cpu().numpy())
+                    assert np.array_equal(b.members[k].flows().cpu().numpy(), single.flows().cpu().numpy())
