@@ -421,6 +421,7 @@ struct BatchDagTma final : BatchBase {
     TmaMaps* maps = nullptr;  // [2][nvol]
     DagLists* lists = nullptr;
     int4* items = nullptr;
+    int* counter = nullptr;  // next work item of the running launch
     int nvol = 0, nitems = 0, smem = 0, bar_off = 0;
 
     ~BatchDagTma() override { release(); }
@@ -430,10 +431,12 @@ struct BatchDagTma final : BatchBase {
         if (maps) cudaFree(maps);
         if (lists) cudaFree(lists);
         if (items) cudaFree(items);
+        if (counter) cudaFree(counter);
         args = nullptr;
         maps = nullptr;
         lists = nullptr;
         items = nullptr;
+        counter = nullptr;
     }
 
     // True if every member can run the TMA DAG kernel.
@@ -488,6 +491,7 @@ struct BatchDagTma final : BatchBase {
         if ((e = cudaMalloc(&maps, sizeof(TmaMaps) * hm.size())) != cudaSuccess) return e;
         if ((e = cudaMalloc(&lists, sizeof(DagLists) * hl.size())) != cudaSuccess) return e;
         if ((e = cudaMalloc(&items, sizeof(int4) * work.size())) != cudaSuccess) return e;
+        if ((e = cudaMalloc(&counter, sizeof(int))) != cudaSuccess) return e;
         if ((e = cudaMemcpy(args, ha.data(), sizeof(Args) * ha.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return e;
         if ((e = cudaMemcpy(maps, hm.data(), sizeof(TmaMaps) * hm.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
             return e;
@@ -499,9 +503,11 @@ struct BatchDagTma final : BatchBase {
     }
 
     cudaError_t launch(int parity, int grid, cudaStream_t s) override {
+        cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), s);
+        if (e != cudaSuccess) return e;
         batched_dag_tma_kernel<DIM, T><<<grid, DAG_TMA_NT, smem, s>>>(args + (size_t)parity * nvol,
                                                                       maps + (size_t)parity * nvol, lists, items,
-                                                                      nitems, bar_off);
+                                                                      nitems, bar_off, counter);
         return cudaGetLastError();
     }
 

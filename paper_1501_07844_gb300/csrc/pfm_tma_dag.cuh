@@ -381,17 +381,20 @@ fused_dag_tma_kernel(const StepArgs<DMAX, DMAX> a, const __grid_constant__ TmaMa
 }
 
 // Many problems in one persistent launch: CTAs take (problem, x tile,
-// y tile, z chunk) items round-robin; args, maps and lists are per problem
-// (this launch's parity), the maps in global memory (64-byte aligned,
-// written before the launch).  The mbarrier ring carries over from item to
-// item; dynamic shared memory is sized for the largest problem layout.
+// y tile, z chunk) items in list order from a global counter (zeroed before
+// the launch), so a CTA that drew short items takes more; args, maps and
+// lists are per problem (this launch's parity), the maps in global memory
+// (64-byte aligned, written before the launch).  The mbarrier ring carries
+// over from item to item; dynamic shared memory is sized for the largest
+// problem layout.
 template <int DIM, typename T>
 __global__ void __launch_bounds__(DAG_TMA_NT, 1)
 batched_dag_tma_kernel(const StepArgs<DMAX, DMAX>* __restrict__ args, const TmaMaps* __restrict__ maps,
                        const DagLists* __restrict__ lists, const int4* __restrict__ items, int n_items,
-                       int bar_off) {
+                       int bar_off, int* next_item) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ DagLists sl;
+    __shared__ int s_item;
     unsigned char* smem = dag_smem_base(smem_raw);
     const unsigned bar0 = smem_addr(smem + bar_off);
     if (threadIdx.x == 0) {
@@ -400,9 +403,14 @@ batched_dag_tma_kernel(const StepArgs<DMAX, DMAX>* __restrict__ args, const TmaM
     }
     DagRing ring;
     bool alive = true;
-    for (int it = blockIdx.x; it < n_items && alive; it += gridDim.x) {
+    while (alive) {
+        // the previous item ended with a CTA barrier: s_item, sl and the
+        // stages are free
+        if (threadIdx.x == 0) s_item = atomicAdd(next_item, 1);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= n_items) break;
         const int4 w = items[it];
-        // the previous item ended with a CTA barrier: sl and the stages are free
         dag_stage_lists(&sl, lists + w.x);
         __syncthreads();
         alive = dag_tma_tile<DIM, T>(args[w.x], maps[w.x], sl, w.y, w.z, w.w, smem, bar0, ring);
