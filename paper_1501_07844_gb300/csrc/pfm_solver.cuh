@@ -155,15 +155,36 @@ struct Solver final : SolverBase {
         fused_smem = sizeof(float) * 3 * MAXL * FNE;
     }
 
+    template <bool IDX32>
+    cudaError_t launch_dag(const StepArgs<MAXL, MAXN>& a, const TmaMaps& m, dim3 grid, int smem, cudaStream_t s) {
+        if constexpr (kDagTmaCapable) {
+            cudaError_t e = cudaFuncSetAttribute(fused_dag_tma_kernel<DIM, T, IDX32>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            if (e != cudaSuccess) return e;
+            fused_dag_tma_kernel<DIM, T, IDX32><<<grid, DAG_TMA_NT, smem, s>>>(a, m, lists);
+            return cudaGetLastError();
+        } else {
+            return cudaErrorInvalidValue;
+        }
+    }
+
+    template <bool EXACT, bool WITH_E, bool IDX32>
+    cudaError_t launch_tma3(const StepArgs<MAXL, MAXN>& a, const TmaMaps& m, dim3 grid, double* partial,
+                            cudaStream_t s) {
+        using Lay = TmaLayout<MAXL, DIM, T>;
+        cudaError_t e = cudaFuncSetAttribute(fused_tma_kernel<MAXL, DIM, T, EXACT, WITH_E, IDX32>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, Lay::total_bytes);
+        if (e != cudaSuccess) return e;
+        fused_tma_kernel<MAXL, DIM, T, EXACT, WITH_E, IDX32><<<grid, TMA_NT, Lay::total_bytes, s>>>(a, m, partial);
+        return cudaGetLastError();
+    }
+
+    // 32-bit slot offsets when every offset of the flow array fits
     template <bool EXACT, bool WITH_E>
     cudaError_t launch_tma(const StepArgs<MAXL, MAXN>& a, const TmaMaps& m, dim3 grid, double* partial,
                            cudaStream_t s) {
-        using Lay = TmaLayout<MAXL, DIM, T>;
-        cudaError_t e = cudaFuncSetAttribute(fused_tma_kernel<MAXL, DIM, T, EXACT, WITH_E>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, Lay::total_bytes);
-        if (e != cudaSuccess) return e;
-        fused_tma_kernel<MAXL, DIM, T, EXACT, WITH_E><<<grid, TMA_NT, Lay::total_bytes, s>>>(a, m, partial);
-        return cudaGetLastError();
+        if ((long long)DIM * a.nn * a.n <= 0xFFFFFFFFll) return launch_tma3<EXACT, WITH_E, true>(a, m, grid, partial, s);
+        return launch_tma3<EXACT, WITH_E, false>(a, m, grid, partial, s);
     }
 
     cudaError_t step(const void* u_in, void* u_out, const void* q_in, void* q_out, bool fused, int zc,
@@ -198,13 +219,11 @@ struct Solver final : SolverBase {
                 const int k = (u_in == tma_u[0]) ? 0 : 1;
                 a.zc = zc < 1 ? 1 : zc;
                 const DagTmaLayout lay(a.nl, lists.nf, DIM, (int)sizeof(T));
-                cudaError_t e = cudaFuncSetAttribute(fused_dag_tma_kernel<DIM, T>,
-                                                     cudaFuncAttributeMaxDynamicSharedMemorySize, lay.total);
-                if (e != cudaSuccess) return e;
                 dim3 grid((a.nx + FTX - 1) / FTX, (a.ny + DTY - 1) / DTY, (a.nz + a.zc - 1) / a.zc);
-                fused_dag_tma_kernel<DIM, T><<<grid, DAG_TMA_NT, lay.total, s>>>(a, tma_maps[k], lists);
                 *launches = 1;
-                return cudaGetLastError();
+                // 32-bit slot offsets when every offset of the flow array fits
+                if ((long long)DIM * a.nn * a.n <= 0xFFFFFFFFll) return launch_dag<true>(a, tma_maps[k], grid, lay.total, s);
+                return launch_dag<false>(a, tma_maps[k], grid, lay.total, s);
             }
         }
         if (fused) {
@@ -423,6 +442,7 @@ struct BatchDagTma final : BatchBase {
     int4* items = nullptr;
     int* counter = nullptr;  // next work item of the running launch
     int nvol = 0, nitems = 0, smem = 0, bar_off = 0;
+    bool idx32 = true;       // every member's slot offsets fit in 32 bits
 
     ~BatchDagTma() override { release(); }
 
@@ -461,8 +481,10 @@ struct BatchDagTma final : BatchBase {
         std::vector<int4> work;
         smem = 0;
         bar_off = 0;
+        idx32 = true;
         for (int k = 0; k < n; ++k) {
             const ProblemView& v = m[k].view;
+            idx32 = idx32 && (long long)DIM * v.nn * v.n <= 0xFFFFFFFFll;
             const Args base = make_step_args<DMAX, DMAX, true>(v, zc);
             DagTmaLayout lay(1, 1, DIM, es);
             if (!build_dag_lists(base, DIM, es, &hl[k], &lay)) return cudaErrorInvalidValue;
@@ -499,15 +521,22 @@ struct BatchDagTma final : BatchBase {
             return e;
         if ((e = cudaMemcpy(items, work.data(), sizeof(int4) * work.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
             return e;
-        return cudaFuncSetAttribute(batched_dag_tma_kernel<DIM, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if ((e = cudaFuncSetAttribute(batched_dag_tma_kernel<DIM, T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      smem)) != cudaSuccess)
+            return e;
+        return cudaFuncSetAttribute(batched_dag_tma_kernel<DIM, T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    smem);
     }
 
     cudaError_t launch(int parity, int grid, cudaStream_t s) override {
         cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), s);
         if (e != cudaSuccess) return e;
-        batched_dag_tma_kernel<DIM, T><<<grid, DAG_TMA_NT, smem, s>>>(args + (size_t)parity * nvol,
-                                                                      maps + (size_t)parity * nvol, lists, items,
-                                                                      nitems, bar_off, counter);
+        if (idx32)
+            batched_dag_tma_kernel<DIM, T, true><<<grid, DAG_TMA_NT, smem, s>>>(
+                args + (size_t)parity * nvol, maps + (size_t)parity * nvol, lists, items, nitems, bar_off, counter);
+        else
+            batched_dag_tma_kernel<DIM, T, false><<<grid, DAG_TMA_NT, smem, s>>>(
+                args + (size_t)parity * nvol, maps + (size_t)parity * nvol, lists, items, nitems, bar_off, counter);
         return cudaGetLastError();
     }
 

@@ -135,6 +135,19 @@ __device__ __forceinline__ float ex2_approx(float x) {
     return y;
 }
 
+// Pointer to slot (component c, plane p, voxel vox) of a pitched array with
+// n slots per component and `plane` slots per plane.  IDX32: the launch
+// guarantees every offset < 2^32, so the offset is formed in 32 bits and
+// widened by the address computation itself (one wide multiply-add per
+// access instead of a 64-bit multiply and add).
+template <bool IDX32, typename T>
+__device__ __forceinline__ T* slot_ptr(T* base, int c, int p, long long n, long long plane, long long vox) {
+    if constexpr (IDX32)
+        return base + ((unsigned)c * (unsigned)n + (unsigned)p * (unsigned)plane + (unsigned)vox);
+    else
+        return base + ((long long)c * n + (long long)p * plane + vox);
+}
+
 // 1/x by the hardware approximation (at most 1 ulp from the rounded
 // quotient) for normal x; subnormal, zero and NaN x take the IEEE division.
 __device__ __forceinline__ float rcp_fast(float x) {
@@ -178,7 +191,7 @@ __device__ __forceinline__ void project_nb(float (&y)[DIM], float s, int aniso) 
 // partial per CTA: P of plane p from the prox's per-voxel minimum, E of
 // plane p-1 (whose z-gradient needs plane p) during the flow phase.  The
 // staged u is never overwritten, so its neighbours are still the input.
-template <int MAXL, int DIM, typename T, bool EXACT, bool WITH_E>
+template <int MAXL, int DIM, typename T, bool EXACT, bool WITH_E, bool IDX32>
 __global__ void __launch_bounds__(TMA_NT, 1)
 fused_tma_kernel(const StepArgs<MAXL, MAXL> a, const __grid_constant__ TmaMaps maps, double* partial) {
     static_assert(MAXL % 4 == 0, "label halves need MAXL % 4 == 0");
@@ -256,6 +269,7 @@ fused_tma_kernel(const StepArgs<MAXL, MAXL> a, const __grid_constant__ TmaMaps m
     const bool ownerE = validE && v < FTX * FTY;
     const int ui = ey * TMA_BX + ex;
     const int qi = (ey + 1) * Lay::QBX + (ex + Lay::QOFF);
+    const long long vox = (long long)ye * a.px + xe;  // slot of this voxel in its plane
     // forward differences are zero at the last index: zero steps there (the
     // g slots outside the grid hold zeros, so a zero step never meets a NaN)
     const float cx = xe < a.nx - 1 ? a.ctau : 0.f;
@@ -382,7 +396,6 @@ fused_tma_kernel(const StepArgs<MAXL, MAXL> a, const __grid_constant__ TmaMaps m
             if (validE) {
                 if (!((sum > 0.f) && (sum <= 3.0e38f))) bad = true;
                 const float inv = rcp_fast(sum);
-                const long long i0 = (long long)p * plane + (long long)ye * a.px + xe;
 #pragma unroll
                 for (int i = 0; i < HL; ++i) {
                     const int j = half_label(h, i);
@@ -390,7 +403,7 @@ fused_tma_kernel(const StepArgs<MAXL, MAXL> a, const __grid_constant__ TmaMaps m
                         const float un = u[i] * inv;
                         gcur[i] = a.literal ? u[i] : un;
                         gC[j * ustride + ui] = gcur[i];
-                        if (ownerE && p < z1) stv<T>(uout + (long long)j * n + i0, un);
+                        if (ownerE && p < z1) stv<T>(slot_ptr<IDX32>(uout, j, p, n, plane, vox), un);
                     }
                 }
             }
@@ -403,7 +416,6 @@ fused_tma_kernel(const StepArgs<MAXL, MAXL> a, const __grid_constant__ TmaMaps m
         const int pm = p - 1;
         if (pm >= z0 && ownerE) {
             const float sf = sprev;
-            const long long i0 = (long long)pm * plane + (long long)ye * a.px + xe;
             const float cz = pm < a.nz - 1 ? a.ctau : 0.f;
             float eloc = 0.f;
 #pragma unroll
@@ -427,9 +439,8 @@ fused_tma_kernel(const StepArgs<MAXL, MAXL> a, const __grid_constant__ TmaMaps m
                         eloc = fmaf(sj, nv, eloc);
                     }
                     project_nb<DIM>(yv, sj, a.aniso);
-                    T* qa = qout + (long long)j * DIM * n + i0;
 #pragma unroll
-                    for (int k = 0; k < DIM; ++k) stv<T>(qa + k * n, yv[k]);
+                    for (int k = 0; k < DIM; ++k) stv<T>(slot_ptr<IDX32>(qout, j * DIM + k, pm, n, plane, vox), yv[k]);
                 }
             }
             if constexpr (WITH_E) sumE.add(eloc);

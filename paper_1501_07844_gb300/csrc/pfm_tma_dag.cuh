@@ -78,7 +78,7 @@ struct DagRing {
 // mbarriers (initialised by the caller).  Returns false after a timed-out
 // wait (FLAG_TIMEOUT raised; the caller drains and stops).  Every thread of
 // the CTA calls it; it ends with a CTA barrier.
-template <int DIM, typename T>
+template <int DIM, typename T, bool IDX32>
 __device__ __forceinline__ bool dag_tma_tile(const StepArgs<DMAX, DMAX>& a, const TmaMaps& maps, const DagLists& sl,
                                              int bx, int by, int bz, unsigned char* smem, unsigned bar0,
                                              DagRing& ring) {
@@ -158,6 +158,7 @@ __device__ __forceinline__ bool dag_tma_tile(const StepArgs<DMAX, DMAX>& a, cons
     float* erow = ebuf + (inE ? v : 0) * lay.row;
     const int ui = ey * TMA_BX + ex;
     const int qi = (ey + 1) * QBX + (ex + QOFF);
+    const long long vox = (long long)ye * px + xe;  // slot of this voxel in its plane
     // zero steps at the last index (the g slots outside the grid hold zeros)
     const float cx = xe < nx - 1 ? ctau : 0.f;
     const float cy = ye < ny - 1 ? ctau : 0.f;
@@ -269,14 +270,14 @@ __device__ __forceinline__ bool dag_tma_tile(const StepArgs<DMAX, DMAX>& a, cons
             if (validE) {
                 if (!((sum > 0.f) && (sum <= 3.0e38f))) bad = true;
                 const float inv = rcp_fast(sum);
-                const long long i0 = (long long)p * plane + (long long)ye * px + xe;
+
 #pragma unroll
                 for (int i = 0; i < PER; ++i) {
                     const int j = h + 4 * i;
                     if (j < nl) {
                         const float un = u[i] * inv;
                         erow[j] = literal ? u[i] : un;
-                        if (ownerE && p < z1) stv<T>(uout + (long long)j * n + i0, un);
+                        if (ownerE && p < z1) stv<T>(slot_ptr<IDX32>(uout, j, p, n, plane, vox), un);
                     }
                 }
             }
@@ -303,7 +304,7 @@ __device__ __forceinline__ bool dag_tma_tile(const StepArgs<DMAX, DMAX>& a, cons
         const int pm = p - 1;
         if (pm >= z0 && ownerE) {
             const float sf = sprev;
-            const long long i0 = (long long)pm * plane + (long long)ye * px + xe;
+
             const float cz = pm < nz - 1 ? ctau : 0.f;
 #pragma unroll
             for (int i = 0; i < PER; ++i) {
@@ -316,9 +317,8 @@ __device__ __forceinline__ bool dag_tma_tile(const StepArgs<DMAX, DMAX>& a, cons
                     yv[1] = qyp[i] - cy * (gA[TMA_BX] - g0);
                     if constexpr (DIM == 3) yv[2] = qzp[i] - cz * (gcur[i] - g0);
                     project_nb<DIM>(yv, cap[i] * sf, aniso);
-                    T* qa = qout + (long long)A * DIM * n + i0;
 #pragma unroll
-                    for (int k = 0; k < DIM; ++k) stv<T>(qa + k * n, yv[k]);
+                    for (int k = 0; k < DIM; ++k) stv<T>(slot_ptr<IDX32>(qout, A * DIM + k, pm, n, plane, vox), yv[k]);
                 }
             }
         }
@@ -359,7 +359,7 @@ __device__ __forceinline__ unsigned char* dag_smem_base(unsigned char* raw) {
 }
 
 // One problem: CTA = (x tile, y tile, z chunk).
-template <int DIM, typename T>
+template <int DIM, typename T, bool IDX32>
 __global__ void __launch_bounds__(DAG_TMA_NT, 1)
 fused_dag_tma_kernel(const StepArgs<DMAX, DMAX> a, const __grid_constant__ TmaMaps maps,
                      const __grid_constant__ DagLists lists) {
@@ -375,7 +375,7 @@ fused_dag_tma_kernel(const StepArgs<DMAX, DMAX> a, const __grid_constant__ TmaMa
     dag_stage_lists(&sl, &lists);
     __syncthreads();
     DagRing ring;
-    if (!dag_tma_tile<DIM, T>(a, maps, sl, blockIdx.x, blockIdx.y, blockIdx.z, smem, bar0, ring) &&
+    if (!dag_tma_tile<DIM, T, IDX32>(a, maps, sl, blockIdx.x, blockIdx.y, blockIdx.z, smem, bar0, ring) &&
         threadIdx.x == 0)
         dag_ring_drain(bar0, ring);
 }
@@ -387,7 +387,7 @@ fused_dag_tma_kernel(const StepArgs<DMAX, DMAX> a, const __grid_constant__ TmaMa
 // (64-byte aligned, written before the launch).  The mbarrier ring carries
 // over from item to item; dynamic shared memory is sized for the largest
 // problem layout.
-template <int DIM, typename T>
+template <int DIM, typename T, bool IDX32>
 __global__ void __launch_bounds__(DAG_TMA_NT, 1)
 batched_dag_tma_kernel(const StepArgs<DMAX, DMAX>* __restrict__ args, const TmaMaps* __restrict__ maps,
                        const DagLists* __restrict__ lists, const int4* __restrict__ items, int n_items,
@@ -413,7 +413,7 @@ batched_dag_tma_kernel(const StepArgs<DMAX, DMAX>* __restrict__ args, const TmaM
         const int4 w = items[it];
         dag_stage_lists(&sl, lists + w.x);
         __syncthreads();
-        alive = dag_tma_tile<DIM, T>(args[w.x], maps[w.x], sl, w.y, w.z, w.w, smem, bar0, ring);
+        alive = dag_tma_tile<DIM, T, IDX32>(args[w.x], maps[w.x], sl, w.y, w.z, w.w, smem, bar0, ring);
     }
     if (!alive && threadIdx.x == 0) dag_ring_drain(bar0, ring);
 }
