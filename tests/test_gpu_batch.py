@@ -117,3 +117,25 @@ def test_tma_dag_batch_2d_bf16_and_hmf(storage):
                     single.iterate(23)
                     assert np.array_equal(b.members[k].labels().cpu().numpy(), single.labels().cpu().numpy())
                     assert np.array_equal(b.members[k].flows().cpu().numpy(), single.flows().cpu().numpy())
+
+
+def test_tma_dag_batch_mixed_layouts_and_ishikawa():
+    """One TMA batch holding members with different shared-memory layouts
+    (HMF: 12 end-labels / 15 nodes; DAGMF: 10 / 14; an Ishikawa chain whose
+    end-labels carry no flow) and odd widths: every member equals its
+    single-problem run bit for bit, and the chain's end-label flows stay 0."""
+    import paper_1501_07844_gb300 as pfm
+    vols = [synth.hmf_problem(seed=4970, shape=(17, 23, 29), iters=20),
+            synth.dagmf_problem(4971, (21, 19, 35), iters=20),
+            synth.ishikawa_problem(4972, (13, 26, 41), nlev=7)]
+    with pfm.Batch([as_dict(p) for p in vols]) as b:
+        assert b.variant == "batched_tma_dag"
+        b.iterate(26)
+        for k, p in enumerate(vols):
+            with gpu_problem(p) as single:
+                assert single.variant == "fused_tma_dag"
+                single.iterate(26)
+                assert np.array_equal(b.members[k].labels().cpu().numpy(), single.labels().cpu().numpy())
+                assert np.array_equal(b.members[k].flows().cpu().numpy(), single.flows().cpu().numpy())
+        q = b.members[2].flows().cpu().numpy()
+        assert np.all(q[7:] == 0)
