@@ -14,7 +14,10 @@
 //   flow:  thread h of an owned voxel updates the flows of nodes A = h, h+4,
 //          ..., from the forward differences of g_A.
 // The lists hold every nonzero path weight W_(A,j) (W_(j,j) = 1), so the sums
-// equal the ordered top-down / bottom-up loops of Algorithm 2; the gradient is
+// equal the ordered top-down / bottom-up loops of Algorithm 2 (up to the
+// rounding order: the first four terms of a list are loaded together under
+// predicates and summed pairwise, so a walk is not a chain of dependent
+// shared-memory loads; longer lists continue in a loop); the gradient is
 // linear, so differencing the accumulated g_A equals accumulating the
 // end-labels' gradients.  Nodes whose capacity is zero carry no flow: the
 // nodes from `nf` on (a suffix of zero-capacity nodes, e.g. the end-labels of
@@ -246,7 +249,13 @@ __device__ __forceinline__ bool dag_tma_tile(const StepArgs<DMAX, DMAX>& a, cons
                     u[i] = lds<T>(uS + j * ustride + ui);
                     float dj = dS[j * ustride + ui];
                     const int na = sl.anc_n[j];
-                    for (int k = 0; k < na; ++k) dj = fmaf(sl.anc_w[j][k], erow[sl.anc[j][k]], dj);
+                    // the first four terms unrolled under predicates (their loads
+                    // issue together), the rest in a loop
+                    float acc[4];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) acc[k] = k < na ? sl.anc_w[j][k] * erow[sl.anc[j][k]] : 0.f;
+                    dj += (acc[0] + acc[1]) + (acc[2] + acc[3]);
+                    for (int k = 4; k < na; ++k) dj = fmaf(sl.anc_w[j][k], erow[sl.anc[j][k]], dj);
                     d[i] = dj;
                     mloc = fminf(mloc, dj);
                 }
@@ -289,8 +298,11 @@ __device__ __forceinline__ bool dag_tma_tile(const StepArgs<DMAX, DMAX>& a, cons
                     const int A = h + 4 * i;
                     if (A < nf) {
                         const int nd = sl.desc_n[A];
-                        float g = 0.f;
-                        for (int k = 0; k < nd; ++k) g = fmaf(sl.desc_w[A][k], erow[sl.desc[A][k]], g);
+                        float acc[4];
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) acc[k] = k < nd ? sl.desc_w[A][k] * erow[sl.desc[A][k]] : 0.f;
+                        float g = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+                        for (int k = 4; k < nd; ++k) g = fmaf(sl.desc_w[A][k], erow[sl.desc[A][k]], g);
                         gcur[i] = g;
                         gC[A * ustride + ui] = g;
                     }
