@@ -57,6 +57,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--dims", type=int, default=0, help="cube edge override (profiling of small cases)")
+    ap.add_argument("--volumes", type=int, default=32, help="volumes of the batched workload (profiling of small cases)")
     return ap.parse_args()
 
 
@@ -251,7 +252,7 @@ def run_batched(args, rank, world):
     import paper_1501_07844_gb300 as pfm
     import synth
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    vols = synth.dagmf_batch(seed=4000 + 100 * rank, count=32)
+    vols = synth.dagmf_batch(seed=4000 + 100 * rank, count=args.volumes)
     stream = torch.cuda.Stream()  # a capturable (non-default) stream shared with the events
     torch.cuda.set_stream(stream)
     probs = [dict(D=torch.from_numpy(p.D).cuda(), S_field=torch.from_numpy(p.S_field).cuda(), s_node=p.s_node,
@@ -289,7 +290,9 @@ def run_batched(args, rank, world):
                        "kernel_variant": b.variant,
                        "shapes": [list(p.spatial) for p in vols]},
             "roofline": {"bound": "hbm", "kernel": {"batched_tma_dag": "batched_dag_tma_kernel"}.get(b.variant, "batched_step_kernel"), "achieved": achieved, "peak": peak,
-                         "unit": "GB/s", "frac": achieved / peak, "algorithmic_bytes_per_launch": alg,
+                         "unit": "GB/s", "frac": achieved / peak, "peak_source": "measured",
+                         "traffic": load_traffic("dagmf_batched") if (b.variant == "batched_tma_dag" and len(vols) == 32) else None,
+                         "algorithmic_bytes_per_launch": alg,
                          "kernel_ms_per_launch": it_ms},
             "gpu_launches": int(b.launches - l0), "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
