@@ -595,7 +595,8 @@ def main():
     achieved = alg_bytes / (kern_ms / 1e3) / 1e9
     traffic = load_traffic(cfg)
     kname = {"fused_tma": "fused_tma_kernel", "fused_tma_dag": "fused_dag_tma_kernel", "fused": "fused_step_kernel",
-             "inplace": "prox_inplace_kernel+flow_inplace_kernel"}[gp.variant]
+             "inplace": "prox_inplace_kernel+flow_inplace_kernel",
+             "inplace_tma": "prox_inplace_tma_kernel+flow_inplace_tma_kernel"}.get(gp.variant, gp.variant)
 
     gp.close()
     if rank != 0:

@@ -465,6 +465,7 @@ static pfm_status create_impl(const pfm_desc* desc, const pfm_params* params, vo
     // the energy reduction (every schedule)
     pb->solver->prepare_tma(pb->u, pb->q, pb->D, pb->S);
     pb->solver->use_tma = params->schedule == PFM_SCHEDULE_FUSED;
+    pb->solver->use_tma_inplace = params->schedule == PFM_SCHEDULE_INPLACE;
     // z-chunk of the fused kernel: aim at >= ~2000 CTAs on large volumes
     {
         const long long tiles = (long long)((pb->nx + pfm::FTX - 1) / pfm::FTX) * ((pb->ny + pfm::FTY - 1) / pfm::FTY);

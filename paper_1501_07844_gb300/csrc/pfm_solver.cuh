@@ -13,6 +13,7 @@
 #include "pfm_device.cuh"
 #include "pfm_tma.cuh"
 #include "pfm_tma_dag.cuh"
+#include "pfm_tma_inplace.cuh"
 
 namespace pfm {
 
@@ -130,6 +131,7 @@ struct SolverBase {
     // TMA-pipelined fused kernel can run on this problem.
     virtual bool prepare_tma(void* const* u, void* const* q, const float* D, const float* S) { return false; }
     bool use_tma = true;  // cleared to force the register-staged fused kernel
+    bool use_tma_inplace = false;  // PFM_SCHEDULE_INPLACE: TMA-staged sweeps where available
     // Name of the kernel family step() launches for the given schedule.
     virtual const char* variant(bool fused) const = 0;
     // True if step() with a partials buffer evaluates the energy of its input.
@@ -149,10 +151,36 @@ struct Solver final : SolverBase {
     TmaMaps tma_maps[2];
     bool dag_tma_ready = false;
     DagLists lists{};
+    bool inplace_ready = false;
+    InplaceMaps inplace_maps{};
 
     explicit Solver(const ProblemView& v) {
         base = make_step_args<MAXL, MAXN, IS_DAG>(v, 0);
         fused_smem = sizeof(float) * 3 * MAXL * FNE;
+    }
+
+    // TMA-staged in-place sweeps: Potts, NORMALISED (PAPER_LITERAL needs the
+    // normaliser field between the sweeps and keeps the per-voxel kernels)
+    bool inplace_tma() const { return kTmaCapable && inplace_ready && use_tma_inplace && !base.literal; }
+
+    template <bool EXACT, bool IDX32>
+    cudaError_t launch_inplace(const StepArgs<MAXL, MAXN>& a, dim3 grid, cudaStream_t s) {
+        if constexpr (kTmaCapable) {
+            using L = InplaceLayout<MAXL, DIM, T>;
+            cudaError_t e = cudaFuncSetAttribute(prox_inplace_tma_kernel<MAXL, DIM, T, EXACT, IDX32>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, L::p_total);
+            if (e != cudaSuccess) return e;
+            e = cudaFuncSetAttribute(flow_inplace_tma_kernel<MAXL, DIM, T, EXACT, IDX32>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, L::f_total);
+            if (e != cudaSuccess) return e;
+            prox_inplace_tma_kernel<MAXL, DIM, T, EXACT, IDX32><<<grid, INPLACE_TMA_NT, L::p_total, s>>>(a, inplace_maps);
+            e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
+            flow_inplace_tma_kernel<MAXL, DIM, T, EXACT, IDX32><<<grid, INPLACE_TMA_NT, L::f_total, s>>>(a, inplace_maps);
+            return cudaGetLastError();
+        } else {
+            return cudaErrorInvalidValue;
+        }
     }
 
     template <bool IDX32>
@@ -237,6 +265,16 @@ struct Solver final : SolverBase {
             dim3 grid((a.nx + FTX - 1) / FTX, (a.ny + FTY - 1) / FTY, (a.nz + a.zc - 1) / a.zc);
             fused_step_kernel<MAXL, MAXN, DIM, IS_DAG, T><<<grid, FUSED_NT, fused_smem, s>>>(a);
             *launches = 1;
+        } else if (inplace_tma()) {
+            if constexpr (kTmaCapable) {
+                a.zc = zc < 1 ? 1 : zc;
+                dim3 grid((a.nx + FTX - 1) / FTX, (a.ny + FTY - 1) / FTY, (a.nz + a.zc - 1) / a.zc);
+                *launches = 2;
+                const bool exact = a.nl == MAXL;
+                const bool idx32 = (long long)DIM * a.nn * a.n <= 0xFFFFFFFFll;
+                if (exact) return idx32 ? launch_inplace<true, true>(a, grid, s) : launch_inplace<true, false>(a, grid, s);
+                return idx32 ? launch_inplace<false, true>(a, grid, s) : launch_inplace<false, false>(a, grid, s);
+            }
         } else {
             const unsigned blocks = (unsigned)((a.n + POINT_NT - 1) / POINT_NT);
             prox_inplace_kernel<MAXL, MAXN, DIM, IS_DAG, T><<<blocks, POINT_NT, 0, s>>>(a);
@@ -289,6 +327,18 @@ struct Solver final : SolverBase {
                 tma_u[k] = u[k];
             }
             tma_ready = true;
+            // maps of the in-place sweeps (single buffer: u[0], q[0])
+            {
+                const unsigned box_t[4] = {(unsigned)FTX, (unsigned)FTY, 1u, (unsigned)nl};
+                const unsigned box_qt[4] = {(unsigned)FTX, (unsigned)FTY, 1u, (unsigned)(DIM * nl)};
+                InplaceMaps& im = inplace_maps;
+                inplace_ready = encode_tiled_map(&im.u_tile, u[0], es, 4, dims_u, st_t, box_t) &&
+                                encode_tiled_map(&im.D_tile, D, 4, 4, dims_u, st_f, box_t) &&
+                                encode_tiled_map(&im.q_tile, q[0], es, 4, dims_q, st_t, box_qt);
+                im.q_halo = tma_maps[0].q;
+                im.u_halo = tma_maps[0].u;
+                im.S = tma_maps[0].S;
+            }
             return true;
         }
     }
@@ -301,7 +351,7 @@ struct Solver final : SolverBase {
     }
 
     const char* variant(bool fused) const override {
-        if (!fused) return "inplace";
+        if (!fused) return inplace_tma() ? "inplace_tma" : "inplace";
         if (kTmaCapable && tma_ready && use_tma) return "fused_tma";
         if (kDagTmaCapable && dag_tma_ready && use_tma) return "fused_tma_dag";
         return "fused";
