@@ -93,15 +93,21 @@ def make_problem(cfg, seed, shape=None):
 
 
 def algorithmic_bytes_per_iter(prob, storage, schedule):
-    """Minimum bytes one fused iteration must move: read u, D, q; write u, q
-    (d and the normaliser stay on chip), plus the S field once per voxel.
+    """Minimum bytes one iteration of the schedule must move: fused, read u,
+    D, q and write u, q (d and the normaliser stay on chip), plus the S field
+    once per voxel; in-place, the two sweeps' reads and writes.
     Only nodes with nonzero capacity carry flow (a zero-capacity node's flow
     is identically zero: the Ishikawa chain's end-labels)."""
     n = int(np.prod(prob.spatial))
     ts = 4 if storage == 0 else 2
     ndim = len(prob.spatial)
     n_flow = prob.n_nodes if prob.s_node is None else int(np.count_nonzero(np.asarray(prob.s_node) > 0))
-    b = n * (prob.n_leaf * (2 * ts + 4) + n_flow * ndim * 2 * ts)
+    if schedule == 1:
+        # in-place schedule: the prox sweep reads u, D, q and writes u; the
+        # flow sweep reads u, q and writes q (u and q cross HBM twice)
+        b = n * (prob.n_leaf * (3 * ts + 4 + ndim * ts) + n_flow * ndim * 2 * ts)
+    else:
+        b = n * (prob.n_leaf * (2 * ts + 4) + n_flow * ndim * 2 * ts)
     if prob.S_field is not None:
         b += 4 * n
     return b
