@@ -157,6 +157,21 @@ PFM_API void pfm_destroy(pfm_problem* pb);
  * Asynchronous on the problem's stream. */
 PFM_API pfm_status pfm_set_data(pfm_problem* pb, const float* D, const float* S_field);
 
+/* Double-buffered data upload (no counterpart in the paper; for callers that
+ * stream new data terms while the solver runs).  pfm_prefetch_data starts
+ * copying D (and S_field, as for pfm_set_data) into a library-owned staging
+ * buffer on a copy stream of its own and returns at once, so the copy
+ * overlaps the iterations already queued; the caller keeps the source
+ * buffers unchanged (pinned host memory for a truly asynchronous copy) until
+ * pfm_commit_data, which makes the problem's stream wait for the copy, moves
+ * the staged data into place (a device-to-device copy) and validates it like
+ * pfm_set_data.  A second prefetch before the commit replaces the first;
+ * pfm_commit_data without a prefetch returns PFM_EINVAL.  The staging buffer
+ * (D and S sized) is allocated on the first prefetch and freed with the
+ * problem. */
+PFM_API pfm_status pfm_prefetch_data(pfm_problem* pb, const float* D, const float* S_field);
+PFM_API pfm_status pfm_commit_data(pfm_problem* pb);
+
 /* u_L = 1/#leaves, q = 0, iteration counter = 0.  Asynchronous. */
 PFM_API pfm_status pfm_reset(pfm_problem* pb);
 

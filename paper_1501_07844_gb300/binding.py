@@ -52,6 +52,8 @@ _SIGS = {
     "pfm_create": (C.c_int, [C.POINTER(pfm_desc), C.POINTER(pfm_params), _P, C.POINTER(_P)]),
     "pfm_destroy": (None, [_P]),
     "pfm_set_data": (C.c_int, [_P, _P, _P]),
+    "pfm_prefetch_data": (C.c_int, [_P, _P, _P]),
+    "pfm_commit_data": (C.c_int, [_P]),
     "pfm_reset": (C.c_int, [_P]),
     "pfm_iterate": (C.c_int, [_P, C.c_int]),
     "pfm_set_step": (C.c_int, [_P, C.c_double, C.c_double]),
@@ -248,6 +250,19 @@ class Problem:
     def set_data(self, D, S_field=None):
         D, S_field = _as_f32(D), _as_f32(S_field)
         check(lib().pfm_set_data(self._h, _ptr(D), _ptr(S_field)))
+
+    def prefetch_data(self, D, S_field=None):
+        """Start copying new D (and S) into the staging buffer on the library's
+        copy stream (pfm_prefetch_data); the sources are kept until commit."""
+        D, S_field = _as_f32(D), _as_f32(S_field)
+        check(lib().pfm_prefetch_data(self._h, _ptr(D), _ptr(S_field)))
+        # a copy may still be reading the previous sources: keep the last two
+        kept = getattr(self, "_prefetched", [])
+        self._prefetched = (kept + [(D, S_field)])[-2:]
+
+    def commit_data(self):
+        """Make the prefetched data current (pfm_commit_data)."""
+        check(lib().pfm_commit_data(self._h))
 
     def iterate(self, n):
         check(lib().pfm_iterate(self._h, int(n)))

@@ -233,6 +233,13 @@ struct pfm_problem {
     std::vector<float> W;  // [nn][nl]
     int64_t iters = 0, launches = 0;
     pfm::SolverBase* solver = nullptr;
+    // double-buffered upload (pfm_prefetch_data / pfm_commit_data)
+    float* D_stage = nullptr;
+    float* S_stage = nullptr;
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t staged = nullptr;    // the prefetch copy is complete
+    cudaEvent_t consumed = nullptr;  // the last commit has moved the staged data
+    bool stage_pending = false;
 };
 
 namespace {
@@ -278,11 +285,15 @@ pfm_status flags_status(unsigned f) {
 
 void free_all(pfm_problem* pb) {
     // the in-place schedule aliases u[1] = u[0] and q[1] = q[0]
+    if (pb->copy_stream) cudaStreamSynchronize(pb->copy_stream);
     void* ptrs[] = {pb->u[0], pb->u[1] != pb->u[0] ? pb->u[1] : nullptr, pb->q[0],
                     pb->q[1] != pb->q[0] ? pb->q[1] : nullptr, pb->D, pb->S, pb->abuf, pb->snode_dev,
-                    pb->flags, pb->partial, pb->result};
+                    pb->flags, pb->partial, pb->result, pb->D_stage, pb->S_stage};
     for (void* p : ptrs)
         if (p) cudaFree(p);
+    if (pb->staged) cudaEventDestroy(pb->staged);
+    if (pb->consumed) cudaEventDestroy(pb->consumed);
+    if (pb->copy_stream) cudaStreamDestroy(pb->copy_stream);
     cudaGetLastError();  // leave no stale error for the next call of this thread
     delete pb->solver;
     pb->solver = nullptr;
@@ -501,6 +512,49 @@ pfm_status pfm_set_data(pfm_problem* pb, const float* D, const float* S_field) {
     if (S_field) PFM_CUDA(copy_rows(pb->S, pb->px, S_field, pb->nx, pb->nx, rows, pb->stream), "copy S");
     PFM_CUDA(pfm::launch_validate(pb->D, (long long)pb->nl * pb->n, pb->S, pb->n, pb->flags, pb->stream), "validate");
     pb->launches++;
+    return PFM_OK;
+}
+
+pfm_status pfm_prefetch_data(pfm_problem* pb, const float* D, const float* S_field) {
+    if (!pb || !D) return fail(PFM_EINVAL, "NULL argument");
+    if ((S_field != nullptr) != (pb->S != nullptr))
+        return fail(PFM_EINVAL, "S_field must be given iff the problem was created with one");
+    if (!pb->copy_stream) {
+        PFM_CUDA(cudaStreamCreateWithFlags(&pb->copy_stream, cudaStreamNonBlocking), "copy stream");
+        PFM_CUDA(cudaEventCreateWithFlags(&pb->staged, cudaEventDisableTiming), "event");
+        PFM_CUDA(cudaEventCreateWithFlags(&pb->consumed, cudaEventDisableTiming), "event");
+        PFM_CUDA(cudaEventRecord(pb->consumed, pb->stream), "event");
+        // the staging buffers mirror the pitched D and S, padding zeroed once
+        PFM_CUDA(cudaMalloc(&pb->D_stage, (size_t)pb->nl * pb->n * 4), "alloc staging D");
+        PFM_CUDA(cudaMemset(pb->D_stage, 0, (size_t)pb->nl * pb->n * 4), "memset");
+        if (pb->S) {
+            PFM_CUDA(cudaMalloc(&pb->S_stage, (size_t)pb->n * 4), "alloc staging S");
+            PFM_CUDA(cudaMemset(pb->S_stage, 0, (size_t)pb->n * 4), "memset");
+        }
+    }
+    // the staging buffer is free once the last commit has moved it (a
+    // prefetch not yet committed is simply overwritten, in copy-stream order)
+    PFM_CUDA(cudaStreamWaitEvent(pb->copy_stream, pb->consumed, 0), "wait");
+    const long long rows = (long long)pb->ny * pb->nz;
+    PFM_CUDA(copy_rows(pb->D_stage, pb->px, D, pb->nx, pb->nx, pb->nl * rows, pb->copy_stream), "copy D");
+    if (S_field) PFM_CUDA(copy_rows(pb->S_stage, pb->px, S_field, pb->nx, pb->nx, rows, pb->copy_stream), "copy S");
+    PFM_CUDA(cudaEventRecord(pb->staged, pb->copy_stream), "event");
+    pb->stage_pending = true;
+    return PFM_OK;
+}
+
+pfm_status pfm_commit_data(pfm_problem* pb) {
+    if (!pb) return fail(PFM_EINVAL, "NULL problem");
+    if (!pb->stage_pending) return fail(PFM_EINVAL, "no data prefetched since the last commit");
+    PFM_CUDA(cudaStreamWaitEvent(pb->stream, pb->staged, 0), "wait");
+    PFM_CUDA(cudaMemcpyAsync(pb->D, pb->D_stage, (size_t)pb->nl * pb->n * 4, cudaMemcpyDeviceToDevice, pb->stream),
+             "move D");
+    if (pb->S)
+        PFM_CUDA(cudaMemcpyAsync(pb->S, pb->S_stage, (size_t)pb->n * 4, cudaMemcpyDeviceToDevice, pb->stream), "move S");
+    PFM_CUDA(cudaEventRecord(pb->consumed, pb->stream), "event");
+    PFM_CUDA(pfm::launch_validate(pb->D, (long long)pb->nl * pb->n, pb->S, pb->n, pb->flags, pb->stream), "validate");
+    pb->launches++;
+    pb->stage_pending = false;
     return PFM_OK;
 }
 

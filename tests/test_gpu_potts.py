@@ -318,3 +318,30 @@ def test_inplace_tma_sweeps(shape, storage):
         assert np.abs(gp.flows().cpu().numpy() - q_i).max() <= tol
     with gpu_problem(prob, schedule=pfm.INPLACE, grad_source=1) as gp:
         assert gp.variant == "inplace"
+
+
+def test_prefetch_commit_equals_set_data():
+    """pfm_prefetch_data + pfm_commit_data (copy on the library's copy stream,
+    overlapping queued iterations) gives the same state as pfm_set_data; a
+    second prefetch replaces the first; a commit without a prefetch is
+    rejected."""
+    import torch
+    import paper_1501_07844_gb300 as pfm
+    prob = synth.random_problem(170, (12, 21, 45), nl=5, s_kind="field")
+    other = synth.random_problem(171, (12, 21, 45), nl=5, s_kind="field")
+    hD, hS = torch.from_numpy(other.D).pin_memory(), torch.from_numpy(other.S_field).pin_memory()
+    junk = torch.rand_like(hD).pin_memory()
+    with gpu_problem(prob) as a, gpu_problem(prob) as b:
+        with pytest.raises(pfm.PfmError) as ei:
+            a.commit_data()
+        assert ei.value.name == "PFM_EINVAL"
+        a.iterate(7)
+        a.prefetch_data(junk, hS)
+        a.prefetch_data(hD, hS)      # replaces the first
+        a.iterate(5)                 # still on the old data
+        a.commit_data()
+        a.iterate(9)
+        b.iterate(12)
+        b.set_data(hD, hS)
+        b.iterate(9)
+        assert torch.equal(a.labels(), b.labels()) and torch.equal(a.flows(), b.flows())
