@@ -36,6 +36,10 @@ constexpr int DAG_TMA_NT = ((4 * DNE + 31) / 32) * 32;  // 672 threads
 constexpr int DAG_UY = DEY;                    // u / D box rows
 constexpr int DAG_QY = DEY + 1;                // flow box rows (y0-1 .. y0+4)
 constexpr int DMAX = 16;                       // max end-labels / nodes
+// Voxel stride of the per-voxel rows in shared memory: the rows are stored
+// transposed ([entry][voxel]) with a stride = 8 (mod 32), so the four lanes
+// of eight consecutive voxels touch 32 different banks.
+constexpr int DAG_NV = 168;
 
 struct DagLists {
     unsigned char anc_n[DMAX];          // ancestors of end-label j (incl. its own node)
@@ -63,7 +67,7 @@ struct DagTmaLayout {
         g_off = TMA_STAGES * stage_bytes;
         e_off = g_off + a128(2 * nf * DAG_UY * TMA_BX * 4);
         row = nl > nf ? nl : nf;
-        bar_off = e_off + a128(DNE * row * 4);
+        bar_off = e_off + a128(DAG_NV * row * 4);
         total = bar_off + 64 + 128;
     }
 };
@@ -158,7 +162,7 @@ __device__ __forceinline__ bool dag_tma_tile(const StepArgs<DMAX, DMAX>& a, cons
     const int xe = x0 + ex, ye = y0 + ey;
     const bool validE = inE && xe < nx && ye < ny;
     const bool ownerE = validE && v < FTX * DTY;
-    float* erow = ebuf + (inE ? v : 0) * lay.row;
+    float* ecol = ebuf + (inE ? v : 0);
     const int ui = ey * TMA_BX + ex;
     const int qi = (ey + 1) * QBX + (ex + QOFF);
     const long long vox = (long long)ye * px + xe;  // slot of this voxel in its plane
@@ -233,7 +237,7 @@ __device__ __forceinline__ bool dag_tma_tile(const StepArgs<DMAX, DMAX>& a, cons
                             qzc[i] = lds<T>(qS + (A * DIM + 2) * qstride + qi);
                             dv += qzc[i] - qzp[i];
                         }
-                        erow[A] = dv;
+                        ecol[(A) * DAG_NV] = dv;
                     }
                 }
             }
@@ -253,9 +257,9 @@ __device__ __forceinline__ bool dag_tma_tile(const StepArgs<DMAX, DMAX>& a, cons
                     // issue together), the rest in a loop
                     float acc[4];
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) acc[k] = k < na ? sl.anc_w[j][k] * erow[sl.anc[j][k]] : 0.f;
+                    for (int k = 0; k < 4; ++k) acc[k] = k < na ? sl.anc_w[j][k] * ecol[sl.anc[j][k] * DAG_NV] : 0.f;
                     dj += (acc[0] + acc[1]) + (acc[2] + acc[3]);
-                    for (int k = 4; k < na; ++k) dj = fmaf(sl.anc_w[j][k], erow[sl.anc[j][k]], dj);
+                    for (int k = 4; k < na; ++k) dj = fmaf(sl.anc_w[j][k], ecol[sl.anc[j][k] * DAG_NV], dj);
                     d[i] = dj;
                     mloc = fminf(mloc, dj);
                 }
@@ -285,7 +289,7 @@ __device__ __forceinline__ bool dag_tma_tile(const StepArgs<DMAX, DMAX>& a, cons
                     const int j = h + 4 * i;
                     if (j < nl) {
                         const float un = u[i] * inv;
-                        erow[j] = literal ? u[i] : un;
+                        ecol[(j) * DAG_NV] = literal ? u[i] : un;
                         if (ownerE && p < z1) stv<T>(slot_ptr<IDX32>(uout, j, p, n, plane, vox), un);
                     }
                 }
@@ -300,9 +304,9 @@ __device__ __forceinline__ bool dag_tma_tile(const StepArgs<DMAX, DMAX>& a, cons
                         const int nd = sl.desc_n[A];
                         float acc[4];
 #pragma unroll
-                        for (int k = 0; k < 4; ++k) acc[k] = k < nd ? sl.desc_w[A][k] * erow[sl.desc[A][k]] : 0.f;
+                        for (int k = 0; k < 4; ++k) acc[k] = k < nd ? sl.desc_w[A][k] * ecol[sl.desc[A][k] * DAG_NV] : 0.f;
                         float g = (acc[0] + acc[1]) + (acc[2] + acc[3]);
-                        for (int k = 4; k < nd; ++k) g = fmaf(sl.desc_w[A][k], erow[sl.desc[A][k]], g);
+                        for (int k = 4; k < nd; ++k) g = fmaf(sl.desc_w[A][k], ecol[sl.desc[A][k] * DAG_NV], g);
                         gcur[i] = g;
                         gC[A * ustride + ui] = g;
                     }
