@@ -567,7 +567,8 @@ def main():
     # the step's D and S current (uploaded by the library's copy stream while
     # the previous step ran: pfm_prefetch_data / pfm_commit_data), start the
     # next step's upload, iterate with the gap check, read the thresholded
-    # labelling back
+    # labelling back (pfm_get_argmax_async: the copy overlaps the next step;
+    # every read-back has landed before the timed region closes)
     e2e = None
     if not args.no_e2e:
         hD = torch.from_numpy(prob.D).pin_memory()
@@ -583,7 +584,8 @@ def main():
                 if k + 1 < k_steps:
                     gp.prefetch_data(hD, hS)
                 step()
-                gp.argmax(out=hL)
+                gp.argmax_async(out=hL)   # lands while the next step runs
+            gp.readback_wait()
         e2e_steps(max(1, args.warmup))
         barrier()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

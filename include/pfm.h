@@ -217,6 +217,23 @@ PFM_API pfm_status pfm_get_labels(pfm_problem* pb, float* dst);
 PFM_API pfm_status pfm_get_argmax(pfm_problem* pb, int32_t* dst);
 PFM_API pfm_status pfm_get_flows(pfm_problem* pb, float* dst);
 
+/* Asynchronous copy of the state (u, q; either may be NULL) into DEVICE
+ * memory, layouts as above, ordered on the problem's stream and not waited
+ * for (no counterpart in the paper: it serves callers that keep many states
+ * on the device, e.g. the recomputation of the adjoint).  Host pointers are
+ * rejected with PFM_EINVAL. */
+PFM_API pfm_status pfm_get_state_async(pfm_problem* pb, float* u_dst, float* q_dst);
+
+/* Asynchronous thresholded read-back (no counterpart in the paper): the
+ * argmax of the current labelling is formed on the problem's stream in a
+ * library buffer and copied to dst (host, pinned for a truly asynchronous
+ * copy, or device) on the library's copy stream, overlapping whatever is
+ * queued next; pfm_readback_wait blocks until the last such copy has
+ * landed.  A second call waits (on the device) for the previous copy before
+ * reusing the buffer.  dst must stay valid until the wait. */
+PFM_API pfm_status pfm_get_argmax_async(pfm_problem* pb, int32_t* dst);
+PFM_API pfm_status pfm_readback_wait(pfm_problem* pb);
+
 /* Overwrites the state from caller memory (host or device), same layouts as
  * the getters, converted to the storage type.  Flows are projected onto the
  * capacity set and the normal component at the last index of each axis is

@@ -24,7 +24,7 @@ class PottsSolve(torch.autograd.Function):
         ckpts = []
         k = 0
         while k < iters:
-            ckpts.append((k, prob.labels(), prob.flows()))
+            ckpts.append((k,) + prob.state_async())
             step = min(checkpoint_every, iters - k)
             prob.iterate(step)
             k += step
@@ -53,8 +53,9 @@ class PottsSolve(torch.autograd.Function):
             us, qs = [u0], [q0]
             for _ in range(seg):
                 prob.iterate(1)
-                us.append(prob.labels())
-                qs.append(prob.flows())
+                u1, q1 = prob.state_async()
+                us.append(u1)
+                qs.append(q1)
             for i in reversed(range(seg)):
                 prob.adjoint_step(us[i], qs[i], us[i + 1], ubar, qbar, ubar, qbar, Dbar,
                                   Sbar if Sbar is not None else dummy, work)

@@ -54,6 +54,9 @@ _SIGS = {
     "pfm_set_data": (C.c_int, [_P, _P, _P]),
     "pfm_prefetch_data": (C.c_int, [_P, _P, _P]),
     "pfm_commit_data": (C.c_int, [_P]),
+    "pfm_get_state_async": (C.c_int, [_P, _P, _P]),
+    "pfm_get_argmax_async": (C.c_int, [_P, _P]),
+    "pfm_readback_wait": (C.c_int, [_P]),
     "pfm_reset": (C.c_int, [_P]),
     "pfm_iterate": (C.c_int, [_P, C.c_int]),
     "pfm_set_step": (C.c_int, [_P, C.c_double, C.c_double]),
@@ -320,11 +323,32 @@ class Problem:
         check(lib().pfm_get_argmax(self._h, _ptr(out)))
         return out
 
+    def argmax_async(self, out):
+        """pfm_get_argmax_async into `out` (int32, pinned host or device);
+        complete after readback_wait()."""
+        self._readback = out
+        check(lib().pfm_get_argmax_async(self._h, _ptr(out)))
+        return out
+
+    def readback_wait(self):
+        check(lib().pfm_readback_wait(self._h))
+
     def flows(self, out=None):
         import torch
         out = self._out((self.n_nodes, self.ndim) + self.spatial, torch.float32, out)
         check(lib().pfm_get_flows(self._h, _ptr(out)))
         return out
+
+    def state_async(self, u_out=None, q_out=None):
+        """pfm_get_state_async: device copies of u and q ordered on the
+        problem's stream, not waited for."""
+        import torch
+        u_out = u_out if u_out is not None else torch.empty((self.n_leaf,) + self.spatial, dtype=torch.float32,
+                                                            device="cuda")
+        q_out = q_out if q_out is not None else torch.empty((self.n_nodes, self.ndim) + self.spatial,
+                                                            dtype=torch.float32, device="cuda")
+        check(lib().pfm_get_state_async(self._h, _ptr(u_out), _ptr(q_out)))
+        return u_out, q_out
 
     def set_labels(self, u):
         u = _as_f32(u)

@@ -43,7 +43,9 @@ __device__ __forceinline__ void coords(long long i, int nx, int ny, int& x, int&
     z = (int)(r / ny);
 }
 
-template <int DIM>
+// L: compile-time bound on the label count (4, 8 or 16), so the label loops
+// unroll and the per-label values live in registers.
+template <int L, int DIM>
 __global__ void __launch_bounds__(NT) adj_proj_kernel(const AdjArgs a) {
     const long long i = (long long)blockIdx.x * NT + threadIdx.x;
     if (i >= a.n) return;
@@ -52,7 +54,9 @@ __global__ void __launch_bounds__(NT) adj_proj_kernel(const AdjArgs a) {
     const long long n = a.n, plane = (long long)a.nx * a.ny;
     const float sf = a.S ? a.S[pitched(a, i, x)] : 1.0f;
     float sbar = 0.f;
-    for (int j = 0; j < a.nl; ++j) {
+#pragma unroll
+    for (int j = 0; j < L; ++j) {
+        if (j >= a.nl) break;
         const float* u1 = a.u_k1 + (long long)j * n + i;
         const float g0 = *u1;
         float gr[DIM];
@@ -98,7 +102,7 @@ __global__ void __launch_bounds__(NT) adj_proj_kernel(const AdjArgs a) {
     if (a.Sbar) a.Sbar[i] += sbar;
 }
 
-template <int DIM>
+template <int L, int DIM>
 __global__ void __launch_bounds__(NT) adj_prox_kernel(const AdjArgs a) {
     const long long i = (long long)blockIdx.x * NT + threadIdx.x;
     if (i >= a.n) return;
@@ -106,10 +110,13 @@ __global__ void __launch_bounds__(NT) adj_prox_kernel(const AdjArgs a) {
     coords(i, a.nx, a.ny, x, y, z);
     const long long n = a.n, plane = (long long)a.nx * a.ny;
     const long long pi = pitched(a, i, x);
-    float d[16], ub[16], u1[16];
+    float d[L], ub[L], u1[L];
     float m = 3.0e38f;
     float dot = 0.f;
-    for (int j = 0; j < a.nl; ++j) {
+#pragma unroll
+    for (int j = 0; j < L; ++j) {
+        d[j] = ub[j] = u1[j] = 0.f;
+        if (j >= a.nl) continue;
         // d_j = D_j + div q_j  (forward recomputation)
         const float* qa = a.q_k + (long long)j * DIM * n + i;
         float dv = (x < a.nx - 1 ? qa[0] : 0.f) - (x > 0 ? qa[-1] : 0.f);
@@ -127,12 +134,16 @@ __global__ void __launch_bounds__(NT) adj_prox_kernel(const AdjArgs a) {
         dot += u1[j] * ub[j];
     }
     float asum = 0.f;
-    for (int j = 0; j < a.nl; ++j) {
+#pragma unroll
+    for (int j = 0; j < L; ++j) {
+        if (j >= a.nl) continue;
         d[j] = __expf(-(d[j] - m) / a.c);  // e_j (shifted)
         asum += a.u_k[(long long)j * n + i] * d[j];
     }
     const float inv_a = 1.0f / asum;
-    for (int j = 0; j < a.nl; ++j) {
+#pragma unroll
+    for (int j = 0; j < L; ++j) {
+        if (j >= a.nl) continue;
         const float w = ub[j] - dot;
         a.ubar_k[(long long)j * n + i] = d[j] * inv_a * w;
         const float dbar = -u1[j] * w / a.c;
@@ -141,14 +152,16 @@ __global__ void __launch_bounds__(NT) adj_prox_kernel(const AdjArgs a) {
     }
 }
 
-template <int DIM>
+template <int L, int DIM>
 __global__ void __launch_bounds__(NT) adj_div_kernel(const AdjArgs a) {
     const long long i = (long long)blockIdx.x * NT + threadIdx.x;
     if (i >= a.n) return;
     int x, y, z;
     coords(i, a.nx, a.ny, x, y, z);
     const long long n = a.n, plane = (long long)a.nx * a.ny;
-    for (int j = 0; j < a.nl; ++j) {
+#pragma unroll
+    for (int j = 0; j < L; ++j) {
+        if (j >= a.nl) break;
         const float* db = a.dbar + (long long)j * n + i;
         const float d0 = *db;
         float gr[DIM];
@@ -162,18 +175,26 @@ __global__ void __launch_bounds__(NT) adj_div_kernel(const AdjArgs a) {
     }
 }
 
+template <int L, int DIM>
+void launch3(const AdjArgs& a, unsigned b, cudaStream_t s) {
+    adj_proj_kernel<L, DIM><<<b, NT, 0, s>>>(a);
+    adj_prox_kernel<L, DIM><<<b, NT, 0, s>>>(a);
+    adj_div_kernel<L, DIM><<<b, NT, 0, s>>>(a);
+}
+
 }  // namespace
 
 cudaError_t launch_adjoint(const AdjArgs& a, int ndim, cudaStream_t s) {
     const unsigned b = (unsigned)((a.n + NT - 1) / NT);
+    const int L = a.nl <= 4 ? 4 : a.nl <= 8 ? 8 : 16;
     if (ndim == 3) {
-        adj_proj_kernel<3><<<b, NT, 0, s>>>(a);
-        adj_prox_kernel<3><<<b, NT, 0, s>>>(a);
-        adj_div_kernel<3><<<b, NT, 0, s>>>(a);
+        if (L == 4) launch3<4, 3>(a, b, s);
+        else if (L == 8) launch3<8, 3>(a, b, s);
+        else launch3<16, 3>(a, b, s);
     } else {
-        adj_proj_kernel<2><<<b, NT, 0, s>>>(a);
-        adj_prox_kernel<2><<<b, NT, 0, s>>>(a);
-        adj_div_kernel<2><<<b, NT, 0, s>>>(a);
+        if (L == 4) launch3<4, 2>(a, b, s);
+        else if (L == 8) launch3<8, 2>(a, b, s);
+        else launch3<16, 2>(a, b, s);
     }
     return cudaGetLastError();
 }

@@ -240,6 +240,10 @@ struct pfm_problem {
     cudaEvent_t staged = nullptr;    // the prefetch copy is complete
     cudaEvent_t consumed = nullptr;  // the last commit has moved the staged data
     bool stage_pending = false;
+    // asynchronous argmax read-back (pfm_get_argmax_async)
+    int* am_buf = nullptr;
+    cudaEvent_t am_ready = nullptr;   // the argmax kernel has written am_buf
+    cudaEvent_t am_done = nullptr;    // the copy out of am_buf has landed
 };
 
 namespace {
@@ -291,6 +295,10 @@ void free_all(pfm_problem* pb) {
                     pb->flags, pb->partial, pb->result, pb->D_stage, pb->S_stage};
     for (void* p : ptrs)
         if (p) cudaFree(p);
+    if (pb->am_done) cudaEventSynchronize(pb->am_done);
+    if (pb->am_buf) cudaFree(pb->am_buf);
+    if (pb->am_ready) cudaEventDestroy(pb->am_ready);
+    if (pb->am_done) cudaEventDestroy(pb->am_done);
     if (pb->staged) cudaEventDestroy(pb->staged);
     if (pb->consumed) cudaEventDestroy(pb->consumed);
     if (pb->copy_stream) cudaStreamDestroy(pb->copy_stream);
@@ -380,6 +388,7 @@ static cudaError_t copy_rows(void* dst, int dpitch, const void* src, int spitch,
 
 static pfm_status create_impl(const pfm_desc* desc, const pfm_params* params, void* stream, bool dense,
                               pfm_problem** out);
+static pfm_status ensure_copy_stream(pfm_problem* pb);
 
 pfm_status pfm_create(const pfm_desc* desc, const pfm_params* params, void* stream, pfm_problem** out) {
     return create_impl(desc, params, stream, false, out);
@@ -519,8 +528,9 @@ pfm_status pfm_prefetch_data(pfm_problem* pb, const float* D, const float* S_fie
     if (!pb || !D) return fail(PFM_EINVAL, "NULL argument");
     if ((S_field != nullptr) != (pb->S != nullptr))
         return fail(PFM_EINVAL, "S_field must be given iff the problem was created with one");
-    if (!pb->copy_stream) {
-        PFM_CUDA(cudaStreamCreateWithFlags(&pb->copy_stream, cudaStreamNonBlocking), "copy stream");
+    if (!pb->staged) {
+        pfm_status st = ensure_copy_stream(pb);
+        if (st != PFM_OK) return st;
         PFM_CUDA(cudaEventCreateWithFlags(&pb->staged, cudaEventDisableTiming), "event");
         PFM_CUDA(cudaEventCreateWithFlags(&pb->consumed, cudaEventDisableTiming), "event");
         PFM_CUDA(cudaEventRecord(pb->consumed, pb->stream), "event");
@@ -723,6 +733,73 @@ pfm_status pfm_get_flows(pfm_problem* pb, float* dst) {
         if (e != cudaSuccess) return cuda_fail(e, "flows");
     }
     PFM_CUDA(cudaStreamSynchronize(pb->stream), "stream sync");
+    return PFM_OK;
+}
+
+pfm_status pfm_get_state_async(pfm_problem* pb, float* u_dst, float* q_dst) {
+    if (!pb || (!u_dst && !q_dst)) return fail(PFM_EINVAL, "NULL argument");
+    for (const void* p : {(const void*)u_dst, (const void*)q_dst}) {
+        if (!p) continue;
+        cudaPointerAttributes at{};
+        const bool dev = cudaPointerGetAttributes(&at, p) == cudaSuccess && at.type == cudaMemoryTypeDevice;
+        cudaGetLastError();
+        if (!dev) return fail(PFM_EINVAL, "pfm_get_state_async needs device destinations");
+    }
+    const long long zy = (long long)pb->ny * pb->nz;
+    if (u_dst) {
+        const long long rows = (long long)pb->nl * zy;
+        if (pb->prm.storage == PFM_STORAGE_F32) {
+            PFM_CUDA(copy_rows(u_dst, pb->nx, pb->u[pb->cur], pb->px, pb->nx, rows, pb->stream), "copy labels");
+        } else {
+            PFM_CUDA(pfm::launch_to_f32(pb->u[pb->cur], pb->prm.storage, rows, pb->nx, pb->px, u_dst, pb->stream),
+                     "labels");
+            pb->launches++;
+        }
+    }
+    if (q_dst) {
+        const long long rows = (long long)pb->nn * pb->ndim * zy;
+        if (pb->prm.storage == PFM_STORAGE_F32) {
+            PFM_CUDA(copy_rows(q_dst, pb->nx, pb->q[pb->cur], pb->px, pb->nx, rows, pb->stream), "copy flows");
+        } else {
+            PFM_CUDA(pfm::launch_to_f32(pb->q[pb->cur], pb->prm.storage, rows, pb->nx, pb->px, q_dst, pb->stream),
+                     "flows");
+            pb->launches++;
+        }
+    }
+    return PFM_OK;
+}
+
+static pfm_status ensure_copy_stream(pfm_problem* pb) {
+    if (!pb->copy_stream) PFM_CUDA(cudaStreamCreateWithFlags(&pb->copy_stream, cudaStreamNonBlocking), "copy stream");
+    return PFM_OK;
+}
+
+pfm_status pfm_get_argmax_async(pfm_problem* pb, int32_t* dst) {
+    if (!pb || !dst) return fail(PFM_EINVAL, "NULL argument");
+    pfm_status st = ensure_copy_stream(pb);
+    if (st != PFM_OK) return st;
+    if (!pb->am_buf) {
+        PFM_CUDA(cudaMalloc(&pb->am_buf, pb->nv * 4), "alloc argmax buffer");
+        PFM_CUDA(cudaEventCreateWithFlags(&pb->am_ready, cudaEventDisableTiming), "event");
+        PFM_CUDA(cudaEventCreateWithFlags(&pb->am_done, cudaEventDisableTiming), "event");
+        PFM_CUDA(cudaEventRecord(pb->am_done, pb->copy_stream), "event");
+    }
+    // the previous copy out of the buffer must have landed before it is rewritten
+    PFM_CUDA(cudaStreamWaitEvent(pb->stream, pb->am_done, 0), "wait");
+    PFM_CUDA(pfm::launch_argmax(pb->u[pb->cur], pb->prm.storage, pb->nl, pb->n, pb->nx, pb->px, pb->nv, pb->am_buf,
+                                pb->stream),
+             "argmax");
+    pb->launches++;
+    PFM_CUDA(cudaEventRecord(pb->am_ready, pb->stream), "event");
+    PFM_CUDA(cudaStreamWaitEvent(pb->copy_stream, pb->am_ready, 0), "wait");
+    PFM_CUDA(cudaMemcpyAsync(dst, pb->am_buf, pb->nv * 4, cudaMemcpyDefault, pb->copy_stream), "copy argmax");
+    PFM_CUDA(cudaEventRecord(pb->am_done, pb->copy_stream), "event");
+    return PFM_OK;
+}
+
+pfm_status pfm_readback_wait(pfm_problem* pb) {
+    if (!pb) return fail(PFM_EINVAL, "NULL problem");
+    if (pb->am_done) PFM_CUDA(cudaEventSynchronize(pb->am_done), "wait");
     return PFM_OK;
 }
 

@@ -345,3 +345,43 @@ def test_prefetch_commit_equals_set_data():
         b.set_data(hD, hS)
         b.iterate(9)
         assert torch.equal(a.labels(), b.labels()) and torch.equal(a.flows(), b.flows())
+
+
+@pytest.mark.parametrize("storage", [0, 1], ids=["f32", "bf16"])
+def test_state_async_equals_readback(storage):
+    """pfm_get_state_async (device destinations, stream-ordered, no wait)
+    gives the same dense arrays as pfm_get_labels / pfm_get_flows, padded
+    rows included; host destinations are rejected."""
+    import torch
+    import paper_1501_07844_gb300 as pfm
+    prob = synth.random_problem(180, (9, 13, 37), nl=5, s_kind="both")
+    with gpu_problem(prob, storage=storage) as gp:
+        gp.iterate(11)
+        u, q = gp.state_async()
+        gp.iterate(3)               # queued after the copies
+        torch.cuda.synchronize()
+        gp2 = None
+        with gpu_problem(prob, storage=storage) as ref:
+            ref.iterate(11)
+            assert torch.equal(u, ref.labels()) and torch.equal(q, ref.flows())
+        with pytest.raises(pfm.PfmError) as ei:
+            gp.state_async(u_out=torch.empty_like(u.cpu()))
+        assert ei.value.name == "PFM_EINVAL"
+
+
+def test_argmax_async_equals_argmax():
+    """pfm_get_argmax_async into pinned host memory, landed after
+    pfm_readback_wait, equals pfm_get_argmax; a second read-back reuses the
+    buffer only after the first copy."""
+    import torch
+    prob = synth.random_problem(190, (11, 17, 29), nl=6, s_kind="field")
+    with gpu_problem(prob) as gp:
+        h1 = torch.empty((11, 17, 29), dtype=torch.int32).pin_memory()
+        h2 = torch.empty_like(h1).pin_memory()
+        gp.iterate(5)
+        gp.argmax_async(out=h1)
+        ref1 = gp.argmax().cpu()
+        gp.iterate(25)
+        gp.argmax_async(out=h2)
+        gp.readback_wait()
+        assert torch.equal(h1, ref1) and torch.equal(h2, gp.argmax().cpu())
