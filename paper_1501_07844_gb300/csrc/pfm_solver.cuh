@@ -19,7 +19,7 @@ namespace pfm {
 
 // Encodes a tiled TMA descriptor (pfm_api.cu; driver entry point looked up
 // through the runtime).  dims / box are innermost first; strides in bytes
-// for dims 1..rank-1.  Returns false if the driver rejects the map.
+// for dims 1..rank-1.  Returns false if the CUDA driver rejects the map.
 bool encode_tiled_map(CUtensorMap* map, const void* base, int elem_bytes, int rank, const unsigned long long* dims,
                       const unsigned long long* strides, const unsigned* box);
 

@@ -23,7 +23,7 @@ def orc():
 
 def pytest_collection_modifyitems(config, items):
     """GPU tests need a CUDA device; on a machine without one they are
-    skipped (the driver's CPU run deselects them with -m "not gpu")."""
+    skipped (a CPU-only run deselects them with -m "not gpu")."""
     try:
         import torch
         has_gpu = torch.cuda.is_available()
