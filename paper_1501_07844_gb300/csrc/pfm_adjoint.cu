@@ -102,51 +102,67 @@ __global__ void __launch_bounds__(NT) adj_proj_kernel(const AdjArgs a) {
     if (a.Sbar) a.Sbar[i] += sbar;
 }
 
+// Two threads per voxel, each owning every other label (j = h, h+2, ...):
+// half the registers per thread and twice the loads in flight per voxel; the
+// per-voxel minimum, <u', ubar'> and the normaliser are combined with one lane
+// shuffle each.
 template <int L, int DIM>
 __global__ void __launch_bounds__(NT) adj_prox_kernel(const AdjArgs a) {
-    const long long i = (long long)blockIdx.x * NT + threadIdx.x;
-    if (i >= a.n) return;
-    int x, y, z;
-    coords(i, a.nx, a.ny, x, y, z);
+    constexpr int HL = L / 2;
+    const long long gt = (long long)blockIdx.x * NT + threadIdx.x;
+    const long long i = gt >> 1;
+    const int h = (int)(gt & 1);
+    const bool live = i < a.n;  // both lanes of a pair agree; every lane reaches the shuffles
+    int x = 0, y = 0, z = 0;
+    long long pi = 0;
+    if (live) {
+        coords(i, a.nx, a.ny, x, y, z);
+        pi = pitched(a, i, x);
+    }
     const long long n = a.n, plane = (long long)a.nx * a.ny;
-    const long long pi = pitched(a, i, x);
-    float d[L], ub[L], u1[L];
+    float d[HL], ub[HL], u1[HL];
     float m = 3.0e38f;
     float dot = 0.f;
 #pragma unroll
-    for (int j = 0; j < L; ++j) {
-        d[j] = ub[j] = u1[j] = 0.f;
-        if (j >= a.nl) continue;
+    for (int k = 0; k < HL; ++k) {
+        const int j = h + 2 * k;
+        d[k] = ub[k] = u1[k] = 0.f;
+        if (!live || j >= a.nl) continue;
         // d_j = D_j + div q_j  (forward recomputation)
         const float* qa = a.q_k + (long long)j * DIM * n + i;
         float dv = (x < a.nx - 1 ? qa[0] : 0.f) - (x > 0 ? qa[-1] : 0.f);
         dv += (y < a.ny - 1 ? qa[n] : 0.f) - (y > 0 ? qa[n - a.nx] : 0.f);
         if constexpr (DIM == 3) dv += (z < a.nz - 1 ? qa[2 * n] : 0.f) - (z > 0 ? qa[2 * n - plane] : 0.f);
-        d[j] = a.D[(long long)j * a.np + pi] + dv;
-        m = fminf(m, d[j]);
+        d[k] = a.D[(long long)j * a.np + pi] + dv;
+        m = fminf(m, d[k]);
         // ubar'_j + c tau div ybar_j
         const float* yb = a.ybar + (long long)j * DIM * n + i;
         float dy = (x < a.nx - 1 ? yb[0] : 0.f) - (x > 0 ? yb[-1] : 0.f);
         dy += (y < a.ny - 1 ? yb[n] : 0.f) - (y > 0 ? yb[n - a.nx] : 0.f);
         if constexpr (DIM == 3) dy += (z < a.nz - 1 ? yb[2 * n] : 0.f) - (z > 0 ? yb[2 * n - plane] : 0.f);
-        ub[j] = a.ubar_k1[(long long)j * n + i] + a.ctau * dy;
-        u1[j] = a.u_k1[(long long)j * n + i];
-        dot += u1[j] * ub[j];
+        ub[k] = a.ubar_k1[(long long)j * n + i] + a.ctau * dy;
+        u1[k] = a.u_k1[(long long)j * n + i];
+        dot += u1[k] * ub[k];
     }
+    m = fminf(m, __shfl_xor_sync(0xffffffffu, m, 1));
+    dot += __shfl_xor_sync(0xffffffffu, dot, 1);
     float asum = 0.f;
 #pragma unroll
-    for (int j = 0; j < L; ++j) {
-        if (j >= a.nl) continue;
-        d[j] = __expf(-(d[j] - m) / a.c);  // e_j (shifted)
-        asum += a.u_k[(long long)j * n + i] * d[j];
+    for (int k = 0; k < HL; ++k) {
+        const int j = h + 2 * k;
+        if (!live || j >= a.nl) continue;
+        d[k] = __expf(-(d[k] - m) / a.c);  // e_j (shifted)
+        asum += a.u_k[(long long)j * n + i] * d[k];
     }
+    asum += __shfl_xor_sync(0xffffffffu, asum, 1);
     const float inv_a = 1.0f / asum;
 #pragma unroll
-    for (int j = 0; j < L; ++j) {
-        if (j >= a.nl) continue;
-        const float w = ub[j] - dot;
-        a.ubar_k[(long long)j * n + i] = d[j] * inv_a * w;
-        const float dbar = -u1[j] * w / a.c;
+    for (int k = 0; k < HL; ++k) {
+        const int j = h + 2 * k;
+        if (!live || j >= a.nl) continue;
+        const float w = ub[k] - dot;
+        a.ubar_k[(long long)j * n + i] = d[k] * inv_a * w;
+        const float dbar = -u1[k] * w / a.c;
         a.dbar[(long long)j * n + i] = dbar;
         a.Dbar[(long long)j * n + i] += dbar;
     }
@@ -175,26 +191,29 @@ __global__ void __launch_bounds__(NT) adj_div_kernel(const AdjArgs a) {
     }
 }
 
+// one thread per voxel for the projection and divergence adjoints, two for
+// the prox adjoint (measured: the split pays only where a voxel's per-label
+// work is heaviest)
 template <int L, int DIM>
-void launch3(const AdjArgs& a, unsigned b, cudaStream_t s) {
-    adj_proj_kernel<L, DIM><<<b, NT, 0, s>>>(a);
-    adj_prox_kernel<L, DIM><<<b, NT, 0, s>>>(a);
-    adj_div_kernel<L, DIM><<<b, NT, 0, s>>>(a);
+void launch3(const AdjArgs& a, cudaStream_t s) {
+    const unsigned b1 = (unsigned)((a.n + NT - 1) / NT), b2 = (unsigned)((2 * a.n + NT - 1) / NT);
+    adj_proj_kernel<L, DIM><<<b1, NT, 0, s>>>(a);
+    adj_prox_kernel<L, DIM><<<b2, NT, 0, s>>>(a);
+    adj_div_kernel<L, DIM><<<b1, NT, 0, s>>>(a);
 }
 
 }  // namespace
 
 cudaError_t launch_adjoint(const AdjArgs& a, int ndim, cudaStream_t s) {
-    const unsigned b = (unsigned)((a.n + NT - 1) / NT);
     const int L = a.nl <= 4 ? 4 : a.nl <= 8 ? 8 : 16;
     if (ndim == 3) {
-        if (L == 4) launch3<4, 3>(a, b, s);
-        else if (L == 8) launch3<8, 3>(a, b, s);
-        else launch3<16, 3>(a, b, s);
+        if (L == 4) launch3<4, 3>(a, s);
+        else if (L == 8) launch3<8, 3>(a, s);
+        else launch3<16, 3>(a, s);
     } else {
-        if (L == 4) launch3<4, 2>(a, b, s);
-        else if (L == 8) launch3<8, 2>(a, b, s);
-        else launch3<16, 2>(a, b, s);
+        if (L == 4) launch3<4, 2>(a, s);
+        else if (L == 8) launch3<8, 2>(a, s);
+        else launch3<16, 2>(a, s);
     }
     return cudaGetLastError();
 }
