@@ -43,7 +43,8 @@ CONFIGS = {
     "diff": ((128, 128, 128), 6, "potts3d", 0, 0),
     "capacity": ((512, 512, 512), 8, "potts3d", 1, 0),
 }
-KERNEL_SOURCES = [os.path.join(ROOT, "paper_1501_07844_gb300", "csrc", f) for f in ("pfm_device.cuh", "pfm_tma.cuh")]
+KERNEL_SOURCES = [os.path.join(ROOT, "paper_1501_07844_gb300", "csrc", f)
+                  for f in ("pfm_device.cuh", "pfm_tma.cuh", "pfm_tma_x2.cuh")]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic.json")
 
 
@@ -58,6 +59,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--dims", type=int, default=0, help="cube edge override (profiling of small cases)")
     ap.add_argument("--volumes", type=int, default=32, help="volumes of the batched workload (profiling of small cases)")
+    ap.add_argument("--zc", type=int, default=0, help="z-chunk length instead of the tuned one (profiling of small cases)")
     return ap.parse_args()
 
 
@@ -288,21 +290,49 @@ def run_batched(args, rank, world):
     it_ms = sum(a.elapsed_time(c) for a, c in ev) / (args.steps * ITERS_PER_STEP)
     peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6800.0)
     achieved = alg / (it_ms / 1e3) / 1e9
+    launches = int(b.launches - l0)
+    variant = b.variant
+    b.close()
+    del b
+    torch.cuda.empty_cache()
+    # the plain FP32 form on the same volumes: one single-problem solver per
+    # volume (fused TMA DAG kernel), stepped one after another on the stream
+    singles = [pfm.Problem(p["D"], S_field=p["S_field"], s_node=p["s_node"], n_nodes=p["n_nodes"],
+                           edges=p["edges"], c=0.5, tau=0.11, stream=stream.cuda_stream) for p in probs]
+    for _ in range(args.warmup):
+        for sp in singles:
+            sp.iterate(ITERS_PER_STEP)
+            sp.energy()
+    torch.cuda.synchronize()
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s0.record(stream)
+    for k in range(args.steps):
+        for sp in singles:
+            sp.iterate(ITERS_PER_STEP)
+            sp.energy()
+    s1.record(stream)
+    torch.cuda.synchronize()
+    single_elapsed = s0.elapsed_time(s1) / 1e3
+    for sp in singles:
+        sp.close()
+    singles_line = {"value": args.steps * vlu_step / single_elapsed, "unit": "VLU/s",
+                    "ms_per_step": 1e3 * single_elapsed / args.steps,
+                    "kernel": "fused_dag_tma_kernel, one problem per volume",
+                    "batched_over_singles": single_elapsed / elapsed}
     line = {"metric": "voxel-label updates/s (dagmf_batched)", "value": args.steps * vlu_step / elapsed, "unit": "VLU/s",
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "dagmf_batched", "volumes": len(vols), "voxels": vox, "labels": 10, "nodes": 14,
                        "iters_per_step": ITERS_PER_STEP, "tuned_zc": zc, "tuned_grid": grid,
-                       "kernel_variant": b.variant,
+                       "kernel_variant": variant,
                        "shapes": [list(p.spatial) for p in vols]},
-            "roofline": {"bound": "hbm", "kernel": {"batched_tma_dag": "batched_dag_tma_kernel"}.get(b.variant, "batched_step_kernel"), "achieved": achieved, "peak": peak,
+            "roofline": {"bound": "hbm", "kernel": {"batched_tma_dag": "batched_dag_tma_kernel"}.get(variant, "batched_step_kernel"), "achieved": achieved, "peak": peak,
                          "unit": "GB/s", "frac": achieved / peak, "peak_source": "measured",
-                         "traffic": load_traffic("dagmf_batched") if (b.variant == "batched_tma_dag" and len(vols) == 32) else None,
+                         "traffic": load_traffic("dagmf_batched") if (variant == "batched_tma_dag" and len(vols) == 32) else None,
                          "algorithmic_bytes_per_launch": alg,
                          "kernel_ms_per_launch": it_ms},
-            "gpu_launches": int(b.launches - l0), "clocks": clk.summary()}
+            "gpu_launches": launches, "clocks": clk.summary(), "plain_fp32_singles": singles_line}
     print(json.dumps(line), flush=True)
-    b.close()
 
 
 def run_continuation(args):
@@ -525,6 +555,12 @@ def main():
     gp = pfm.Problem(D, S_field=S, s_node=prob.s_node, n_nodes=prob.n_nodes, edges=prob.edges,
                      c=prob.c, tau=prob.tau, schedule=schedule, storage=storage,
                      stream=stream.cuda_stream)
+    # z-chunk length of the plane-marching kernels picked by the autotuner
+    # (the trials are discarded: the state starts from the initial one)
+    zc = gp.tune(3)
+    if args.zc:
+        gp.chunk_length = args.zc
+        zc = gp.chunk_length
     n = int(np.prod(shape))
     vlu_step = ITERS_PER_STEP * n * prob.n_nodes
     alg_bytes = algorithmic_bytes_per_iter(prob, storage, schedule)
@@ -608,7 +644,9 @@ def main():
     peak = peak or 6800.0
     achieved = alg_bytes / (kern_ms / 1e3) / 1e9
     traffic = load_traffic(cfg)
-    kname = {"fused_tma": "fused_tma_kernel", "fused_tma_dag": "fused_dag_tma_kernel", "fused": "fused_step_kernel",
+    # 3-D Potts iterations with BF16 storage run the voxel-pair kernel
+    kname = {"fused_tma": "fused_tma_x2_kernel" if (len(shape) == 3 and storage == 1) else "fused_tma_kernel",
+             "fused_tma_dag": "fused_dag_tma_kernel", "fused": "fused_step_kernel",
              "inplace": "prox_inplace_kernel+flow_inplace_kernel",
              "inplace_tma": "prox_inplace_tma_kernel+flow_inplace_tma_kernel"}.get(gp.variant, gp.variant)
 
@@ -629,6 +667,7 @@ def main():
         "data": "synthetic (seeded sphere phantom)",
         "config": {"workload": cfg, "dims": list(shape), "labels": prob.n_leaf, "nodes": prob.n_nodes,
                    "iters_per_step": ITERS_PER_STEP, "schedule": "fused" if schedule == 0 else "in-place",
+                   "tuned_zc": zc,
                    "c": prob.c, "tau": prob.tau, "norm": "iso", "grad_source": "normalised",
                    "l2": "inputs larger than L2 (%.2f GB moved per iteration)" % (alg_bytes / 1e9),
                    "parallelism": "independent volume per GPU" if world > 1 else "single GPU"},

@@ -257,6 +257,24 @@ PFM_API const char* pfm_kernel_variant(const pfm_problem* pb);
 PFM_API int64_t pfm_iterations_done(const pfm_problem* pb);
 PFM_API int64_t pfm_launch_count(const pfm_problem* pb);
 
+/* Autotuner of the plane-marching kernels (the iteration kernels walk their
+ * tile through a chunk of consecutive z-planes; one CTA per tile and chunk):
+ * times trial_iters iterations (after one warm-up iteration) for each chunk
+ * length in {4, 8, 16, 32, 64, 128} and the cost model's choice made at
+ * create (all clamped to nz), keeps the fastest and writes it to *zc_out
+ * (may be NULL).  The trials advance the state, so the problem is reset to
+ * its initial state (as pfm_reset) afterwards: tune before pfm_set_labels /
+ * pfm_set_flows.  Synchronises the stream.  Not part of the paper's method
+ * (a launch-configuration search): the iterates u, q do not depend on the
+ * chunk length (every voxel's arithmetic is the same), the energy's
+ * summation order does. */
+PFM_API pfm_status pfm_tune(pfm_problem* pb, int trial_iters, int* zc_out);
+/* Sets the z-chunk length (zc >= 1, clamped to nz; PFM_EINVAL otherwise)
+ * for the following launches; may reallocate the energy partials (and then
+ * synchronises the stream).  pfm_chunk_length returns it (-1 for NULL). */
+PFM_API pfm_status pfm_set_chunk_length(pfm_problem* pb, int zc);
+PFM_API int pfm_chunk_length(const pfm_problem* pb);
+
 /* Reverse-mode step of one Potts iteration (the paper has no gradient; this differentiates the unrolled iteration of
  * Algorithm 1, NORMALISED gradient source, ISO or ANISO, flat label set).
  * Given the forward input state (u_k, q_k) of an iteration, its output

@@ -73,6 +73,9 @@ _SIGS = {
     "pfm_kernel_variant": (C.c_char_p, [_P]),
     "pfm_iterations_done": (C.c_int64, [_P]),
     "pfm_launch_count": (C.c_int64, [_P]),
+    "pfm_tune": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int)]),
+    "pfm_set_chunk_length": (C.c_int, [_P, C.c_int]),
+    "pfm_chunk_length": (C.c_int, [_P]),
     "pfm_adjoint_step": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "pfm_batch_create": (C.c_int, [C.c_int, C.c_void_p, C.POINTER(pfm_params), _P, C.POINTER(_P)]),
     "pfm_batch_destroy": (None, [_P]),
@@ -284,6 +287,21 @@ class Problem:
         E, P = C.c_double(), C.c_double()
         check(lib().pfm_iterate_energy(self._h, int(n), C.byref(E), C.byref(P)))
         return E.value, P.value
+
+    def tune(self, trial_iters=3):
+        """Times the z-chunk lengths and keeps the fastest; resets the state
+        to the initial one.  Returns the chunk length."""
+        zc = C.c_int()
+        check(lib().pfm_tune(self._h, int(trial_iters), C.byref(zc)))
+        return zc.value
+
+    @property
+    def chunk_length(self):
+        return lib().pfm_chunk_length(self._h)
+
+    @chunk_length.setter
+    def chunk_length(self, zc):
+        check(lib().pfm_set_chunk_length(self._h, int(zc)))
 
     def run_to_gap(self, max_iters):
         it, gap = C.c_int(), C.c_double()

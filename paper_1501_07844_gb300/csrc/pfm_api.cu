@@ -110,6 +110,41 @@ pfm_status analyse_dag(const pfm_desc* d, DagInfo* out) {
 }
 
 int potts_bucket(int nl) { return nl <= 4 ? 4 : nl <= 8 ? 8 : nl <= 16 ? 16 : 0; }
+
+// z-chunk length of the plane-marching kernels from a cost model: a CTA of
+// chunk length zc costs about zc + 3 plane times (the chunk, the flows of
+// plane z0-1 and the pipeline fill), CTAs run in waves of `sms` (one CTA per
+// SM: the staging ring takes most of the shared memory), so the launch
+// costs ceil(CTAs / sms) * (zc + 3).  The chunk counts considered keep every
+// SM busy in the first wave when the volume allows it.
+int model_zc(long long tiles, int nz, int sms) {
+    if (nz <= 4) return std::max(nz, 1);
+    sms = std::max(sms, 1);
+    long long best_cost = -1;
+    int best = 4;
+    const bool can_fill = tiles * ((nz + 3) / 4) >= sms;
+    for (int c = 1; c <= nz; ++c) {
+        const int zc = (nz + c - 1) / c;
+        if (zc < 4) break;
+        if (c > 1 && zc == (nz + c - 2) / (c - 1)) continue;  // same chunk length as c - 1
+        const long long ctas = tiles * c;
+        if (can_fill && ctas < sms) continue;
+        const long long cost = ((ctas + sms - 1) / sms) * (zc + 3);
+        if (best_cost < 0 || cost < best_cost) {
+            best_cost = cost;
+            best = zc;
+        }
+    }
+    return best;
+}
+
+int device_sms() {
+    int dev = 0, sms = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms;
+}
+
+long long zc_tiles(const pfm_problem* pb);
 void dag_bucket(int nl, int nn, int* ml, int* mn) {
     *ml = *mn = 0;
     if (nl <= 8 && nn <= 12) {
@@ -247,6 +282,13 @@ struct pfm_problem {
 };
 
 namespace {
+
+// tiles of one z-chunk row of the grid: 32 x 8 for the Potts kernels and the
+// register-staged ones, 32 x 4 for the TMA DAG kernel
+long long zc_tiles(const pfm_problem* pb) {
+    const int ty = (!pb->flat && pb->prm.schedule == PFM_SCHEDULE_FUSED) ? pfm::DTY : pfm::FTY;
+    return (long long)((pb->nx + pfm::FTX - 1) / pfm::FTX) * ((pb->ny + ty - 1) / ty);
+}
 
 pfm::ProblemView view_of(const pfm_problem* pb) {
     pfm::ProblemView v{};
@@ -486,12 +528,7 @@ static pfm_status create_impl(const pfm_desc* desc, const pfm_params* params, vo
     pb->solver->prepare_tma(pb->u, pb->q, pb->D, pb->S);
     pb->solver->use_tma = params->schedule == PFM_SCHEDULE_FUSED;
     pb->solver->use_tma_inplace = params->schedule == PFM_SCHEDULE_INPLACE;
-    // z-chunk of the fused kernel: aim at >= ~2000 CTAs on large volumes
-    {
-        const long long tiles = (long long)((pb->nx + pfm::FTX - 1) / pfm::FTX) * ((pb->ny + pfm::FTY - 1) / pfm::FTY);
-        long long zc = (tiles * pb->nz) / 2048;
-        pb->zc = (int)std::max<long long>(4, std::min<long long>(64, zc));
-    }
+    pb->zc = model_zc(zc_tiles(pb), pb->nz, device_sms());
     pb->energy_blocks = (int)std::max<long long>(pb->energy_blocks, pb->solver->tma_energy_blocks(pb->zc));
     if ((e = cudaMalloc(&pb->partial, sizeof(double) * 2 * pb->energy_blocks)) != cudaSuccess)
         return bail(cuda_fail(e, "alloc"));
@@ -1187,6 +1224,74 @@ pfm_status pfm_batch_tune(pfm_batch* b, int trial_iters, int* zc_out, int* grid_
 }
 
 int64_t pfm_batch_launch_count(const pfm_batch* b) { return b ? b->launches : -1; }
+
+pfm_status pfm_tune(pfm_problem* pb, int trial_iters, int* zc_out) {
+    if (!pb) return fail(PFM_EINVAL, "NULL problem");
+    if (trial_iters < 1) return fail(PFM_EINVAL, "trial_iters must be >= 1");
+    std::vector<int> cand = {4, 8, 16, 32, 64, 128, model_zc(zc_tiles(pb), pb->nz, device_sms())};
+    for (int& z : cand) z = std::max(1, std::min(z, pb->nz));
+    std::sort(cand.begin(), cand.end());
+    cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
+    cudaEvent_t e0, e1;
+    PFM_CUDA(cudaEventCreate(&e0), "event");
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return fail(PFM_ECUDA, "event");
+    }
+    const int zc0 = pb->zc;
+    float best = 3.0e38f;
+    int best_zc = zc0;
+    pfm_status st = PFM_OK;
+    for (int zc : cand) {
+        pb->zc = zc;
+        if ((st = pfm_iterate(pb, 1)) != PFM_OK) break;  // warm-up
+        cudaEventRecord(e0, pb->stream);
+        if ((st = pfm_iterate(pb, trial_iters)) != PFM_OK) break;
+        cudaEventRecord(e1, pb->stream);
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+            st = fail(PFM_ECUDA, "tune: event sync");
+            break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) {
+            best = ms;
+            best_zc = zc;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    pb->zc = zc0;
+    if (st != PFM_OK) return st;
+    if ((st = pfm_set_chunk_length(pb, best_zc)) != PFM_OK) return st;
+    // the trials advanced the state: start again from the initial one
+    if ((st = pfm_reset(pb)) != PFM_OK) return st;
+    unsigned f = 0;
+    if ((st = read_flags(pb, &f)) != PFM_OK) return st;
+    if ((st = flags_status(f)) != PFM_OK) return st;
+    if (zc_out) *zc_out = pb->zc;
+    return PFM_OK;
+}
+
+pfm_status pfm_set_chunk_length(pfm_problem* pb, int zc) {
+    if (!pb) return fail(PFM_EINVAL, "NULL problem");
+    if (zc < 1) return fail(PFM_EINVAL, "chunk length must be >= 1");
+    zc = std::min(zc, pb->nz);
+    // the TMA energy reduction writes one partial per CTA of the chunking
+    const long long need = pb->solver->tma_energy_blocks(zc);
+    if (need > pb->energy_blocks) {
+        PFM_CUDA(cudaStreamSynchronize(pb->stream), "stream sync");
+        double* part = nullptr;
+        PFM_CUDA(cudaMalloc(&part, sizeof(double) * 2 * need), "alloc");
+        cudaFree(pb->partial);
+        pb->partial = part;
+        pb->energy_blocks = (int)need;
+    }
+    pb->zc = zc;
+    return PFM_OK;
+}
+
+int pfm_chunk_length(const pfm_problem* pb) { return pb ? pb->zc : -1; }
 
 // ---------------------------------------------------------------------------
 // Explicit-flow ("full-flow") augmented-Lagrangian solver (comparison path).

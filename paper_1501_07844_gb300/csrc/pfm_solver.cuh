@@ -14,6 +14,7 @@
 #include "pfm_tma.cuh"
 #include "pfm_tma_dag.cuh"
 #include "pfm_tma_inplace.cuh"
+#include "pfm_tma_x2.cuh"
 
 namespace pfm {
 
@@ -200,6 +201,16 @@ struct Solver final : SolverBase {
     cudaError_t launch_tma3(const StepArgs<MAXL, MAXN>& a, const TmaMaps& m, dim3 grid, double* partial,
                             cudaStream_t s) {
         using Lay = TmaLayout<MAXL, DIM, T>;
+        if constexpr (DIM == 3 && sizeof(T) == 2) {
+            // 3-D, BF16 storage: voxel pairs with packed FP32 arithmetic (the
+            // one-voxel kernel is issue-bound there; with FP32 storage it is
+            // at the bandwidth roof and the pair kernel measured slower)
+            cudaError_t e = cudaFuncSetAttribute(fused_tma_x2_kernel<MAXL, T, EXACT, WITH_E, IDX32>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, Lay::total_bytes);
+            if (e != cudaSuccess) return e;
+            fused_tma_x2_kernel<MAXL, T, EXACT, WITH_E, IDX32><<<grid, X2_NT, Lay::total_bytes, s>>>(a, m, partial);
+            return cudaGetLastError();
+        }
         cudaError_t e = cudaFuncSetAttribute(fused_tma_kernel<MAXL, DIM, T, EXACT, WITH_E, IDX32>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, Lay::total_bytes);
         if (e != cudaSuccess) return e;

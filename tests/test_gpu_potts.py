@@ -385,3 +385,52 @@ def test_argmax_async_equals_argmax():
         gp.argmax_async(out=h2)
         gp.readback_wait()
         assert torch.equal(h1, ref1) and torch.equal(h2, gp.argmax().cpu())
+
+
+@pytest.mark.parametrize("kind", ["fused_f32", "fused_bf16", "inplace", "hmf"])
+def test_chunk_length_leaves_iterates_unchanged(kind):
+    """The z-chunk length (planes per CTA) changes only which CTA runs a
+    plane: the iterates are bit-identical for every length, the energy
+    agrees up to its summation order; lengths beyond the volume clamp."""
+    import paper_1501_07844_gb300 as pfm
+    if kind == "hmf":
+        prob = synth.hmf_problem(seed=2600, shape=(23, 18, 45))
+    else:
+        prob = synth.potts3d_problem(seed=2600, nl=8, shape=(23, 18, 45))
+    sched = pfm.INPLACE if kind == "inplace" else pfm.FUSED
+    storage = pfm.BF16 if kind == "fused_bf16" else pfm.F32
+    res = []
+    for zc in (1, 4, 7, 64):
+        with gpu_problem(prob, schedule=sched, storage=storage) as gp:
+            gp.chunk_length = zc
+            assert gp.chunk_length == min(zc, 23)
+            gp.iterate(6)
+            E, P = gp.iterate_energy(1)
+            res.append((gp.labels().cpu().numpy(), gp.flows().cpu().numpy(), E, P))
+    for u, q, E, P in res[1:]:
+        assert np.array_equal(u, res[0][0]) and np.array_equal(q, res[0][1])
+        # per-thread partials are compensated FP32 sums (about 1e-7 of a
+        # thread's share), combined in FP64
+        assert abs(E - res[0][2]) <= 1e-6 * abs(res[0][2])
+        assert abs(P - res[0][3]) <= 1e-6 * abs(res[0][3]) + 1e-6
+
+
+def test_tune_picks_a_candidate_and_restarts():
+    """pfm_tune keeps one of its candidate lengths, leaves the problem in its
+    initial state, and the solver then matches the oracle."""
+    prob = synth.potts3d_problem(seed=2601, nl=8, shape=(40, 33, 70), iters=30)
+    with gpu_problem(prob) as gp:
+        zc = gp.tune(2)
+        assert zc == gp.chunk_length and 1 <= zc <= 40
+        assert gp.iterations == 0
+        assert np.all(gp.labels().cpu().numpy() == np.float32(1.0 / 8))
+        assert not np.any(gp.flows().cpu().numpy())
+        compare(prob, gp, 30)
+    with gpu_problem(prob) as gp:
+        with pytest.raises(pfm_error()):
+            gp.chunk_length = 0
+
+
+def pfm_error():
+    import paper_1501_07844_gb300 as pfm
+    return pfm.PfmError
