@@ -43,8 +43,7 @@ CONFIGS = {
     "diff": ((128, 128, 128), 6, "potts3d", 0, 0),
     "capacity": ((512, 512, 512), 8, "potts3d", 1, 0),
 }
-KERNEL_SOURCES = [os.path.join(ROOT, "paper_1501_07844_gb300", "csrc", f)
-                  for f in ("pfm_device.cuh", "pfm_tma.cuh", "pfm_tma_x2.cuh")]
+KERNEL_SOURCES = [os.path.join(ROOT, "paper_1501_07844_gb300", "csrc", f) for f in ("pfm_device.cuh", "pfm_tma.cuh")]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic.json")
 
 
