@@ -283,8 +283,9 @@ PFM_API int pfm_chunk_length(const pfm_problem* pb);
  * ADDS this iteration's contribution to Dbar (gradient w.r.t. D) and Sbar
  * (gradient w.r.t. S_field; ignored if the problem has no field).  All
  * buffers are caller-owned FP32 device memory in the getters' layouts;
- * ubar_k may alias ubar_k1 and qbar_k may alias qbar_k1.  work: device
- * scratch of (ndim + 1) * n_leaf * n floats.  D, S, c, tau, the capacities
+ * ubar_k may alias ubar_k1 and qbar_k may alias qbar_k1; Dbar, Sbar and
+ * work overlap no other argument.  work: device scratch of
+ * (ndim + 1) * n_leaf * n floats.  D, S, c, tau, the capacities
  * and the norm are the problem's.  Asynchronous on the problem's stream.
  * PFM_EUNSUPPORTED for DAG problems, PAPER_LITERAL or more than 16 labels. */
 PFM_API pfm_status pfm_adjoint_step(pfm_problem* pb, const float* u_k, const float* q_k, const float* u_k1,

@@ -30,21 +30,24 @@ constexpr int NT = 256;
 
 using AdjArgs = AdjLaunch;
 
-// Slot of voxel i (dense index, row coordinate x) in the problem's pitched
-// D and S arrays.
-__device__ __forceinline__ long long pitched(const AdjArgs& a, long long i, int x) {
-    return (i / a.nx) * a.px + x;
+// Slot of voxel (x, y, z) in the problem's pitched D and S arrays.
+__device__ __forceinline__ long long pitched(const AdjArgs& a, int x, int y, int z) {
+    return ((long long)z * a.ny + y) * a.px + x;
 }
 
 __device__ __forceinline__ void coords(long long i, int nx, int ny, int& x, int& y, int& z) {
-    x = (int)(i % nx);
-    const long long r = i / nx;
-    y = (int)(r % ny);
-    z = (int)(r / ny);
+    split3(i, nx, ny, x, y, z);
 }
 
 // L: compile-time bound on the label count (4, 8 or 16), so the label loops
-// unroll and the per-label values live in registers.
+// unroll and the per-label values live in registers.  In the prox and
+// divergence adjoints every load is unconditional and in bounds (a label
+// past nl reads label nl-1, a neighbour past the grid's last index reads the
+// voxel itself, which makes its forward difference exactly zero), so the
+// loads of all labels issue before the first store; only the stores and
+// accumulations are guarded.  The projection adjoint keeps one thread per
+// voxel and one label's loads at a time: with all of them in flight (one or
+// two threads per voxel) it measured slower.
 template <int L, int DIM>
 __global__ void __launch_bounds__(NT) adj_proj_kernel(const AdjArgs a) {
     const long long i = (long long)blockIdx.x * NT + threadIdx.x;
@@ -52,7 +55,7 @@ __global__ void __launch_bounds__(NT) adj_proj_kernel(const AdjArgs a) {
     int x, y, z;
     coords(i, a.nx, a.ny, x, y, z);
     const long long n = a.n, plane = (long long)a.nx * a.ny;
-    const float sf = a.S ? a.S[pitched(a, i, x)] : 1.0f;
+    const float sf = a.S ? a.S[pitched(a, x, y, z)] : 1.0f;
     float sbar = 0.f;
 #pragma unroll
     for (int j = 0; j < L; ++j) {
@@ -105,66 +108,74 @@ __global__ void __launch_bounds__(NT) adj_proj_kernel(const AdjArgs a) {
 // Two threads per voxel, each owning every other label (j = h, h+2, ...):
 // half the registers per thread and twice the loads in flight per voxel; the
 // per-voxel minimum, <u', ubar'> and the normaliser are combined with one lane
-// shuffle each.
+// shuffle each.  Every operand, the accumulated Dbar included, is read
+// before the first store (ubar_k may alias ubar_k1: each slot is read, then
+// written, by its own thread).
 template <int L, int DIM>
 __global__ void __launch_bounds__(NT) adj_prox_kernel(const AdjArgs a) {
     constexpr int HL = L / 2;
     const long long gt = (long long)blockIdx.x * NT + threadIdx.x;
-    const long long i = gt >> 1;
+    const long long i0 = gt >> 1;
     const int h = (int)(gt & 1);
-    const bool live = i < a.n;  // both lanes of a pair agree; every lane reaches the shuffles
-    int x = 0, y = 0, z = 0;
-    long long pi = 0;
-    if (live) {
-        coords(i, a.nx, a.ny, x, y, z);
-        pi = pitched(a, i, x);
-    }
+    const bool live = i0 < a.n;  // both lanes of a pair agree; every lane reaches the shuffles
+    const long long i = live ? i0 : a.n - 1;
+    int x, y, z;
+    coords(i, a.nx, a.ny, x, y, z);
+    const long long pi = pitched(a, x, y, z);
     const long long n = a.n, plane = (long long)a.nx * a.ny;
-    float d[HL], ub[HL], u1[HL];
+    // backward neighbours (the voxel itself at index 0) and the zero normal
+    // flow at the last index
+    const long long mx = x > 0 ? 1 : 0, my = y > 0 ? a.nx : 0, mz = z > 0 ? plane : 0;
+    const float fx = x < a.nx - 1 ? 1.f : 0.f, fy = y < a.ny - 1 ? 1.f : 0.f, fz = z < a.nz - 1 ? 1.f : 0.f;
+    const float bx = x > 0 ? 1.f : 0.f, by = y > 0 ? 1.f : 0.f, bz = z > 0 ? 1.f : 0.f;
+    float d[HL], ub[HL], u1[HL], uk[HL], db0[HL];
+    bool valid[HL];
     float m = 3.0e38f;
     float dot = 0.f;
 #pragma unroll
     for (int k = 0; k < HL; ++k) {
         const int j = h + 2 * k;
-        d[k] = ub[k] = u1[k] = 0.f;
-        if (!live || j >= a.nl) continue;
+        valid[k] = live && j < a.nl;
+        const int jl = j < a.nl ? j : a.nl - 1;
         // d_j = D_j + div q_j  (forward recomputation)
-        const float* qa = a.q_k + (long long)j * DIM * n + i;
-        float dv = (x < a.nx - 1 ? qa[0] : 0.f) - (x > 0 ? qa[-1] : 0.f);
-        dv += (y < a.ny - 1 ? qa[n] : 0.f) - (y > 0 ? qa[n - a.nx] : 0.f);
-        if constexpr (DIM == 3) dv += (z < a.nz - 1 ? qa[2 * n] : 0.f) - (z > 0 ? qa[2 * n - plane] : 0.f);
-        d[k] = a.D[(long long)j * a.np + pi] + dv;
-        m = fminf(m, d[k]);
+        const float* qa = a.q_k + (long long)jl * DIM * n + i;
+        float dv = fx * qa[0] - bx * qa[-mx];
+        dv += fy * qa[n] - by * qa[n - my];
+        if constexpr (DIM == 3) dv += fz * qa[2 * n] - bz * qa[2 * n - mz];
+        d[k] = a.D[(long long)jl * a.np + pi] + dv;
         // ubar'_j + c tau div ybar_j
-        const float* yb = a.ybar + (long long)j * DIM * n + i;
-        float dy = (x < a.nx - 1 ? yb[0] : 0.f) - (x > 0 ? yb[-1] : 0.f);
-        dy += (y < a.ny - 1 ? yb[n] : 0.f) - (y > 0 ? yb[n - a.nx] : 0.f);
-        if constexpr (DIM == 3) dy += (z < a.nz - 1 ? yb[2 * n] : 0.f) - (z > 0 ? yb[2 * n - plane] : 0.f);
-        ub[k] = a.ubar_k1[(long long)j * n + i] + a.ctau * dy;
-        u1[k] = a.u_k1[(long long)j * n + i];
-        dot += u1[k] * ub[k];
+        const float* yb = a.ybar + (long long)jl * DIM * n + i;
+        float dy = fx * yb[0] - bx * yb[-mx];
+        dy += fy * yb[n] - by * yb[n - my];
+        if constexpr (DIM == 3) dy += fz * yb[2 * n] - bz * yb[2 * n - mz];
+        ub[k] = a.ubar_k1[(long long)jl * n + i] + a.ctau * dy;
+        u1[k] = a.u_k1[(long long)jl * n + i];
+        uk[k] = a.u_k[(long long)jl * n + i];
+        db0[k] = a.Dbar[(long long)jl * n + i];
+        if (valid[k]) {
+            m = fminf(m, d[k]);
+            dot += u1[k] * ub[k];
+        }
     }
     m = fminf(m, __shfl_xor_sync(0xffffffffu, m, 1));
     dot += __shfl_xor_sync(0xffffffffu, dot, 1);
     float asum = 0.f;
 #pragma unroll
     for (int k = 0; k < HL; ++k) {
-        const int j = h + 2 * k;
-        if (!live || j >= a.nl) continue;
         d[k] = __expf(-(d[k] - m) / a.c);  // e_j (shifted)
-        asum += a.u_k[(long long)j * n + i] * d[k];
+        if (valid[k]) asum += uk[k] * d[k];
     }
     asum += __shfl_xor_sync(0xffffffffu, asum, 1);
     const float inv_a = 1.0f / asum;
 #pragma unroll
     for (int k = 0; k < HL; ++k) {
         const int j = h + 2 * k;
-        if (!live || j >= a.nl) continue;
+        if (!valid[k]) continue;
         const float w = ub[k] - dot;
         a.ubar_k[(long long)j * n + i] = d[k] * inv_a * w;
         const float dbar = -u1[k] * w / a.c;
         a.dbar[(long long)j * n + i] = dbar;
-        a.Dbar[(long long)j * n + i] += dbar;
+        a.Dbar[(long long)j * n + i] = db0[k] + dbar;
     }
 }
 
@@ -175,18 +186,29 @@ __global__ void __launch_bounds__(NT) adj_div_kernel(const AdjArgs a) {
     int x, y, z;
     coords(i, a.nx, a.ny, x, y, z);
     const long long n = a.n, plane = (long long)a.nx * a.ny;
+    // dbar and ybar are the work buffer, which qbar_k does not overlap
+    const float* __restrict__ dbar = a.dbar;
+    const float* __restrict__ ybar = a.ybar;
+    float* __restrict__ qbar = a.qbar_k;
+    const long long ox = x < a.nx - 1 ? 1 : 0, oy = y < a.ny - 1 ? a.nx : 0, oz = z < a.nz - 1 ? plane : 0;
+    // all loads first
+    float dl[L][DIM + 1], yl[L][DIM];
 #pragma unroll
     for (int j = 0; j < L; ++j) {
-        if (j >= a.nl) break;
-        const float* db = a.dbar + (long long)j * n + i;
-        const float d0 = *db;
-        float gr[DIM];
-        gr[0] = x < a.nx - 1 ? db[1] - d0 : 0.f;
-        gr[1] = y < a.ny - 1 ? db[a.nx] - d0 : 0.f;
-        if constexpr (DIM == 3) gr[2] = z < a.nz - 1 ? db[plane] - d0 : 0.f;
-        for (int k = 0; k < DIM; ++k) {
-            const long long o = ((long long)j * DIM + k) * n + i;
-            a.qbar_k[o] = a.ybar[o] - gr[k];
+        const int jl = j < a.nl ? j : a.nl - 1;
+        const float* db = dbar + (long long)jl * n + i;
+        dl[j][0] = db[0];
+        dl[j][1] = db[ox];
+        dl[j][2] = db[oy];
+        if constexpr (DIM == 3) dl[j][3] = db[oz];
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) yl[j][k] = ybar[((long long)jl * DIM + k) * n + i];
+    }
+#pragma unroll
+    for (int j = 0; j < L; ++j) {
+        if (j < a.nl) {
+#pragma unroll
+            for (int k = 0; k < DIM; ++k) qbar[((long long)j * DIM + k) * n + i] = yl[j][k] - (dl[j][k + 1] - dl[j][0]);
         }
     }
 }

@@ -37,7 +37,8 @@ template <int MAXL, int DIM>
 __global__ void __launch_bounds__(NT) alm_f_kernel(const AlmArgs a) {
     const long long i = (long long)blockIdx.x * NT + threadIdx.x;
     if (i >= a.n) return;
-    const int x = (int)(i % a.nx), y = (int)((i / a.nx) % a.ny), z = (int)(i / ((long long)a.nx * a.ny));
+    int x, y, z;
+    split3(i, a.nx, a.ny, x, y, z);
     const long long n = a.n, plane = (long long)a.nx * a.ny;
     const float ps = a.pS[i];
 #pragma unroll
@@ -53,7 +54,8 @@ template <int MAXL, int DIM>
 __global__ void __launch_bounds__(NT) alm_q_kernel(const AlmArgs a) {
     const long long i = (long long)blockIdx.x * NT + threadIdx.x;
     if (i >= a.n) return;
-    const int x = (int)(i % a.nx), y = (int)((i / a.nx) % a.ny), z = (int)(i / ((long long)a.nx * a.ny));
+    int x, y, z;
+    split3(i, a.nx, a.ny, x, y, z);
     const long long n = a.n, plane = (long long)a.nx * a.ny;
     const float sf = a.S ? a.S[i] : 1.0f;
 #pragma unroll
@@ -77,7 +79,8 @@ template <int MAXL, int DIM>
 __global__ void __launch_bounds__(NT) alm_p_kernel(const AlmArgs a) {
     const long long i = (long long)blockIdx.x * NT + threadIdx.x;
     if (i >= a.n) return;
-    const int x = (int)(i % a.nx), y = (int)((i / a.nx) % a.ny), z = (int)(i / ((long long)a.nx * a.ny));
+    int x, y, z;
+    split3(i, a.nx, a.ny, x, y, z);
     const long long n = a.n, plane = (long long)a.nx * a.ny;
     const float ps = a.pS[i];
     const float ig = 1.0f / a.gamma;

@@ -71,6 +71,24 @@ template <> __device__ __forceinline__ float ldv<float>(const float* p) { return
 template <> __device__ __forceinline__ float ldv<__nv_bfloat16>(const __nv_bfloat16* p) {
     return __bfloat162float(__ldg(p));
 }
+// (x, y, z) of slot i of a volume with rows of `row` slots (nx, or the pitch
+// px) and ny rows per plane.  32-bit divisions whenever the index fits: the
+// 64-bit division is a long instruction sequence, and a per-element kernel
+// that splits its index twice spends most of its issue slots there.
+__device__ __forceinline__ void split3(long long i, int row, int ny, int& x, int& y, int& z) {
+    if (i <= 0xFFFFFFFFll) {
+        const unsigned u = (unsigned)i, r = u / (unsigned)row, zz = r / (unsigned)ny;
+        x = (int)(u - r * (unsigned)row);
+        y = (int)(r - zz * (unsigned)ny);
+        z = (int)zz;
+    } else {
+        const long long r = i / row, zz = r / ny;
+        x = (int)(i - r * row);
+        y = (int)(r - zz * ny);
+        z = (int)zz;
+    }
+}
+
 template <typename T> __device__ __forceinline__ void stv(T* p, float v);
 template <> __device__ __forceinline__ void stv<float>(float* p, float v) { *p = v; }
 template <> __device__ __forceinline__ void stv<__nv_bfloat16>(__nv_bfloat16* p, float v) {
@@ -349,11 +367,9 @@ prox_inplace_kernel(const StepArgs<MAXL, MAXN> a) {
     const long long n = a.n;
     const long long i = (long long)blockIdx.x * POINT_NT + threadIdx.x;
     if (i >= n) return;
-    const int x = (int)(i % a.px);
+    int x, y, z;
+    split3(i, a.px, a.ny, x, y, z);
     if (x >= a.nx) return;  // row padding
-    const long long r = i / a.px;
-    const int y = (int)(r % a.ny);
-    const int z = (int)(r / a.ny);
     const long long plane = (long long)a.px * a.ny;
     T* u = static_cast<T*>(a.u_out);
     const T* q = static_cast<const T*>(a.q_in);
@@ -390,11 +406,9 @@ flow_inplace_kernel(const StepArgs<MAXL, MAXN> a) {
     const long long n = a.n;
     const long long i = (long long)blockIdx.x * POINT_NT + threadIdx.x;
     if (i >= n) return;
-    const int x = (int)(i % a.px);
+    int x, y, z;
+    split3(i, a.px, a.ny, x, y, z);
     if (x >= a.nx) return;  // row padding
-    const long long r = i / a.px;
-    const int y = (int)(r % a.ny);
-    const int z = (int)(r / a.ny);
     const long long plane = (long long)a.px * a.ny;
     const T* u = static_cast<const T*>(a.u_in);
     T* q = static_cast<T*>(a.q_out);
@@ -480,11 +494,9 @@ energy_partial_kernel(const StepArgs<MAXL, MAXN> a, double* partial) {
     SumF sumE, sumP;
     for (long long i = (long long)blockIdx.x * ENERGY_NT + threadIdx.x; i < n;
          i += (long long)gridDim.x * ENERGY_NT) {
-        const int x = (int)(i % a.px);
+        int x, y, z;
+        split3(i, a.px, a.ny, x, y, z);
         if (x >= a.nx) continue;  // row padding
-        const long long r = i / a.px;
-        const int y = (int)(r % a.ny);
-        const int z = (int)(r / a.ny);
         float uv[MAXL], gr[MAXL][DIM];
         float eData = 0.f;
 #pragma unroll

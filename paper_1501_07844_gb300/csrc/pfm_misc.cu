@@ -12,8 +12,17 @@ constexpr int NT = 256;
 
 inline unsigned blocks_for(long long count) { return (unsigned)((count + NT - 1) / NT); }
 
-// Slot of dense element e (rows of nx values) in an array of rows of pitch px.
-__device__ __forceinline__ long long slot(long long e, int nx, int px) { return (e / nx) * px + e % nx; }
+// Slot of dense element e (rows of nx values) in an array of rows of pitch px
+// (32-bit division whenever e fits; the identity without padding).
+__device__ __forceinline__ long long slot(long long e, int nx, int px) {
+    if (px == nx) return e;
+    if (e <= 0xFFFFFFFFll) {
+        const unsigned u = (unsigned)e, r = u / (unsigned)nx;
+        return (long long)r * px + (u - r * (unsigned)nx);
+    }
+    const long long r = e / nx;
+    return r * px + (e - r * nx);
+}
 
 // u_L = 1/#leaves (Algorithm 1 and Algorithm 2, first line).
 template <typename T>
@@ -80,14 +89,12 @@ __global__ void set_flows_kernel(const float* src, int nn, int ndim, int nx, int
                                  const float* s_node, const float* S, int aniso, T* dst) {
     const long long n = (long long)nx * ny * nz;       // dense voxels of src
     const long long np = (long long)px * ny * nz;      // slots of the pitched S and dst
-    const long long gi = (long long)blockIdx.x * NT + threadIdx.x;
-    if (gi >= (long long)nn * n) return;
-    const int A = (int)(gi / n);
-    const long long i = gi % n;
-    const long long pi = slot(i, nx, px);
-    const int x = (int)(i % nx);
-    const int y = (int)((i / nx) % ny);
-    const int z = (int)(i / ((long long)nx * ny));
+    const long long i = (long long)blockIdx.x * NT + threadIdx.x;  // voxel
+    const int A = blockIdx.y;                                       // node
+    if (i >= n) return;
+    int x, y, z;
+    split3(i, nx, ny, x, y, z);
+    const long long pi = ((long long)z * ny + y) * px + x;
     float yv[3] = {0.f, 0.f, 0.f};
     for (int k = 0; k < ndim; ++k) yv[k] = src[((long long)A * ndim + k) * n + i];
     if (x == nx - 1) yv[0] = 0.f;
@@ -192,7 +199,7 @@ cudaError_t launch_set_labels(const float* src, int storage, int nl, long long n
 
 cudaError_t launch_set_flows(const float* src, int storage, int nn, int ndim, int nx, int ny, int nz, int px,
                              const float* s_node_dev, const float* S, int aniso, void* dst, cudaStream_t s) {
-    const unsigned b = blocks_for((long long)nn * nx * ny * nz);
+    const dim3 b(blocks_for((long long)nx * ny * nz), (unsigned)nn);  // voxels x nodes (nn <= 16)
     PFM_BY_STORAGE(storage,
                    (set_flows_kernel<float><<<b, NT, 0, s>>>(src, nn, ndim, nx, ny, nz, px, s_node_dev, S, aniso,
                                                              (float*)dst)),
