@@ -485,7 +485,7 @@ struct SumF {
 
 
 template <int MAXL, int MAXN, int DIM, bool IS_DAG, typename T>
-__global__ void __launch_bounds__(ENERGY_NT)
+__global__ void __launch_bounds__(ENERGY_NT, 2)
 energy_partial_kernel(const StepArgs<MAXL, MAXN> a, double* partial) {
     const long long n = a.n;
     const long long plane = (long long)a.px * a.ny;
@@ -497,62 +497,67 @@ energy_partial_kernel(const StepArgs<MAXL, MAXN> a, double* partial) {
         int x, y, z;
         split3(i, a.px, a.ny, x, y, z);
         if (x >= a.nx) continue;  // row padding
-        float uv[MAXL], gr[MAXL][DIM];
+        // Every load is unconditional and in bounds (a label or node past the
+        // count reads the last one, a neighbour past the grid's last index
+        // reads the voxel itself, so its forward difference is exactly 0), so
+        // the loads batch; the path weights past the counts are zero.
+        const long long ox = x < a.nx - 1 ? 1 : 0, oy = y < a.ny - 1 ? a.px : 0;
+        const long long oz = (DIM == 3 && z < a.nz - 1) ? plane : 0;
+        const long long mx = x > 0 ? 1 : 0, my = y > 0 ? a.px : 0, mz = (DIM == 3 && z > 0) ? plane : 0;
+        const float fx = x < a.nx - 1 ? 1.f : 0.f, fy = y < a.ny - 1 ? 1.f : 0.f, fz = z < a.nz - 1 ? 1.f : 0.f;
+        const float bx = x > 0 ? 1.f : 0.f, by = y > 0 ? 1.f : 0.f, bz = z > 0 ? 1.f : 0.f;
+        // primal: data term, then the nodes' gradient norms one axis at a
+        // time (the end-labels' differences along one axis, 16 values, are
+        // live at once instead of all three axes)
+        float u0[MAXL];
         float eData = 0.f;
 #pragma unroll
         for (int j = 0; j < MAXL; ++j) {
-            if (j < a.nl) {
-                const T* uj = u + (long long)j * n + i;
-                uv[j] = ldv<T>(uj);
-                eData = fmaf(__ldg(a.D + (long long)j * n + i), uv[j], eData);
-                gr[j][0] = x < a.nx - 1 ? ldv<T>(uj + 1) - uv[j] : 0.f;
-                gr[j][1] = y < a.ny - 1 ? ldv<T>(uj + a.px) - uv[j] : 0.f;
-                if constexpr (DIM == 3) gr[j][2] = z < a.nz - 1 ? ldv<T>(uj + plane) - uv[j] : 0.f;
-            } else {
-                uv[j] = 0.f;
-#pragma unroll
-                for (int k = 0; k < DIM; ++k) gr[j][k] = 0.f;
-            }
+            const int jl = j < a.nl ? j : a.nl - 1;
+            u0[j] = ldv<T>(u + (long long)jl * n + i);
+            if (j < a.nl) eData = fmaf(__ldg(a.D + (long long)jl * n + i), u0[j], eData);
         }
         const float sf = a.S ? __ldg(a.S + i) : 1.0f;
+        float acc[MAXN];  // sum of |g_A,k| (ANISO) or g_A,k^2 (ISO) over the axes so far
+#pragma unroll
+        for (int A = 0; A < MAXN; ++A) acc[A] = 0.f;
+#pragma unroll 1
+        for (int k = 0; k < DIM; ++k) {
+            const long long off = k == 0 ? ox : k == 1 ? oy : oz;
+            float g[MAXL];
+#pragma unroll
+            for (int j = 0; j < MAXL; ++j) {
+                const int jl = j < a.nl ? j : a.nl - 1;
+                g[j] = j < a.nl ? ldv<T>(u + (long long)jl * n + i + off) - u0[j] : 0.f;
+            }
+#pragma unroll
+            for (int A = 0; A < MAXN; ++A) {
+                float gA;
+                if constexpr (IS_DAG) {
+                    gA = 0.f;
+#pragma unroll
+                    for (int j = 0; j < MAXL; ++j) gA = fmaf(a.W[A][j], g[j], gA);
+                } else {
+                    gA = g[A];
+                }
+                acc[A] = a.aniso ? acc[A] + fabsf(gA) : (k == 0 ? gA * gA : fmaf(gA, gA, acc[A]));
+            }
+        }
         float tv = 0.f;
+#pragma unroll
+        for (int A = 0; A < MAXN; ++A)
+            if (A < a.nn) tv = fmaf(a.s_node[A] * sf, a.aniso ? acc[A] : sqrtf(acc[A]), tv);
+        // dual: every node's divergence (zero normal flow at the last index),
+        // then the end-labels' excess d_j and its minimum
         float e[MAXN];
 #pragma unroll
         for (int A = 0; A < MAXN; ++A) {
-            e[A] = 0.f;
-            if (A < a.nn) {
-                float gA[DIM];
-#pragma unroll
-                for (int k = 0; k < DIM; ++k) {
-                    if constexpr (IS_DAG) {
-                        float s = 0.f;
-#pragma unroll
-                        for (int j = 0; j < MAXL; ++j)
-                            if (j < a.nl) s = fmaf(a.W[A][j], gr[j][k], s);
-                        gA[k] = s;
-                    } else {
-                        gA[k] = gr[A][k];
-                    }
-                }
-                float nv;
-                if (a.aniso) {
-                    nv = 0.f;
-#pragma unroll
-                    for (int k = 0; k < DIM; ++k) nv += fabsf(gA[k]);
-                } else {
-                    float r2 = 0.f;
-#pragma unroll
-                    for (int k = 0; k < DIM; ++k) r2 = fmaf(gA[k], gA[k], r2);
-                    nv = sqrtf(r2);
-                }
-                tv = fmaf(a.s_node[A] * sf, nv, tv);
-                const T* qa = q + (long long)A * DIM * n + i;
-                float dv = (x < a.nx - 1 ? ldv<T>(qa) : 0.f) - (x > 0 ? ldv<T>(qa - 1) : 0.f);
-                dv += (y < a.ny - 1 ? ldv<T>(qa + n) : 0.f) - (y > 0 ? ldv<T>(qa + n - a.px) : 0.f);
-                if constexpr (DIM == 3)
-                    dv += (z < a.nz - 1 ? ldv<T>(qa + 2 * n) : 0.f) - (z > 0 ? ldv<T>(qa + 2 * n - plane) : 0.f);
-                e[A] = dv;
-            }
+            const int Al = A < a.nn ? A : a.nn - 1;
+            const T* qa = q + (long long)Al * DIM * n + i;
+            float dv = fx * ldv<T>(qa) - bx * ldv<T>(qa - mx);
+            dv += fy * ldv<T>(qa + n) - by * ldv<T>(qa + n - my);
+            if constexpr (DIM == 3) dv += fz * ldv<T>(qa + 2 * n) - bz * ldv<T>(qa + 2 * n - mz);
+            e[A] = A < a.nn ? dv : 0.f;
         }
         float dmin = 3.0e38f;
 #pragma unroll
@@ -563,8 +568,7 @@ energy_partial_kernel(const StepArgs<MAXL, MAXN> a, double* partial) {
                 if constexpr (IS_DAG) {
                     dj = 0.f;
 #pragma unroll
-                    for (int A = 0; A < MAXN; ++A)
-                        if (A < a.nn) dj = fmaf(a.W[A][j], e[A], dj);
+                    for (int A = 0; A < MAXN; ++A) dj = fmaf(a.W[A][j], e[A], dj);
                     dj += Dj;  // W_(leaf,leaf) = 1 and D sits on the end-label itself
                 } else {
                     dj = e[j] + Dj;
