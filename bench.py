@@ -645,7 +645,8 @@ def main():
     traffic = load_traffic(cfg)
     # 3-D Potts iterations with BF16 storage run the voxel-pair kernel
     kname = {"fused_tma": "fused_tma_x2_kernel" if (len(shape) == 3 and storage == 1) else "fused_tma_kernel",
-             "fused_tma_dag": "fused_dag_tma_kernel", "fused": "fused_step_kernel",
+             "fused_tma_dag": "fused_dag_tma_kernel", "fused_tma_ishikawa": "ishikawa_tma_kernel",
+             "fused": "fused_step_kernel",
              "inplace": "prox_inplace_kernel+flow_inplace_kernel",
              "inplace_tma": "prox_inplace_tma_kernel+flow_inplace_tma_kernel"}.get(gp.variant, gp.variant)
 

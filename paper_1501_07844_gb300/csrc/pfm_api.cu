@@ -283,10 +283,12 @@ struct pfm_problem {
 
 namespace {
 
-// tiles of one z-chunk row of the grid: 32 x 8 for the Potts kernels and the
-// register-staged ones, 32 x 4 for the TMA DAG kernel
+// tiles of one z-chunk row of the grid: 32 x 4 for the TMA DAG kernel,
+// 32 x 8 for every other kernel
 long long zc_tiles(const pfm_problem* pb) {
-    const int ty = (!pb->flat && pb->prm.schedule == PFM_SCHEDULE_FUSED) ? pfm::DTY : pfm::FTY;
+    const int ty = strcmp(pb->solver->variant(pb->prm.schedule != PFM_SCHEDULE_INPLACE), "fused_tma_dag") == 0
+                       ? pfm::DTY
+                       : pfm::FTY;
     return (long long)((pb->nx + pfm::FTX - 1) / pfm::FTX) * ((pb->ny + ty - 1) / ty);
 }
 

@@ -14,6 +14,7 @@
 #include "pfm_tma.cuh"
 #include "pfm_tma_dag.cuh"
 #include "pfm_tma_inplace.cuh"
+#include "pfm_tma_ishikawa.cuh"
 #include "pfm_tma_x2.cuh"
 
 namespace pfm {
@@ -65,6 +66,46 @@ inline bool build_dag_lists(const StepArgs<DMAX, DMAX>& a, int dim, int es, DagL
 
 // Tensor maps of one parity of a DAG problem: logical extents, pitched
 // strides; the flow box covers the nf flow-carrying nodes.
+// The flow-carrying nodes 0..nf-1 are the N = nl - 1 levels of an Ishikawa
+// model (node k-1 is level k): every path weight W_(node k-1, L_j) is 1 for
+// j >= k and 0 below (Algorithm 3's cumulative excess and accumulation),
+// with at most 8 labels.
+template <int MAXL, int MAXN>
+inline bool is_ishikawa_chain(const StepArgs<MAXL, MAXN>& a) {
+    int nf = 0;
+    for (int A = 0; A < a.nn; ++A)
+        if (a.s_node[A] > 0.f) nf = A + 1;
+    if (a.nl < 2 || a.nl > ISH_MAXL || nf != a.nl - 1) return false;
+    for (int A = 0; A < nf; ++A)
+        for (int j = 0; j < a.nl; ++j)
+            if (a.W[A][j] != (j > A ? 1.0f : 0.0f)) return false;
+    return true;
+}
+
+// Maps of the Ishikawa kernel: the Potts kernel's boxes (32 x 8 tiles) over
+// the nl labels and the flows of the nl - 1 levels (nodes 0..nl-2).
+template <int MAXL, int MAXN>
+inline bool encode_ishikawa_maps(const StepArgs<MAXL, MAXN>& a, int es, const void* u, const void* q,
+                                 const float* D, const float* S, TmaMaps* m) {
+    constexpr int DIM = 3;
+    const int qbx = FTX + 2 * (16 / es);
+    const unsigned long long nx = a.nx, ny = a.ny, nz = a.nz, px = a.px;
+    const unsigned long long dims_u[4] = {nx, ny, nz, (unsigned long long)a.nl};
+    const unsigned long long dims_q[4] = {nx, ny, nz, (unsigned long long)DIM * a.nn};
+    const unsigned long long st_t[3] = {px * es, px * ny * es, px * ny * nz * es};
+    const unsigned long long st_f[3] = {px * 4, px * ny * 4, px * ny * nz * 4};
+    const unsigned box_u[4] = {(unsigned)TMA_BX, (unsigned)TMA_UY, 1u, (unsigned)a.nl};
+    const unsigned box_q[4] = {(unsigned)qbx, (unsigned)TMA_QY, 1u, (unsigned)(DIM * (a.nl - 1))};
+    const unsigned long long dims_s[3] = {nx, ny, nz};
+    const unsigned box_s[3] = {(unsigned)FTX, (unsigned)FTY, 1u};
+    if (!encode_tiled_map(&m->u, u, es, 4, dims_u, st_t, box_u)) return false;
+    if (!encode_tiled_map(&m->q, q, es, 4, dims_q, st_t, box_q)) return false;
+    if (!encode_tiled_map(&m->D, D, 4, 4, dims_u, st_f, box_u)) return false;
+    if (S) return encode_tiled_map(&m->S, S, 4, 3, dims_s, st_f, box_s);
+    m->S = m->D;  // never read: the kernel skips S when the problem has no field
+    return true;
+}
+
 inline bool encode_dag_maps(const StepArgs<DMAX, DMAX>& a, int dim, int es, int nf, const void* u, const void* q,
                             const float* D, const float* S, TmaMaps* m) {
     const int qbx = FTX + 2 * (16 / es);
@@ -152,6 +193,8 @@ struct Solver final : SolverBase {
     TmaMaps tma_maps[2];
     bool dag_tma_ready = false;
     DagLists lists{};
+    bool ishi_ready = false;  // the DAG is an Ishikawa chain: chain-specialised kernel
+    TmaMaps ishi_maps[2];
     bool inplace_ready = false;
     InplaceMaps inplace_maps{};
 
@@ -178,6 +221,20 @@ struct Solver final : SolverBase {
             e = cudaGetLastError();
             if (e != cudaSuccess) return e;
             flow_inplace_tma_kernel<MAXL, DIM, T, EXACT, IDX32><<<grid, INPLACE_TMA_NT, L::f_total, s>>>(a, inplace_maps);
+            return cudaGetLastError();
+        } else {
+            return cudaErrorInvalidValue;
+        }
+    }
+
+    template <bool IDX32>
+    cudaError_t launch_ishikawa(const StepArgs<MAXL, MAXN>& a, const TmaMaps& m, dim3 grid, cudaStream_t s) {
+        if constexpr (IS_DAG && DIM == 3) {
+            using Lay = TmaLayout<ISH_MAXL, 3, T>;
+            cudaError_t e = cudaFuncSetAttribute(ishikawa_tma_kernel<MAXL, MAXN, T, IDX32>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, Lay::total_bytes);
+            if (e != cudaSuccess) return e;
+            ishikawa_tma_kernel<MAXL, MAXN, T, IDX32><<<grid, TMA_NT, Lay::total_bytes, s>>>(a, m);
             return cudaGetLastError();
         } else {
             return cudaErrorInvalidValue;
@@ -253,6 +310,16 @@ struct Solver final : SolverBase {
                 return e;
             }
         }
+        if constexpr (IS_DAG && DIM == 3) {
+            if (fused && ishi_ready && use_tma) {
+                const int k = (u_in == tma_u[0]) ? 0 : 1;
+                a.zc = zc < 1 ? 1 : zc;
+                dim3 grid((a.nx + FTX - 1) / FTX, (a.ny + FTY - 1) / FTY, (a.nz + a.zc - 1) / a.zc);
+                *launches = 1;
+                return (long long)DIM * a.nn * a.n <= 0xFFFFFFFFll ? launch_ishikawa<true>(a, ishi_maps[k], grid, s)
+                                                                   : launch_ishikawa<false>(a, ishi_maps[k], grid, s);
+            }
+        }
         if constexpr (kDagTmaCapable) {
             if (fused && dag_tma_ready && use_tma) {
                 const int k = (u_in == tma_u[0]) ? 0 : 1;
@@ -297,6 +364,21 @@ struct Solver final : SolverBase {
         return cudaGetLastError();
     }
 
+    // Maps of the chain-specialised Ishikawa kernel when the DAG is an
+    // Ishikawa chain (3-D, any DAG bucket).
+    void prepare_ishikawa(void* const* u, void* const* q, const float* D, const float* S) {
+        if constexpr (IS_DAG && DIM == 3) {
+            if (!is_ishikawa_chain(base)) return;
+            const int es = (int)sizeof(T);
+            bool ok = true;
+            for (int k = 0; k < 2 && ok; ++k) {
+                ok = encode_ishikawa_maps(base, es, u[k], q[k], D, S, &ishi_maps[k]);
+                tma_u[k] = u[k];
+            }
+            ishi_ready = ok;
+        }
+    }
+
     bool prepare_tma(void* const* u, void* const* q, const float* D, const float* S) override {
         if constexpr (kDagTmaCapable) {
             const int es = (int)sizeof(T);
@@ -307,8 +389,10 @@ struct Solver final : SolverBase {
                 tma_u[k] = u[k];
             }
             dag_tma_ready = true;
+            prepare_ishikawa(u, q, D, S);
             return false;  // the energy reduction keeps its own (non-TMA) kernel
         } else if constexpr (!kTmaCapable) {
+            prepare_ishikawa(u, q, D, S);
             return false;
         } else {
             using Lay = TmaLayout<MAXL, DIM, T>;
@@ -364,6 +448,7 @@ struct Solver final : SolverBase {
     const char* variant(bool fused) const override {
         if (!fused) return inplace_tma() ? "inplace_tma" : "inplace";
         if (kTmaCapable && tma_ready && use_tma) return "fused_tma";
+        if (IS_DAG && ishi_ready && use_tma) return "fused_tma_ishikawa";
         if (kDagTmaCapable && dag_tma_ready && use_tma) return "fused_tma_dag";
         return "fused";
     }

@@ -123,7 +123,9 @@ def test_tma_dag_batch_mixed_layouts_and_ishikawa():
     """One TMA batch holding members with different shared-memory layouts
     (HMF: 12 end-labels / 15 nodes; DAGMF: 10 / 14; an Ishikawa chain whose
     end-labels carry no flow) and odd widths: every member equals its
-    single-problem run bit for bit, and the chain's end-label flows stay 0."""
+    single-problem run bit for bit -- the chain to FP32 rounding, since alone
+    it runs the chain-specialised kernel (prefix / suffix sums instead of
+    path-weight lists) -- and the chain's end-label flows stay 0."""
     import paper_1501_07844_gb300 as pfm
     vols = [synth.hmf_problem(seed=4970, shape=(17, 23, 29), iters=20),
             synth.dagmf_problem(4971, (21, 19, 35), iters=20),
@@ -133,9 +135,14 @@ def test_tma_dag_batch_mixed_layouts_and_ishikawa():
         b.iterate(26)
         for k, p in enumerate(vols):
             with gpu_problem(p) as single:
-                assert single.variant == "fused_tma_dag"
                 single.iterate(26)
-                assert np.array_equal(b.members[k].labels().cpu().numpy(), single.labels().cpu().numpy())
-                assert np.array_equal(b.members[k].flows().cpu().numpy(), single.flows().cpu().numpy())
+                ub, us = b.members[k].labels().cpu().numpy(), single.labels().cpu().numpy()
+                qb, qs = b.members[k].flows().cpu().numpy(), single.flows().cpu().numpy()
+                if k == 2:
+                    assert single.variant == "fused_tma_ishikawa"
+                    assert np.abs(ub - us).max() <= 1e-5 and np.abs(qb - qs).max() <= 1e-5
+                else:
+                    assert single.variant == "fused_tma_dag"
+                    assert np.array_equal(ub, us) and np.array_equal(qb, qs)
         q = b.members[2].flows().cpu().numpy()
         assert np.all(q[7:] == 0)
