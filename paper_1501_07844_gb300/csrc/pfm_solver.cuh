@@ -227,14 +227,15 @@ struct Solver final : SolverBase {
         }
     }
 
-    template <bool IDX32>
-    cudaError_t launch_ishikawa(const StepArgs<MAXL, MAXN>& a, const TmaMaps& m, dim3 grid, cudaStream_t s) {
+    template <bool WITH_E, bool IDX32>
+    cudaError_t launch_ishikawa(const StepArgs<MAXL, MAXN>& a, const TmaMaps& m, dim3 grid, double* partial,
+                                cudaStream_t s) {
         if constexpr (IS_DAG && DIM == 3) {
             using Lay = TmaLayout<ISH_MAXL, 3, T>;
-            cudaError_t e = cudaFuncSetAttribute(ishikawa_tma_kernel<MAXL, MAXN, T, IDX32>,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, Lay::total_bytes);
+            auto kern = ishikawa_tma_kernel<MAXL, MAXN, T, WITH_E, IDX32>;
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Lay::total_bytes);
             if (e != cudaSuccess) return e;
-            ishikawa_tma_kernel<MAXL, MAXN, T, IDX32><<<grid, TMA_NT, Lay::total_bytes, s>>>(a, m);
+            kern<<<grid, TMA_NT, Lay::total_bytes, s>>>(a, m, partial);
             return cudaGetLastError();
         } else {
             return cudaErrorInvalidValue;
@@ -316,8 +317,14 @@ struct Solver final : SolverBase {
                 a.zc = zc < 1 ? 1 : zc;
                 dim3 grid((a.nx + FTX - 1) / FTX, (a.ny + FTY - 1) / FTY, (a.nz + a.zc - 1) / a.zc);
                 *launches = 1;
-                return (long long)DIM * a.nn * a.n <= 0xFFFFFFFFll ? launch_ishikawa<true>(a, ishi_maps[k], grid, s)
-                                                                   : launch_ishikawa<false>(a, ishi_maps[k], grid, s);
+                const bool idx32 = (long long)DIM * a.nn * a.n <= 0xFFFFFFFFll;
+                if (partial) {
+                    if (nblocks) *nblocks = (int)(grid.x * grid.y * grid.z);
+                    return idx32 ? launch_ishikawa<true, true>(a, ishi_maps[k], grid, partial, s)
+                                 : launch_ishikawa<true, false>(a, ishi_maps[k], grid, partial, s);
+                }
+                return idx32 ? launch_ishikawa<false, true>(a, ishi_maps[k], grid, nullptr, s)
+                             : launch_ishikawa<false, false>(a, ishi_maps[k], grid, nullptr, s);
             }
         }
         if constexpr (kDagTmaCapable) {
@@ -438,7 +445,9 @@ struct Solver final : SolverBase {
         }
     }
 
-    bool fuses_energy(bool fused) const override { return fused && kTmaCapable && tma_ready && use_tma; }
+    bool fuses_energy(bool fused) const override {
+        return fused && use_tma && ((kTmaCapable && tma_ready) || (IS_DAG && ishi_ready));
+    }
 
     void set_step(float c, float tau) override {
         base.inv_c = 1.0f / c;
@@ -454,7 +463,9 @@ struct Solver final : SolverBase {
     }
 
     long long tma_energy_blocks(int zc) const override {
-        if (!(kTmaCapable && tma_ready)) return 0;
+        // one partial per CTA of the TMA energy kernel or of an iteration
+        // that reduces its input (Potts and Ishikawa kernels: 32 x 8 tiles)
+        if (!((kTmaCapable && tma_ready) || (IS_DAG && ishi_ready))) return 0;
         zc = zc < 1 ? 1 : zc;
         return (long long)((base.nx + FTX - 1) / FTX) * ((base.ny + FTY - 1) / FTY) * ((base.nz + zc - 1) / zc);
     }

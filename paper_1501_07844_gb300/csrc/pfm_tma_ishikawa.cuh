@@ -27,14 +27,21 @@ namespace pfm {
 
 constexpr int ISH_MAXL = 8;  // labels (N + 1 <= 8, N <= 7 levels)
 
-template <int MAXL, int MAXN, typename T, bool IDX32>
+// WITH_E: also reduce E(u) and P(q) of the input state into one (E, P)
+// partial per CTA: P of plane p from the prox's per-voxel minimum; E of
+// plane p-1 in the flow phase, the data term and, per level, S_k |grad g_k|
+// of the input labelling's accumulated g_k = u_{L_k} + ... + u_{L_N} (the
+// labels carry no capacity), its z-difference from plane p's staged u.  The
+// update itself is the same arithmetic.
+template <int MAXL, int MAXN, typename T, bool WITH_E, bool IDX32>
 __global__ void __launch_bounds__(TMA_NT, 1)
-ishikawa_tma_kernel(const StepArgs<MAXL, MAXN> a, const __grid_constant__ TmaMaps maps) {
+ishikawa_tma_kernel(const StepArgs<MAXL, MAXN> a, const __grid_constant__ TmaMaps maps, double* partial) {
     constexpr int DIM = 3;
     constexpr int HL = ISH_MAXL / 2;
     using Lay = TmaLayout<ISH_MAXL, DIM, T>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ int s_abort;
+    __shared__ double sE[TMA_NT / 32], sP[TMA_NT / 32];
     unsigned char* smem = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
     const int t = threadIdx.x;
     const int h = t & 1;
@@ -125,6 +132,12 @@ ishikawa_tma_kernel(const StepArgs<MAXL, MAXN> a, const __grid_constant__ TmaMap
         if (t == 0) atomicOr(a.flags, FLAG_TIMEOUT);
         s_abort = 1;
     }
+    // WITH_E: the input's accumulated g of each level at this voxel and the
+    // x / y part of its gradient norm, carried to the next plane
+    float ginp[HL], txy_prev[HL];
+#pragma unroll
+    for (int i = 0; i < HL; ++i) ginp[i] = txy_prev[i] = 0.f;
+    SumF sumE, sumP;
     bool bad = false;
     int p_stop = z0 - 1;
     for (int p = z0; p <= z1 && !s_abort; ++p) {
@@ -140,10 +153,11 @@ ishikawa_tma_kernel(const StepArgs<MAXL, MAXN> a, const __grid_constant__ TmaMap
         ok = true;
         if (p < a.nz) ok = mbar_wait_bounded(bar0 + 8 * cs, (unsigned)((s / 3) & 1));
         if (!ok) atomicOr(a.flags, FLAG_TIMEOUT);
-        float qxc[HL], qyc[HL], qzc[HL];
+        float qxc[HL], qyc[HL], qzc[HL], gin[HL], txy[HL];
 #pragma unroll
-        for (int i = 0; i < HL; ++i) qxc[i] = qyc[i] = qzc[i] = 0.f;
+        for (int i = 0; i < HL; ++i) qxc[i] = qyc[i] = qzc[i] = gin[i] = txy[i] = 0.f;
         float scur = 1.0f;
+        float eD = 0.f;  // sum of D u over this thread's labels of plane p (WITH_E)
 
         // ---- label prox of plane p on the halo-extended tile
         if (p < a.nz) {
@@ -184,6 +198,43 @@ ishikawa_tma_kernel(const StepArgs<MAXL, MAXN> a, const __grid_constant__ TmaMap
                 }
             }
             const float dmin = fminf(mloc, __shfl_xor_sync(0xffffffffu, mloc, 1));
+            if constexpr (WITH_E) {
+                if (ownerE && p < z1 && h == 0) sumP.add(dmin);
+                // input labelling: running suffix sums at x, x+1, y+1 of this
+                // half, the lower half adding the upper half's totals
+                float f0[HL], f1[HL], f2[HL];
+                float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+#pragma unroll
+                for (int i = HL - 1; i >= 0; --i) {
+                    const int j = HL * h + i;
+                    if (validE && j < nl) {
+                        const T* uj = uS + j * ustride + ui;
+                        s0 += u[i];
+                        if (ownerE) {
+                            s1 += lds<T>(uj + 1);
+                            s2 += lds<T>(uj + TMA_BX);
+                            if (p < z1) eD = fmaf(dS[j * ustride + ui], u[i], eD);
+                        }
+                    }
+                    f0[i] = s0;
+                    f1[i] = s1;
+                    f2[i] = s2;
+                }
+                const float t0 = __shfl_xor_sync(0xffffffffu, s0, 1);
+                const float t1 = __shfl_xor_sync(0xffffffffu, s1, 1);
+                const float t2 = __shfl_xor_sync(0xffffffffu, s2, 1);
+                const float c0 = h == 0 ? t0 : 0.f, c1 = h == 0 ? t1 : 0.f, c2 = h == 0 ? t2 : 0.f;
+#pragma unroll
+                for (int i = 0; i < HL; ++i) {
+                    const int j = HL * h + i;
+                    if (j >= 1 && j <= nlev) {
+                        gin[i] = f0[i] + c0;
+                        const float gx = cx != 0.f ? (f1[i] + c1) - gin[i] : 0.f;
+                        const float gy = cy != 0.f ? (f2[i] + c2) - gin[i] : 0.f;
+                        txy[i] = a.aniso ? fabsf(gx) + fabsf(gy) : fmaf(gx, gx, gy * gy);
+                    }
+                }
+            }
             const float m = a.literal ? 0.f : dmin;
             float sloc = 0.f;
 #pragma unroll
@@ -235,10 +286,17 @@ ishikawa_tma_kernel(const StepArgs<MAXL, MAXN> a, const __grid_constant__ TmaMap
         if (pm >= z0 && ownerE) {
             const float sf = sprev;
             const float cz = pm < a.nz - 1 ? a.ctau : 0.f;
+            float eloc = 0.f;
 #pragma unroll
             for (int i = 0; i < HL; ++i) {
                 const int j = HL * h + i;
                 if (j >= 1 && j <= nlev) {
+                    if constexpr (WITH_E) {
+                        // TV of level j on the input labelling, plane p-1
+                        const float gz = cz != 0.f ? gin[i] - ginp[i] : 0.f;
+                        const float nv = a.aniso ? txy_prev[i] + fabsf(gz) : sqrtf(fmaf(gz, gz, txy_prev[i]));
+                        eloc = fmaf(cap[i] * sf, nv, eloc);
+                    }
                     const float* gj = gP + j * ustride;
                     const float g0 = gprev[i];
                     float yv[DIM];
@@ -251,13 +309,17 @@ ishikawa_tma_kernel(const StepArgs<MAXL, MAXN> a, const __grid_constant__ TmaMap
                         stv<T>(slot_ptr<IDX32>(qout, (j - 1) * DIM + k, pm, n, plane, vox), yv[k]);
                 }
             }
+            if constexpr (WITH_E) sumE.add(eloc);
         }
+        if constexpr (WITH_E) sumE.add(eD);
 #pragma unroll
         for (int i = 0; i < HL; ++i) {
             gprev[i] = gcur[i];
             qxp[i] = qxc[i];
             qyp[i] = qyc[i];
             qzp[i] = qzc[i];
+            ginp[i] = gin[i];
+            txy_prev[i] = txy[i];
         }
         sprev = scur;
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -272,6 +334,29 @@ ishikawa_tma_kernel(const StepArgs<MAXL, MAXN> a, const __grid_constant__ TmaMap
         for (int p = p_stop; p <= inflight_hi; ++p) {
             const int s = p - z0 + 1;
             mbar_wait_bounded(bar0 + 8 * (s % 3), (unsigned)((s / 3) & 1));
+        }
+    }
+    if constexpr (WITH_E) {
+        double accE = sumE.value(), accP = sumP.value();
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            accE += __shfl_down_sync(0xffffffffu, accE, off);
+            accP += __shfl_down_sync(0xffffffffu, accP, off);
+        }
+        if ((t & 31) == 0) {
+            sE[t >> 5] = accE;
+            sP[t >> 5] = accP;
+        }
+        __syncthreads();
+        if (t == 0) {
+            double E = 0.0, P = 0.0;
+            for (int k = 0; k < TMA_NT / 32; ++k) {
+                E += sE[k];
+                P += sP[k];
+            }
+            const long long b = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+            partial[2 * b] = E;
+            partial[2 * b + 1] = P;
         }
     }
 }

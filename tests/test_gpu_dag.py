@@ -169,13 +169,16 @@ def test_ishikawa_kernel_modes(mode, norm):
     assert np.abs(q[:nlev] - q3).max() <= tol
 
 
-def test_ishikawa_kernel_bf16_and_energy():
+@pytest.mark.parametrize("norm", [0, 1], ids=["iso", "aniso"])
+def test_ishikawa_kernel_bf16_and_energy(norm):
     """BF16 storage on the chain-specialised kernel agrees with FP32 storage
-    to BF16 resolution; iterate_energy returns the energy of the state the
-    last iteration started from and leaves the plain iterations' state."""
+    to BF16 resolution; iterate_energy (E and P reduced inside the last
+    iteration) returns the energy of the state that iteration started from,
+    equal to the separate reduction, and leaves the plain iterations' state."""
     import paper_1501_07844_gb300 as pfm
     prob = ishikawa_with_field(5900, (24, 35, 48), 7)
-    with gpu_problem(prob) as a, gpu_problem(prob) as b, gpu_problem(prob, storage=pfm.BF16) as c:
+    with gpu_problem(prob, norm=norm) as a, gpu_problem(prob, norm=norm) as b, \
+            gpu_problem(prob, norm=norm, storage=pfm.BF16) as c:
         assert c.variant == "fused_tma_ishikawa"
         a.iterate(14)
         E_ref, P_ref = a.energy()
