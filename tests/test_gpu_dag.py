@@ -3,7 +3,7 @@ import numpy as np
 import pytest
 
 import synth
-from helpers import compare, gpu_problem
+from helpers import TOL_E, compare, gpu_problem, oracle_run
 
 pytestmark = pytest.mark.gpu
 
@@ -189,3 +189,30 @@ def test_ishikawa_kernel_bf16_and_energy(norm):
         assert np.array_equal(a.flows().cpu().numpy(), b.flows().cpu().numpy())
         c.iterate(15)
         assert np.abs(c.labels().cpu().numpy() - a.labels().cpu().numpy()).max() <= 3e-2
+
+
+@pytest.mark.parametrize("kind", ["hmf", "dagmf"])
+@pytest.mark.parametrize("storage", [0, 1], ids=["f32", "bf16"])
+@pytest.mark.parametrize("norm", [0, 1], ids=["iso", "aniso"])
+def test_dag_iterate_energy(kind, storage, norm):
+    """pfm_iterate_energy on the TMA DAG path (the per-voxel reduction of the
+    input queued ahead of the last iteration) returns the energy of the
+    state after n-1 iterations, equal to pfm_energy of that state and, in
+    FP32, to the oracle's energy; the state after the call equals the plain
+    iterations' bit for bit."""
+    prob = synth.hmf_problem(seed=3500, shape=(21, 26, 47), iters=12) if kind == "hmf" else \
+        synth.dagmf_problem(4500, (19, 30, 41), iters=12)
+    with gpu_problem(prob, storage=storage, norm=norm) as a, gpu_problem(prob, storage=storage, norm=norm) as b:
+        assert a.variant == "fused_tma_dag"
+        a.chunk_length = 8
+        b.chunk_length = 8
+        a.iterate(11)
+        E_ref, P_ref = a.energy()
+        a.iterate(1)
+        E, P = b.iterate_energy(12)
+        assert abs(E - E_ref) <= 1e-6 * abs(E_ref) and abs(P - P_ref) <= 1e-6 * abs(P_ref) + 1e-6
+        assert np.array_equal(a.labels().cpu().numpy(), b.labels().cpu().numpy())
+        assert np.array_equal(a.flows().cpu().numpy(), b.flows().cpu().numpy())
+    if storage == 0:
+        _, _, E_o, P_o = oracle_run(prob, 11, norm=norm)
+        assert abs(E - E_o) <= TOL_E * abs(E_o) and abs(P - P_o) <= TOL_E * abs(P_o) + 1e-6
