@@ -110,3 +110,20 @@ def test_create_validates_before_device_work(pfm):
     with pytest.raises(pfm.PfmError) as ei:
         pfm.Problem(D, n_nodes=2, edges=[(-1, 0, 1.0), (0, 1, 1.0), (1, 0, 1.0)])
     assert ei.value.name == "PFM_EDAG"
+
+
+def test_null_handles_rejected_on_host(pfm):
+    """Entry points on a NULL problem or batch return PFM_EINVAL (or -1 for
+    the counters) without touching the device."""
+    import ctypes as C
+    L = pfm.lib()
+    zc = C.c_int(-7)
+    assert L.pfm_tune(None, 3, C.byref(zc)) == 1 and zc.value == -7
+    assert L.pfm_set_chunk_length(None, 8) == 1
+    assert L.pfm_chunk_length(None) == -1
+    assert L.pfm_iterate(None, 1) == 1
+    assert L.pfm_iterations_done(None) == -1 and L.pfm_launch_count(None) == -1
+    assert L.pfm_batch_launch_count(None) == -1
+    E, P = C.c_double(), C.c_double()
+    assert L.pfm_energy(None, C.byref(E), C.byref(P)) == 1
+    assert b"NULL" in L.pfm_last_error()
