@@ -84,8 +84,8 @@ __global__ void set_labels_kernel(const float* src, int nl, long long nv, int nx
 
 // Checkpoint import of flows: zero normal flux at the last index of each
 // axis, then projection onto the capacity set.
-template <typename T>
-__global__ void set_flows_kernel(const float* src, int nn, int ndim, int nx, int ny, int nz, int px,
+template <typename T, int DIM>
+__global__ void set_flows_kernel(const float* src, int nn, int nx, int ny, int nz, int px,
                                  const float* s_node, const float* S, int aniso, T* dst) {
     const long long n = (long long)nx * ny * nz;       // dense voxels of src
     const long long np = (long long)px * ny * nz;      // slots of the pitched S and dst
@@ -95,27 +95,34 @@ __global__ void set_flows_kernel(const float* src, int nn, int ndim, int nx, int
     int x, y, z;
     split3(i, nx, ny, x, y, z);
     const long long pi = ((long long)z * ny + y) * px + x;
-    float yv[3] = {0.f, 0.f, 0.f};
-    for (int k = 0; k < ndim; ++k) yv[k] = src[((long long)A * ndim + k) * n + i];
+    float yv[DIM];
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) yv[k] = src[((long long)A * DIM + k) * n + i];
     if (x == nx - 1) yv[0] = 0.f;
     if (y == ny - 1) yv[1] = 0.f;
-    if (ndim == 3 && z == nz - 1) yv[2] = 0.f;
+    if constexpr (DIM == 3) {
+        if (z == nz - 1) yv[2] = 0.f;
+    }
     const float s = s_node[A] * (S ? S[pi] : 1.0f);
     if (aniso) {
-        for (int k = 0; k < ndim; ++k) yv[k] = fminf(fmaxf(yv[k], -s), s);
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) yv[k] = fminf(fmaxf(yv[k], -s), s);
     } else {
         // a flow that is feasible up to the rounding of the storage type (e.g.
         // read back from a solver) is kept bit for bit; anything outside is
         // scaled onto the ball
         const float slack = sizeof(T) == 4 ? 1.000001f : 1.02f;
         float r2 = 0.f;
-        for (int k = 0; k < ndim; ++k) r2 = fmaf(yv[k], yv[k], r2);
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) r2 = fmaf(yv[k], yv[k], r2);
         if (r2 > s * s * slack || s <= 0.f) {
             const float f = s > 0.f ? s * rsqrtf(r2) : 0.f;
-            for (int k = 0; k < ndim; ++k) yv[k] *= f;
+#pragma unroll
+            for (int k = 0; k < DIM; ++k) yv[k] *= f;
         }
     }
-    for (int k = 0; k < ndim; ++k) stv<T>(dst + ((long long)A * ndim + k) * np + pi, yv[k]);
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) stv<T>(dst + ((long long)A * DIM + k) * np + pi, yv[k]);
 }
 
 __global__ void validate_kernel(const float* D, long long nD, const float* S, long long nS, unsigned* flags) {
@@ -201,10 +208,14 @@ cudaError_t launch_set_flows(const float* src, int storage, int nn, int ndim, in
                              const float* s_node_dev, const float* S, int aniso, void* dst, cudaStream_t s) {
     const dim3 b(blocks_for((long long)nx * ny * nz), (unsigned)nn);  // voxels x nodes (nn <= 16)
     PFM_BY_STORAGE(storage,
-                   (set_flows_kernel<float><<<b, NT, 0, s>>>(src, nn, ndim, nx, ny, nz, px, s_node_dev, S, aniso,
-                                                             (float*)dst)),
-                   (set_flows_kernel<__nv_bfloat16><<<b, NT, 0, s>>>(src, nn, ndim, nx, ny, nz, px, s_node_dev, S,
-                                                                     aniso, (__nv_bfloat16*)dst)));
+                   (ndim == 3 ? set_flows_kernel<float, 3><<<b, NT, 0, s>>>(src, nn, nx, ny, nz, px, s_node_dev, S,
+                                                                           aniso, (float*)dst)
+                              : set_flows_kernel<float, 2><<<b, NT, 0, s>>>(src, nn, nx, ny, nz, px, s_node_dev, S,
+                                                                           aniso, (float*)dst)),
+                   (ndim == 3 ? set_flows_kernel<__nv_bfloat16, 3><<<b, NT, 0, s>>>(src, nn, nx, ny, nz, px, s_node_dev,
+                                                                                   S, aniso, (__nv_bfloat16*)dst)
+                              : set_flows_kernel<__nv_bfloat16, 2><<<b, NT, 0, s>>>(src, nn, nx, ny, nz, px, s_node_dev,
+                                                                                   S, aniso, (__nv_bfloat16*)dst)));
     return cudaGetLastError();
 }
 
