@@ -64,7 +64,7 @@ typedef enum {
     PFM_ENONFINITE = 5,     /* NaN or Inf in inputs, energy or dual */
     PFM_ETIMEOUT = 6,       /* a bounded device-side wait expired */
     PFM_ENOTCONVERGED = 7,  /* gap target not met within max_iters */
-    PFM_EUNSUPPORTED = 8    /* valid request this build does not implement */
+    PFM_EUNSUPPORTED = 8    /* valid request the library does not implement */
 } pfm_status;
 
 enum { PFM_NORM_ISO = 0, PFM_NORM_ANISO = 1 };
