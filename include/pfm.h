@@ -292,6 +292,22 @@ PFM_API pfm_status pfm_adjoint_step(pfm_problem* pb, const float* u_k, const flo
                                     const float* ubar_k1, const float* qbar_k1, float* ubar_k, float* qbar_k,
                                     float* Dbar, float* Sbar, float* work);
 
+/* The reverse-mode steps of n_steps consecutive iterations in one call (a
+ * checkpoint segment): u_states is a host array of n_steps + 1 device
+ * pointers (the labelling entering iteration 0, ..., leaving the last) and
+ * q_states one of n_steps (the flows entering each iteration).  On entry
+ * ubar / qbar hold the adjoints of the last iteration's outputs; on return
+ * those of iteration 0's inputs.  Dbar and Sbar accumulate as with
+ * pfm_adjoint_step, work as there.  Equal, bit for bit, to applying
+ * pfm_adjoint_step to the iterations from the last to the first; the
+ * divergence adjoint of each iteration and the projection adjoint of the one
+ * before it share a pass, so the flow adjoints between iterations never go
+ * to memory (2 n_steps + 1 launches instead of 3 n_steps).  Errors as
+ * pfm_adjoint_step; PFM_EINVAL for n_steps < 1 or a NULL pointer. */
+PFM_API pfm_status pfm_adjoint_steps(pfm_problem* pb, int n_steps, const float* const* u_states,
+                                     const float* const* q_states, float* ubar, float* qbar, float* Dbar,
+                                     float* Sbar, float* work);
+
 /* ---- Batches (many independent problems, one persistent kernel per
  * iteration) ----
  * A batch advances n problems of possibly different grid sizes and label

@@ -6,8 +6,8 @@ Forward: K iterations through the C ABI, saving the state (u, q) every
 `checkpoint_every` iterations.  Backward: for each segment, last first, the
 state is restored from its checkpoint, the segment is recomputed one
 iteration at a time (the kernels are deterministic, so the recomputed states
-equal the forward ones bit for bit), and pfm_adjoint_step is applied to its
-iterations in reverse.  Memory: K / checkpoint_every checkpoints plus one
+equal the forward ones bit for bit), and its iterations' reverse-mode steps
+run in one pfm_adjoint_steps call.  Memory: K / checkpoint_every checkpoints plus one
 segment of states.
 """
 import torch
@@ -56,9 +56,9 @@ class PottsSolve(torch.autograd.Function):
                 u1, q1 = prob.state_async()
                 us.append(u1)
                 qs.append(q1)
-            for i in reversed(range(seg)):
-                prob.adjoint_step(us[i], qs[i], us[i + 1], ubar, qbar, ubar, qbar, Dbar,
-                                  Sbar if Sbar is not None else dummy, work)
+            # the segment's reverse steps in one call (equal to pfm_adjoint_step
+            # applied from its last iteration to its first)
+            prob.adjoint_steps(us, qs[:seg], ubar, qbar, Dbar, Sbar if Sbar is not None else dummy, work)
         return Dbar, Sbar, None, None, None, None, None, None
 
 

@@ -77,6 +77,7 @@ _SIGS = {
     "pfm_set_chunk_length": (C.c_int, [_P, C.c_int]),
     "pfm_chunk_length": (C.c_int, [_P]),
     "pfm_adjoint_step": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "pfm_adjoint_steps": (C.c_int, [_P, C.c_int, _P, _P, _P, _P, _P, _P, _P]),
     "pfm_batch_create": (C.c_int, [C.c_int, C.c_void_p, C.POINTER(pfm_params), _P, C.POINTER(_P)]),
     "pfm_batch_destroy": (None, [_P]),
     "pfm_batch_size": (C.c_int, [_P]),
@@ -376,6 +377,17 @@ class Problem:
         """pfm_adjoint_step on FP32 CUDA tensors (see pfm.h)."""
         check(lib().pfm_adjoint_step(self._h, _ptr(u_k), _ptr(q_k), _ptr(u_k1), _ptr(ubar_k1), _ptr(qbar_k1),
                                      _ptr(ubar_k), _ptr(qbar_k), _ptr(Dbar), _ptr(Sbar), _ptr(work)))
+
+    def adjoint_steps(self, us, qs, ubar, qbar, Dbar, Sbar, work):
+        """pfm_adjoint_steps over a segment: us = [u_0, ..., u_n], qs = [q_0, ...,
+        q_{n-1}] (FP32 CUDA tensors); ubar / qbar in place (see pfm.h)."""
+        n = len(qs)
+        if len(us) != n + 1:
+            raise ValueError("need one more labelling than flows")
+        U = (C.c_void_p * (n + 1))(*[_ptr(u) for u in us])
+        Q = (C.c_void_p * n)(*[_ptr(q) for q in qs])
+        check(lib().pfm_adjoint_steps(self._h, n, U, Q, _ptr(ubar), _ptr(qbar), _ptr(Dbar), _ptr(Sbar),
+                                      _ptr(work)))
 
     def set_flows(self, q):
         q = _as_f32(q)

@@ -48,57 +48,99 @@ __device__ __forceinline__ void coords(long long i, int nx, int ny, int& x, int&
 // accumulations are guarded.  The projection adjoint keeps one thread per
 // voxel and one label's loads at a time: with all of them in flight (one or
 // two threads per voxel) it measured slower.
+// Projection adjoint of label j at voxel i (K1): y = q - c tau grad u' from
+// the step's flows and output labelling, then ybar = J_proj(y)^T qbar' and
+// the derivative of q' with respect to the capacity s, dotted with qbar'.
+// Shared by the per-step kernel and the chained kernel, so both apply the
+// same arithmetic.
+template <int DIM>
+__device__ __forceinline__ float proj_adjoint_label(const AdjArgs& a, int j, long long i, int x, int y, int z,
+                                                    float sf, const float (&qb)[DIM], float (&yb)[DIM]) {
+    const long long n = a.n, plane = (long long)a.nx * a.ny;
+    const float* u1 = a.u_k1 + (long long)j * n + i;
+    const float g0 = *u1;
+    float gr[DIM];
+    gr[0] = x < a.nx - 1 ? u1[1] - g0 : 0.f;
+    gr[1] = y < a.ny - 1 ? u1[a.nx] - g0 : 0.f;
+    if constexpr (DIM == 3) gr[2] = z < a.nz - 1 ? u1[plane] - g0 : 0.f;
+    float yv[DIM];
+    for (int k = 0; k < DIM; ++k) yv[k] = a.q_k[((long long)j * DIM + k) * n + i] - a.ctau * gr[k];
+    const float s = a.s_node[j] * sf;
+    float ds = 0.f;  // d q' / d s . qbar'
+    if (a.aniso) {
+        for (int k = 0; k < DIM; ++k) {
+            if (yv[k] > s) {
+                yb[k] = 0.f;
+                ds += qb[k];
+            } else if (yv[k] < -s) {
+                yb[k] = 0.f;
+                ds -= qb[k];
+            } else {
+                yb[k] = qb[k];
+            }
+        }
+    } else {
+        float r2 = 0.f;
+        for (int k = 0; k < DIM; ++k) r2 += yv[k] * yv[k];
+        if (r2 > s * s && r2 > 0.f) {
+            const float r = sqrtf(r2);
+            float yq = 0.f;
+            for (int k = 0; k < DIM; ++k) yq += yv[k] * qb[k];
+            yq /= r;  // yhat . qbar'
+            for (int k = 0; k < DIM; ++k) yb[k] = (s / r) * (qb[k] - (yv[k] / r) * yq);
+            ds = yq;
+        } else {
+            for (int k = 0; k < DIM; ++k) yb[k] = qb[k];
+        }
+    }
+    return ds;
+}
+
 template <int L, int DIM>
 __global__ void __launch_bounds__(NT) adj_proj_kernel(const AdjArgs a) {
     const long long i = (long long)blockIdx.x * NT + threadIdx.x;
     if (i >= a.n) return;
     int x, y, z;
     coords(i, a.nx, a.ny, x, y, z);
-    const long long n = a.n, plane = (long long)a.nx * a.ny;
+    const long long n = a.n;
     const float sf = a.S ? a.S[pitched(a, x, y, z)] : 1.0f;
     float sbar = 0.f;
 #pragma unroll
     for (int j = 0; j < L; ++j) {
         if (j >= a.nl) break;
-        const float* u1 = a.u_k1 + (long long)j * n + i;
-        const float g0 = *u1;
-        float gr[DIM];
-        gr[0] = x < a.nx - 1 ? u1[1] - g0 : 0.f;
-        gr[1] = y < a.ny - 1 ? u1[a.nx] - g0 : 0.f;
-        if constexpr (DIM == 3) gr[2] = z < a.nz - 1 ? u1[plane] - g0 : 0.f;
-        float yv[DIM], qb[DIM], yb[DIM];
-        for (int k = 0; k < DIM; ++k) {
-            yv[k] = a.q_k[((long long)j * DIM + k) * n + i] - a.ctau * gr[k];
-            qb[k] = a.qbar_k1[((long long)j * DIM + k) * n + i];
-        }
-        const float s = a.s_node[j] * sf;
-        float ds = 0.f;  // d q' / d s . qbar'
-        if (a.aniso) {
-            for (int k = 0; k < DIM; ++k) {
-                if (yv[k] > s) {
-                    yb[k] = 0.f;
-                    ds += qb[k];
-                } else if (yv[k] < -s) {
-                    yb[k] = 0.f;
-                    ds -= qb[k];
-                } else {
-                    yb[k] = qb[k];
-                }
-            }
-        } else {
-            float r2 = 0.f;
-            for (int k = 0; k < DIM; ++k) r2 += yv[k] * yv[k];
-            if (r2 > s * s && r2 > 0.f) {
-                const float r = sqrtf(r2);
-                float yq = 0.f;
-                for (int k = 0; k < DIM; ++k) yq += yv[k] * qb[k];
-                yq /= r;  // yhat . qbar'
-                for (int k = 0; k < DIM; ++k) yb[k] = (s / r) * (qb[k] - (yv[k] / r) * yq);
-                ds = yq;
-            } else {
-                for (int k = 0; k < DIM; ++k) yb[k] = qb[k];
-            }
-        }
+        float qb[DIM], yb[DIM];
+        for (int k = 0; k < DIM; ++k) qb[k] = a.qbar_k1[((long long)j * DIM + k) * n + i];
+        const float ds = proj_adjoint_label<DIM>(a, j, i, x, y, z, sf, qb, yb);
+        for (int k = 0; k < DIM; ++k) a.ybar[((long long)j * DIM + k) * n + i] = yb[k];
+        sbar += a.s_node[j] * ds;
+    }
+    if (a.Sbar) a.Sbar[i] += sbar;
+}
+
+// The divergence adjoint of step k (K3: qbar_k = ybar_k - grad dbar_k) and
+// the projection adjoint of step k-1 (K1, which reads qbar_k at the voxel
+// only) in one pass: qbar_k never goes to memory, ybar_{k-1} overwrites
+// ybar_k in the work buffer (each thread reads and writes its own voxel;
+// the gradient reads only dbar).  b: step k, a: step k-1 (a.u_k1 = b.u_k).
+template <int L, int DIM>
+__global__ void __launch_bounds__(NT) adj_div_proj_kernel(const AdjArgs b, const AdjArgs a) {
+    const long long i = (long long)blockIdx.x * NT + threadIdx.x;
+    if (i >= a.n) return;
+    int x, y, z;
+    coords(i, a.nx, a.ny, x, y, z);
+    const long long n = a.n, plane = (long long)a.nx * a.ny;
+    const long long o[3] = {x < a.nx - 1 ? 1 : 0, y < a.ny - 1 ? (long long)a.nx : 0,
+                            z < a.nz - 1 ? plane : 0};
+    const float sf = a.S ? a.S[pitched(a, x, y, z)] : 1.0f;
+    float sbar = 0.f;
+#pragma unroll
+    for (int j = 0; j < L; ++j) {
+        if (j >= a.nl) break;
+        const float* db = b.dbar + (long long)j * n + i;
+        const float d0 = db[0];
+        float qb[DIM], yb[DIM];
+        for (int k = 0; k < DIM; ++k) qb[k] = b.ybar[((long long)j * DIM + k) * n + i] - (db[o[k]] - d0);
+        const float ds = proj_adjoint_label<DIM>(a, j, i, x, y, z, sf, qb, yb);
         for (int k = 0; k < DIM; ++k) a.ybar[((long long)j * DIM + k) * n + i] = yb[k];
         sbar += a.s_node[j] * ds;
     }
@@ -238,6 +280,33 @@ cudaError_t launch_adjoint(const AdjArgs& a, int ndim, cudaStream_t s) {
         else launch3<16, 2>(a, s);
     }
     return cudaGetLastError();
+}
+
+namespace {
+
+template <int L, int DIM>
+cudaError_t launch_chain(const AdjArgs* st, int nsteps, cudaStream_t s) {
+    const AdjArgs& last = st[nsteps - 1];
+    const unsigned b1 = (unsigned)((last.n + NT - 1) / NT), b2 = (unsigned)((2 * last.n + NT - 1) / NT);
+    adj_proj_kernel<L, DIM><<<b1, NT, 0, s>>>(last);
+    for (int k = nsteps - 1; k >= 0; --k) {
+        adj_prox_kernel<L, DIM><<<b2, NT, 0, s>>>(st[k]);
+        if (k > 0)
+            adj_div_proj_kernel<L, DIM><<<b1, NT, 0, s>>>(st[k], st[k - 1]);
+        else
+            adj_div_kernel<L, DIM><<<b1, NT, 0, s>>>(st[0]);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_adjoint_chain(const AdjArgs* steps, int nsteps, int ndim, cudaStream_t s) {
+    const int L = steps[0].nl <= 4 ? 4 : steps[0].nl <= 8 ? 8 : 16;
+    if (ndim == 3) return L == 4 ? launch_chain<4, 3>(steps, nsteps, s)
+                                 : L == 8 ? launch_chain<8, 3>(steps, nsteps, s) : launch_chain<16, 3>(steps, nsteps, s);
+    return L == 4 ? launch_chain<4, 2>(steps, nsteps, s)
+                  : L == 8 ? launch_chain<8, 2>(steps, nsteps, s) : launch_chain<16, 2>(steps, nsteps, s);
 }
 
 }  // namespace pfm

@@ -281,6 +281,11 @@ struct pfm_problem {
     cudaEvent_t am_done = nullptr;    // the copy out of am_buf has landed
 };
 
+namespace pfm {
+// The reverse-mode steps of n consecutive iterations (pfm_adjoint.cu).
+cudaError_t launch_adjoint_chain(const AdjLaunch* steps, int nsteps, int ndim, cudaStream_t s);
+}  // namespace pfm
+
 namespace {
 
 // tiles of one z-chunk row of the grid: 32 x 4 for the TMA DAG kernel,
@@ -966,6 +971,52 @@ pfm_status pfm_adjoint_step(pfm_problem* pb, const float* u_k, const float* q_k,
     for (int j = 0; j < 16; ++j) L.s_node[j] = j < pb->nl ? pb->s_node[j] : 0.f;
     PFM_CUDA(pfm::launch_adjoint(L, pb->ndim, pb->stream), "adjoint");
     pb->launches += 3;
+    return PFM_OK;
+}
+
+pfm_status pfm_adjoint_steps(pfm_problem* pb, int n_steps, const float* const* u_states,
+                             const float* const* q_states, float* ubar, float* qbar, float* Dbar, float* Sbar,
+                             float* work) {
+    if (!pb) return fail(PFM_EINVAL, "NULL problem");
+    if (n_steps < 1) return fail(PFM_EINVAL, "n_steps must be >= 1");
+    if (!u_states || !q_states || !ubar || !qbar || !Dbar || !work) return fail(PFM_EINVAL, "NULL buffer");
+    for (int k = 0; k <= n_steps; ++k)
+        if (!u_states[k] || (k < n_steps && !q_states[k])) return fail(PFM_EINVAL, "NULL state");
+    if (!pb->flat) return fail(PFM_EUNSUPPORTED, "the adjoint covers the Potts model (flat label set)");
+    if (pb->nl > 16) return fail(PFM_EUNSUPPORTED, "the adjoint supports at most 16 labels");
+    if (pb->prm.grad_source != PFM_GRAD_NORMALISED)
+        return fail(PFM_EUNSUPPORTED, "the adjoint differentiates the NORMALISED iteration");
+    std::vector<pfm::AdjLaunch> st((size_t)n_steps);
+    for (int k = 0; k < n_steps; ++k) {
+        pfm::AdjLaunch& L = st[(size_t)k];
+        L = pfm::AdjLaunch{};
+        L.u_k = u_states[k];
+        L.q_k = q_states[k];
+        L.u_k1 = u_states[k + 1];
+        L.ubar_k1 = ubar;  // the prox adjoint updates ubar in place, step by step
+        L.qbar_k1 = qbar;  // read by the last step's projection adjoint only
+        L.ubar_k = ubar;
+        L.qbar_k = qbar;   // written by the first step's divergence adjoint only
+        L.Dbar = Dbar;
+        L.Sbar = pb->S ? Sbar : nullptr;
+        L.ybar = work;
+        L.dbar = work + (size_t)pb->nl * pb->ndim * pb->nv;
+        L.D = pb->D;
+        L.S = pb->S;
+        L.nx = pb->nx;
+        L.px = pb->px;
+        L.np = pb->n;
+        L.ny = pb->ny;
+        L.nz = pb->nz;
+        L.nl = pb->nl;
+        L.n = pb->nv;
+        L.c = (float)pb->prm.c;
+        L.ctau = (float)(pb->prm.c * pb->prm.tau);
+        L.aniso = pb->prm.norm == PFM_NORM_ANISO;
+        for (int j = 0; j < 16; ++j) L.s_node[j] = j < pb->nl ? pb->s_node[j] : 0.f;
+    }
+    PFM_CUDA(pfm::launch_adjoint_chain(st.data(), n_steps, pb->ndim, pb->stream), "adjoint");
+    pb->launches += 2 * n_steps + 1;
     return PFM_OK;
 }
 

@@ -119,6 +119,7 @@ def test_null_handles_rejected_on_host(pfm):
     L = pfm.lib()
     zc = C.c_int(-7)
     assert L.pfm_tune(None, 3, C.byref(zc)) == 1 and zc.value == -7
+    assert L.pfm_adjoint_steps(None, 2, None, None, None, None, None, None, None) == 1
     assert L.pfm_set_chunk_length(None, 8) == 1
     assert L.pfm_chunk_length(None) == -1
     assert L.pfm_iterate(None, 1) == 1

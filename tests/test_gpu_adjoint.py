@@ -155,3 +155,50 @@ def test_adjoint_matches_finite_differences_of_oracle():
         assert abs(g - fd) <= 1e-2 * abs(fd) + 2e-3, (which, idx, g, fd)
         checked += 1
     assert checked >= 16
+
+
+@pytest.mark.parametrize("shape,nl,aniso,field", [((14, 19, 33), 5, False, True), ((23, 30), 3, True, True),
+                                                  ((9, 12, 20), 4, False, False)],
+                         ids=["3d_iso_field", "2d_aniso_field", "3d_iso_levels"])
+def test_adjoint_steps_equal_single_steps(shape, nl, aniso, field):
+    """pfm_adjoint_steps over a segment of 4 iterations equals
+    pfm_adjoint_step applied from the last iteration to the first, bit for
+    bit (ubar, qbar, Dbar, Sbar), on seeded random output adjoints."""
+    import torch
+    import paper_1501_07844_gb300 as pfm
+    prob = synth.random_problem(5500 + nl, shape, nl=nl, s_kind="field", s_scale=0.3)
+    S = torch.from_numpy(prob.S_field).cuda() if field else None
+    s_label = np.linspace(0.7, 1.3, nl).astype(np.float32)
+    gp = pfm.Problem(torch.from_numpy(prob.D).cuda(), S_field=S, s_node=s_label, c=0.5, tau=0.11,
+                     norm=1 if aniso else 0)
+    try:
+        gp.iterate(3)
+        us, qs = [], []
+        for k in range(5):
+            u, q = gp.state_async()
+            us.append(u)
+            qs.append(q)
+            if k < 4:
+                gp.iterate(1)
+        rng = np.random.default_rng(5600 + nl)
+        ubar0 = torch.from_numpy(rng.normal(size=us[0].shape).astype(np.float32)).cuda()
+        qbar0 = torch.from_numpy(rng.normal(size=qs[0].shape).astype(np.float32)).cuda()
+        n = int(np.prod(shape))
+        work = torch.empty((len(shape) + 1) * nl * n, dtype=torch.float32, device="cuda")
+        res = []
+        for chained in (False, True):
+            ubar, qbar = ubar0.clone(), qbar0.clone()
+            Dbar = torch.full(us[0].shape, 0.25, dtype=torch.float32, device="cuda")
+            Sbar = torch.full(shape, 0.5, dtype=torch.float32, device="cuda")
+            torch.cuda.synchronize()  # the library's stream reads what torch's wrote
+            if chained:
+                gp.adjoint_steps(us, qs[:4], ubar, qbar, Dbar, Sbar, work)
+            else:
+                for i in reversed(range(4)):
+                    gp.adjoint_step(us[i], qs[i], us[i + 1], ubar, qbar, ubar, qbar, Dbar, Sbar, work)
+            torch.cuda.synchronize()
+            res.append([t.cpu().numpy() for t in (ubar, qbar, Dbar, Sbar)])
+        for a, b in zip(res[0], res[1]):
+            assert np.array_equal(a, b), np.abs(a - b).max()
+    finally:
+        gp.close()
