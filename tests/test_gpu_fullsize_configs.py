@@ -1,8 +1,9 @@
 """Parity at the full sizes of the other benchmark workloads, in the launch
 configurations bench.py times: HMF 192^3 (FP32 and BF16 storage, TMA DAG
-kernel), Potts 256^3 x 8 with BF16 storage, the 32-volume DAGMF batch (TMA
-batched kernel) and the differentiable Potts 128^3 x 6 (100 unrolled
-iterations, checkpoint every 10).  Every voxel is compared with the FP64
+kernel), Potts 256^3 x 8 with BF16 storage, Ishikawa 256^3 with 8 labels
+(chain-specialised kernel at the tuned chunk length), the 32-volume DAGMF
+batch (TMA batched kernel) and the differentiable Potts 128^3 x 6 (100
+unrolled iterations, checkpoint every 10).  Every voxel is compared with the FP64
 oracle after a few iterations (the oracle's cost bounds the count; 20 for
 BF16 storage, whose thresholded labels are compared where the oracle's two
 largest labels are further apart than BF16 resolves); the
@@ -143,3 +144,25 @@ def test_diff_128_gradients_at_sampled_entries():
             g = gS[idx]
         fd = (loss(Dp, Sp) - loss(Dm, Sm)) / (2 * h)
         assert abs(g - fd) <= 2e-2 * abs(fd) + 2e-3, (which, idx, g, fd)
+
+
+def test_ishikawa_256_every_voxel():
+    """The bench's Ishikawa volume (256^3, 7 levels / 8 labels) on the
+    chain-specialised kernel at the chunk length the tuner picks there (64),
+    against the oracle's literal Algorithm 3 at every voxel after 3
+    iterations."""
+    import oracle
+    nlev = 7
+    prob = synth.ishikawa_problem(seed=2000, spatial=(256, 256, 256), nlev=nlev)
+    with gpu_problem(prob) as gp:
+        assert gp.variant == "fused_tma_ishikawa"
+        gp.chunk_length = 64
+        gp.iterate(3)
+        u = gp.labels().cpu().numpy()
+        q = gp.flows().cpu().numpy()
+    D = prob.D.astype(np.float64)
+    u3, q3 = oracle.ishikawa_init(prob.spatial, nlev)
+    oracle.ishikawa_iterate(D, u3, q3, 3, prob.c, prob.tau, s_level=prob.s_node[:nlev].astype(np.float64))
+    assert np.abs(u - u3).max() <= TOL_U
+    assert np.abs(q[:nlev] - q3).max() <= TOL_U and not np.any(q[nlev:])
+    assert np.mean(np.argmax(u, 0) == np.argmax(u3, 0)) >= TOL_ARGMAX
