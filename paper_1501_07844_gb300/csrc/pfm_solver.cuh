@@ -268,12 +268,14 @@ struct Solver final : SolverBase {
             if (e != cudaSuccess) return e;
             fused_tma_x2_kernel<MAXL, T, EXACT, WITH_E, IDX32><<<grid, X2_NT, Lay::total_bytes, s>>>(a, m, partial);
             return cudaGetLastError();
+        } else {
+            // the one-voxel kernel (not instantiated for 3-D BF16, which never runs it)
+            cudaError_t e = cudaFuncSetAttribute(fused_tma_kernel<MAXL, DIM, T, EXACT, WITH_E, IDX32>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, Lay::total_bytes);
+            if (e != cudaSuccess) return e;
+            fused_tma_kernel<MAXL, DIM, T, EXACT, WITH_E, IDX32><<<grid, TMA_NT, Lay::total_bytes, s>>>(a, m, partial);
+            return cudaGetLastError();
         }
-        cudaError_t e = cudaFuncSetAttribute(fused_tma_kernel<MAXL, DIM, T, EXACT, WITH_E, IDX32>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, Lay::total_bytes);
-        if (e != cudaSuccess) return e;
-        fused_tma_kernel<MAXL, DIM, T, EXACT, WITH_E, IDX32><<<grid, TMA_NT, Lay::total_bytes, s>>>(a, m, partial);
-        return cudaGetLastError();
     }
 
     // 32-bit slot offsets when every offset of the flow array fits

@@ -3,15 +3,15 @@
 // Same arithmetic as fused_step_kernel (label prox of plane p on the
 // halo-extended 33 x 9 tile, then the flow step of plane p-1), but every
 // operand of a plane is brought into shared memory by the Tensor Memory
-// Accelerator (cp.async.bulk.tensor) one plane ahead, through a 3-stage ring
-// guarded by mbarriers:
-//   stage(p-1): flows and S of plane p-1, and the field g of plane p-1
-//   stage(p)  : u, D, flows of plane p (g written over u in place)
-//   stage(p+1): in flight
-// so memory latency overlaps the arithmetic of the current plane and no
-// operand is carried in registers across planes.  Out-of-range box elements
-// (x0-4 < 0, y0-1 < 0, z = -1, beyond the far edges) are zero-filled by the
-// TMA unit, which is exactly the zero boundary flow of the divergence.
+// Accelerator (cp.async.bulk.tensor) through a 3-stage ring guarded by
+// mbarriers.  An iteration reads only its own plane's stage: what the flow
+// step of plane p-1 needs at a voxel (its flows, g and S) stays in the
+// registers of the threads that own the voxel, the neighbours' g goes
+// through a two-plane shared buffer, so the stage of plane p-1 is refilled
+// with plane p+2 at the start of plane p and two planes are in flight while
+// one is consumed.  Out-of-range box elements (x0-4 < 0, y0-1 < 0, z = -1,
+// beyond the far edges) are zero-filled by the TMA unit, which is exactly
+// the zero boundary flow of the divergence.
 //
 // Every mbarrier wait is bounded by a cycle budget; on expiry the kernel
 // sets FLAG_TIMEOUT, stops issuing, waits (bounded) for its own copies in

@@ -8,12 +8,16 @@
 // lane h of the pair's four threads takes labels h, h+4, ...  Every load,
 // every add / multiply / fused multiply-add and every store of the
 // iteration then serves two voxels (64-bit shared loads and global stores of
-// FP32 pairs, 32-bit ones of BF16 pairs; add.f32x2 / fma.rn.f32x2), so the
-// kernel issues about half the instructions per voxel-label update of the
-// one-voxel-per-thread form.  Only the hardware approximations (ex2,
-// rsqrt, rcp), the minimum and the projection's scale stay per voxel.  The
-// per-voxel minimum and normaliser of the prox are combined over the four
-// lanes with two shuffle rounds.
+// FP32 pairs, 32-bit ones of BF16 pairs; packed f32x2 add / multiply / fma),
+// so the kernel issues fewer instructions per voxel-label update than the
+// one-voxel-per-thread form (about a fifth fewer with BF16 storage: widening
+// BF16 pairs, the per-voxel work below and the operands assembled from
+// neighbours stay).  Only the hardware approximations (ex2, rsqrt, rcp),
+// the minimum and the projection's scale stay per voxel.  The per-voxel
+// minimum and normaliser of the prox are combined over the four lanes with
+// two shuffle rounds.  Used for BF16 storage: with FP32 storage the
+// one-voxel kernel already runs at the bandwidth roof and this one measured
+// slower.
 //
 // The halo-extended tile is covered by 153 pairs: 16 x 8 owned pairs, the
 // 16 pairs of the y-halo row and 9 pairs (x0+32, x0+33) of the x-halo column,
