@@ -86,8 +86,9 @@ __device__ __forceinline__ float proj_adjoint_label(const AdjArgs& a, int j, lon
             const float r = sqrtf(r2);
             float yq = 0.f;
             for (int k = 0; k < DIM; ++k) yq += yv[k] * qb[k];
-            yq /= r;  // yhat . qbar'
-            for (int k = 0; k < DIM; ++k) yb[k] = (s / r) * (qb[k] - (yv[k] / r) * yq);
+            const float ir = 1.0f / r;
+            yq *= ir;  // yhat . qbar'
+            for (int k = 0; k < DIM; ++k) yb[k] = (s * ir) * (qb[k] - (yv[k] * ir) * yq);
             ds = yq;
         } else {
             for (int k = 0; k < DIM; ++k) yb[k] = qb[k];
@@ -172,6 +173,7 @@ __global__ void __launch_bounds__(NT) adj_prox_kernel(const AdjArgs a) {
     const float bx = x > 0 ? 1.f : 0.f, by = y > 0 ? 1.f : 0.f, bz = z > 0 ? 1.f : 0.f;
     float d[HL], ub[HL], u1[HL], uk[HL], db0[HL];
     bool valid[HL];
+    const float inv_c = 1.0f / a.c;
     float m = 3.0e38f;
     float dot = 0.f;
 #pragma unroll
@@ -204,7 +206,7 @@ __global__ void __launch_bounds__(NT) adj_prox_kernel(const AdjArgs a) {
     float asum = 0.f;
 #pragma unroll
     for (int k = 0; k < HL; ++k) {
-        d[k] = __expf(-(d[k] - m) / a.c);  // e_j (shifted)
+        d[k] = __expf((m - d[k]) * inv_c);  // e_j (shifted)
         if (valid[k]) asum += uk[k] * d[k];
     }
     asum += __shfl_xor_sync(0xffffffffu, asum, 1);
@@ -215,7 +217,7 @@ __global__ void __launch_bounds__(NT) adj_prox_kernel(const AdjArgs a) {
         if (!valid[k]) continue;
         const float w = ub[k] - dot;
         a.ubar_k[(long long)j * n + i] = d[k] * inv_a * w;
-        const float dbar = -u1[k] * w / a.c;
+        const float dbar = -u1[k] * w * inv_c;
         a.dbar[(long long)j * n + i] = dbar;
         a.Dbar[(long long)j * n + i] = db0[k] + dbar;
     }
