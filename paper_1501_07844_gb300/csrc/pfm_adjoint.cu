@@ -83,10 +83,9 @@ __device__ __forceinline__ float proj_adjoint_label(const AdjArgs& a, int j, lon
         float r2 = 0.f;
         for (int k = 0; k < DIM; ++k) r2 += yv[k] * yv[k];
         if (r2 > s * s && r2 > 0.f) {
-            const float r = sqrtf(r2);
+            const float ir = rsqrtf(r2);  // 1 / |y|
             float yq = 0.f;
             for (int k = 0; k < DIM; ++k) yq += yv[k] * qb[k];
-            const float ir = 1.0f / r;
             yq *= ir;  // yhat . qbar'
             for (int k = 0; k < DIM; ++k) yb[k] = (s * ir) * (qb[k] - (yv[k] * ir) * yq);
             ds = yq;
