@@ -255,6 +255,14 @@ PFM_API const char* pfm_kernel_variant(const pfm_problem* pb);
 /* Iterations run since creation or the last reset, and kernels this problem
  * has launched since creation (for launch accounting). */
 PFM_API int64_t pfm_iterations_done(const pfm_problem* pb);
+/* Failure-detection self-test: runs, on the problem's stream, one bounded
+ * mbarrier wait of the kind every TMA pipeline uses, on a barrier nothing
+ * arrives on.  The wait gives up after its cycle budget (about 2 s), raises
+ * the timeout flag and the kernel returns; the call then restores the
+ * problem's flags and returns PFM_ETIMEOUT (PFM_ECUDA if the wait did not
+ * report).  The problem and the CUDA context stay usable.  Not part of the
+ * paper's method. */
+PFM_API pfm_status pfm_selftest_timeout(pfm_problem* pb);
 PFM_API int64_t pfm_launch_count(const pfm_problem* pb);
 
 /* Autotuner of the plane-marching kernels (the iteration kernels walk their

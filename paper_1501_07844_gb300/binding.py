@@ -74,6 +74,7 @@ _SIGS = {
     "pfm_iterations_done": (C.c_int64, [_P]),
     "pfm_launch_count": (C.c_int64, [_P]),
     "pfm_tune": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int)]),
+    "pfm_selftest_timeout": (C.c_int, [_P]),
     "pfm_set_chunk_length": (C.c_int, [_P, C.c_int]),
     "pfm_chunk_length": (C.c_int, [_P]),
     "pfm_adjoint_step": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),

@@ -284,6 +284,8 @@ struct pfm_problem {
 namespace pfm {
 // The reverse-mode steps of n consecutive iterations (pfm_adjoint.cu).
 cudaError_t launch_adjoint_chain(const AdjLaunch* steps, int nsteps, int ndim, cudaStream_t s);
+// A bounded mbarrier wait that nothing completes (pfm_misc.cu).
+cudaError_t launch_wait_selftest(unsigned* flags, cudaStream_t s);
 }  // namespace pfm
 
 namespace {
@@ -1018,6 +1020,22 @@ pfm_status pfm_adjoint_steps(pfm_problem* pb, int n_steps, const float* const* u
     PFM_CUDA(pfm::launch_adjoint_chain(st.data(), n_steps, pb->ndim, pb->stream), "adjoint");
     pb->launches += 2 * n_steps + 1;
     return PFM_OK;
+}
+
+pfm_status pfm_selftest_timeout(pfm_problem* pb) {
+    if (!pb) return fail(PFM_EINVAL, "NULL problem");
+    unsigned before = 0;
+    pfm_status st = read_flags(pb, &before);
+    if (st != PFM_OK) return st;
+    PFM_CUDA(pfm::launch_wait_selftest(pb->flags, pb->stream), "self-test");
+    pb->launches++;
+    unsigned after = 0;
+    if ((st = read_flags(pb, &after)) != PFM_OK) return st;
+    // the problem's own state is untouched: restore its flags word
+    PFM_CUDA(cudaMemcpyAsync(pb->flags, &before, sizeof before, cudaMemcpyHostToDevice, pb->stream), "flags");
+    PFM_CUDA(cudaStreamSynchronize(pb->stream), "stream sync");
+    if (after & pfm::FLAG_TIMEOUT) return fail(PFM_ETIMEOUT, "a bounded device-side wait expired (self-test)");
+    return fail(PFM_ECUDA, "self-test: the bounded wait did not report its timeout");
 }
 
 int64_t pfm_iterations_done(const pfm_problem* pb) { return pb ? pb->iters : -1; }

@@ -125,6 +125,21 @@ __global__ void set_flows_kernel(const float* src, int nn, int nx, int ny, int n
     for (int k = 0; k < DIM; ++k) stv<T>(dst + ((long long)A * DIM + k) * np + pi, yv[k]);
 }
 
+// Self-test of the bounded wait every TMA pipeline uses: an mbarrier that
+// nothing arrives on; each thread's wait must give up after its cycle budget
+// and raise FLAG_TIMEOUT, and the kernel must return normally.
+__global__ void wait_selftest_kernel(unsigned* flags) {
+    __shared__ __align__(8) unsigned long long bar;
+    const unsigned b = smem_addr(&bar);
+    if (threadIdx.x == 0) {
+        mbar_init(b, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const bool ok = mbar_wait_bounded(b, 0u);
+    if (__syncthreads_or(!ok) && threadIdx.x == 0) atomicOr(flags, FLAG_TIMEOUT);
+}
+
 __global__ void validate_kernel(const float* D, long long nD, const float* S, long long nS, unsigned* flags) {
     bool bad = false;
     for (long long i = (long long)blockIdx.x * NT + threadIdx.x; i < nD; i += (long long)gridDim.x * NT)
@@ -216,6 +231,11 @@ cudaError_t launch_set_flows(const float* src, int storage, int nn, int ndim, in
                                                                                    S, aniso, (__nv_bfloat16*)dst)
                               : set_flows_kernel<__nv_bfloat16, 2><<<b, NT, 0, s>>>(src, nn, nx, ny, nz, px, s_node_dev,
                                                                                    S, aniso, (__nv_bfloat16*)dst)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wait_selftest(unsigned* flags, cudaStream_t s) {
+    wait_selftest_kernel<<<1, 32, 0, s>>>(flags);
     return cudaGetLastError();
 }
 

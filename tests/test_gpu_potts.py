@@ -434,3 +434,19 @@ def test_tune_picks_a_candidate_and_restarts():
 def pfm_error():
     import paper_1501_07844_gb300 as pfm
     return pfm.PfmError
+
+
+def test_bounded_wait_gives_up_and_the_context_survives():
+    """Failure detection without a fault: a bounded mbarrier wait that
+    nothing completes (the wait primitive of every TMA pipeline) gives up,
+    the host reads PFM_ETIMEOUT, and the problem then solves correctly."""
+    import time
+    import paper_1501_07844_gb300 as pfm
+    prob = synth.potts3d_problem(seed=2700, nl=8, shape=(12, 20, 40), iters=20)
+    with gpu_problem(prob) as gp:
+        t0 = time.time()
+        st = pfm.lib().pfm_selftest_timeout(gp._h)
+        assert st == 6, st  # PFM_ETIMEOUT
+        assert b"self-test" in pfm.lib().pfm_last_error()
+        assert time.time() - t0 < 60
+        compare(prob, gp, 20)
