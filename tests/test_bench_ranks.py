@@ -53,3 +53,28 @@ def test_single_rank_helpers():
     assert bench.reduce_max(3.5, None, "cpu") == 3.5
     assert bench.throughput(1, 4, 10, 2.0) == 20.0
     assert bench.rank_seed(0) != bench.rank_seed(1)
+
+
+def test_algorithmic_bytes_match_the_per_update_counts():
+    """The roofline denominators bench.py reports: the fused schedule reads
+    u, D, q and writes u, q once per iteration (d and the normaliser stay on
+    chip), S once per voxel; the in-place schedule reads u and q twice.  Per
+    voxel: Potts 8 labels FP32 8 * 36 + 4 = 292 B (BF16 storage 8 * 20 + 4),
+    in place 8 * 52 + 4; HMF 12 end-labels / 15 flow nodes with per-node
+    capacities 504 B; Ishikawa 8 labels / 7 flow-carrying levels 264 B; 2-D
+    Potts 4 labels 4 * 28 B + 4."""
+    import numpy as np
+    import bench
+    import synth
+    cases = [
+        (synth.potts3d_problem(seed=1, nl=8, shape=(4, 5, 6)), 0, 0, 8 * 36 + 4),
+        (synth.potts3d_problem(seed=1, nl=8, shape=(4, 5, 6)), 1, 0, 8 * 20 + 4),
+        (synth.potts3d_problem(seed=1, nl=8, shape=(4, 5, 6)), 0, 1, 8 * 52 + 4),
+        (synth.hmf_problem(seed=1, shape=(4, 5, 6)), 0, 0, 504),
+        (synth.ishikawa_problem(1, (4, 5, 6), nlev=7), 0, 0, 264),
+        (synth.potts2d_problem(seed=1), 0, 0, 4 * 28 + 4),
+    ]
+    for prob, storage, schedule, per_voxel in cases:
+        n = int(np.prod(prob.spatial))
+        got = bench.algorithmic_bytes_per_iter(prob, storage, schedule)
+        assert got == n * per_voxel, (prob.name, storage, schedule, got / n, per_voxel)
