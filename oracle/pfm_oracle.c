@@ -204,6 +204,7 @@ void orc_potts_energy(const orc_grid* g, int nl, const double* D,
             e += DL[i] * uL[i] + cap(S_field, s_node, L, i) * vnorm(nd, norm, gb, n, i);
         E += e;
         orc_div(g, q + (long)L * nd * n, z + (long)L * n);
+#pragma omp parallel for schedule(static) if (n > 65536)
         for (long i = 0; i < n; ++i) z[(long)L * n + i] += DL[i];
     }
     double P = 0.0;
@@ -345,6 +346,7 @@ static void dag_excess(const orc_grid* g, const orc_dag* dag, const dag_info* di
     for (int A = 0; A < di->nn; ++A)
         if (di->is_leaf[A]) {
             const double* DL = D + (long)di->leaf_of[A] * n;
+#pragma omp parallel for schedule(static) if (n > 65536)
             for (long i = 0; i < n; ++i) d[(long)A * n + i] += DL[i];
         }
     for (int k = 0; k < di->nn; ++k) {
@@ -354,6 +356,7 @@ static void dag_excess(const orc_grid* g, const orc_dag* dag, const dag_info* di
                 double* dc = d + (long)dag->child[e] * n;
                 const double* da = d + (long)A * n;
                 const double w = dag->w[e];
+#pragma omp parallel for schedule(static) if (n > 65536)
                 for (long i = 0; i < n; ++i) dc[i] += w * da[i];
             }
     }
@@ -375,6 +378,7 @@ int orc_dag_iterate(const orc_grid* g, const orc_dag* dag, const double* D,
             if (di.is_leaf[A]) {
                 double* uL = u + (long)di.leaf_of[A] * n;
                 const double* dA = d + (long)A * n;
+#pragma omp parallel for schedule(static) if (n > 65536)
                 for (long i = 0; i < n; ++i) uL[i] *= exp(-dA[i] / p->c);
             }
         if (p->grad_source == ORC_PAPER_LITERAL) {
@@ -400,6 +404,7 @@ int orc_dag_iterate(const orc_grid* g, const orc_dag* dag, const double* D,
                     double* dp = d + (long)dag->parent[e] * n;
                     const double* da = d + (long)A * n;
                     const double w = dag->w[e];
+#pragma omp parallel for schedule(static) if (n > 65536)
                     for (long i = 0; i < n; ++i) dp[i] += w * da[i];
                 }
         }
@@ -430,8 +435,13 @@ int orc_dag_energy(const orc_grid* g, const orc_dag* dag, const double* D,
     for (int k = nn - 1; k >= 0; --k) {
         const int A = di.order[k];
         for (int e = 0; e < dag->n_edges; ++e)
-            if (dag->child[e] == A && dag->parent[e] >= 0)
-                for (long i = 0; i < n; ++i) uA[(long)dag->parent[e] * n + i] += dag->w[e] * uA[(long)A * n + i];
+            if (dag->child[e] == A && dag->parent[e] >= 0) {
+                double* up = uA + (long)dag->parent[e] * n;
+                const double* ua = uA + (long)A * n;
+                const double w = dag->w[e];
+#pragma omp parallel for schedule(static) if (n > 65536)
+                for (long i = 0; i < n; ++i) up[i] += w * ua[i];
+            }
     }
     double E = 0.0;
     for (int A = 0; A < nn; ++A) {
@@ -446,6 +456,7 @@ int orc_dag_energy(const orc_grid* g, const orc_dag* dag, const double* D,
     }
     dag_excess(g, dag, &di, D, q, d);
     double P = 0.0;
+#pragma omp parallel for reduction(+ : P) schedule(static) if (n > 65536)
     for (long i = 0; i < n; ++i) {
         double m = INFINITY;
         for (int A = 0; A < nn; ++A)
@@ -484,14 +495,18 @@ void orc_ishikawa_iterate(const orc_grid* g, int nlev, const double* D,
     double* gb = (double*)malloc(sizeof(double) * nd * n);
     for (int it = 0; it < iters; ++it) {
         /* d_{L_0} = 0; d_{L_i} = d_{L_{i-1}} + div q_{L_i} for i = 1..N */
+#pragma omp parallel for schedule(static) if (n > 65536)
         for (long x = 0; x < n; ++x) d[x] = 0.0;
         for (int i = 1; i <= nlev; ++i) {
             orc_div(g, q + (long)(i - 1) * nd * n, dv);
+#pragma omp parallel for schedule(static) if (n > 65536)
             for (long x = 0; x < n; ++x) d[(long)i * n + x] = d[(long)(i - 1) * n + x] + dv[x];
         }
         /* d_{L_i} += D_{L_i} for every label */
+#pragma omp parallel for schedule(static) if (n > 65536)
         for (long k = 0; k < (long)nlab * n; ++k) d[k] += D[k];
         /* u_{L_i} <- u_{L_i} exp(-d_{L_i}/c) */
+#pragma omp parallel for schedule(static) if (n > 65536)
         for (long k = 0; k < (long)nlab * n; ++k) u[k] *= exp(-d[k] / p->c);
         if (p->grad_source == ORC_PAPER_LITERAL) {
             memcpy(d, u, sizeof(double) * (size_t)nlab * n); /* d <- u before normalising */
@@ -501,8 +516,10 @@ void orc_ishikawa_iterate(const orc_grid* g, int nlev, const double* D,
             memcpy(d, u, sizeof(double) * (size_t)nlab * n);
         }
         /* d_{L_i} += d_{L_{i+1}} for i = N-1 .. 1 */
-        for (int i = nlev - 1; i >= 1; --i)
+        for (int i = nlev - 1; i >= 1; --i) {
+#pragma omp parallel for schedule(static) if (n > 65536)
             for (long x = 0; x < n; ++x) d[(long)i * n + x] += d[(long)(i + 1) * n + x];
+        }
         /* q_{L_i} <- Proj(q_{L_i} - c tau grad d_{L_i}) for i = 1..N */
         for (int i = 1; i <= nlev; ++i)
             flow_step(g, p->norm, p->c * p->tau, d + (long)i * n, S_field, s_level, i - 1,

@@ -5,6 +5,8 @@ hand-computed value, a closed form, an invariant, an independent algorithm
 (explicit-flow ALM, linear programming, exhaustive search) or the paper's
 own definitions (path weights W, flow excess d).
 """
+import math
+
 import numpy as np
 import pytest
 
@@ -418,3 +420,153 @@ def test_ishikawa_converges_to_lp_optimum(orc):
     E, P = orc.dag_energy(dag, D, u, qd, s_node=prob.s_node.astype(np.float64), norm=orc.ANISO)
     lp = _lp_optimum(D, dag.path_weights(), dag.leaves(), None, prob.s_node.astype(np.float64))
     assert abs(E - lp) <= 1e-7 * abs(lp) and abs(P - lp) <= 1e-7 * abs(lp)
+
+
+# ---------------------------------------------------------------- PAPER_LITERAL worked by hand
+#
+# The flow step as Algorithms 1, 2 and 3 print it differentiates the
+# UNNORMALISED product u exp(-d/c), formed before the normaliser a(x)
+# divides it out.  These two-voxel examples (grid nx = 2, ny = 1, so only the
+# x flow at x = 0 can be nonzero: the forward difference is zero at the last
+# index and along y) are worked by hand from the algorithms' lines, two
+# iterations each so that the second divergence uses the literal flow.  The
+# data terms are multiples of ln 2 with c = 1, so the first iteration's
+# numbers are exact binary fractions; the applied step is c tau = 1/4.
+# Divergence on this grid: div q = (q(0), -q(0)).
+
+LN2 = math.log(2.0)
+C_HAND, TAU_HAND = 1.0, 0.25
+STEP_HAND = C_HAND * TAU_HAND
+
+
+def _clip(y, s):
+    """Proj onto |y| <= s for a one-component (x-only) flow; also returns
+    whether the capacity was active."""
+    return (max(-s, min(s, y)), abs(y) > s)
+
+
+def test_potts_paper_literal_worked_by_hand(orc):
+    """Algorithm 1 with the flow step on u exp(-(D + div q)/c), two labels."""
+    D = np.array([[[0.0, 2 * LN2]], [[LN2, 0.0]]])      # [label][y][x]
+    s = np.array([0.2, 1.0])                             # capacity per label
+    # iteration 1: q = 0, div q = 0, u = 1/2
+    ut0 = [0.5, 0.125]                                   # 0.5 * 2^0, 0.5 * 2^-2
+    ut1 = [0.25, 0.5]                                    # 0.5 * 2^-1, 0.5 * 2^0
+    q0, act0 = _clip(0.0 - STEP_HAND * (ut0[1] - ut0[0]), s[0])   # 0.09375
+    q1, act1 = _clip(0.0 - STEP_HAND * (ut1[1] - ut1[0]), s[1])   # -0.0625
+    assert (q0, q1, act0, act1) == (0.09375, -0.0625, False, False)
+    a = [ut0[0] + ut1[0], ut0[1] + ut1[1]]               # 3/4, 5/8
+    u0 = [ut0[0] / a[0], ut0[1] / a[1]]                  # 2/3, 1/5
+    u1 = [ut1[0] / a[0], ut1[1] / a[1]]                  # 1/3, 4/5
+    u, q = orc.potts_init((1, 2), 2)
+    orc.potts_iterate(D, u, q, 1, C_HAND, TAU_HAND, s_node=s, grad_source=orc.PAPER_LITERAL)
+    assert np.abs(u[:, 0] - [u0, u1]).max() <= 1e-15
+    assert np.array_equal(q[:, 0, 0], [[q0, 0.0], [q1, 0.0]]) and not np.any(q[:, 1])
+    # iteration 2: d_L = D_L + div q_L with the literal flows
+    ut0 = [u0[0] * math.exp(-(0.0 + q0)), u0[1] * math.exp(-(2 * LN2 - q0))]
+    ut1 = [u1[0] * math.exp(-(LN2 + q1)), u1[1] * math.exp(-(0.0 - q1))]
+    q0, act0 = _clip(q0 - STEP_HAND * (ut0[1] - ut0[0]), s[0])
+    q1, act1 = _clip(q1 - STEP_HAND * (ut1[1] - ut1[0]), s[1])
+    assert act0 and not act1 and q0 == 0.2               # the capacity bites on label 0 now
+    a = [ut0[0] + ut1[0], ut0[1] + ut1[1]]
+    u_hand = np.array([[ut0[0] / a[0], ut0[1] / a[1]], [ut1[0] / a[0], ut1[1] / a[1]]])
+    orc.potts_iterate(D, u, q, 1, C_HAND, TAU_HAND, s_node=s, grad_source=orc.PAPER_LITERAL)
+    assert np.abs(u[:, 0] - u_hand).max() <= 1e-15
+    assert np.abs(q[:, 0, 0] - [[q0, 0.0], [q1, 0.0]]).max() <= 1e-15 and not np.any(q[:, 1])
+    # the flow step on the normalised labelling gives different numbers
+    un, qn = orc.potts_init((1, 2), 2)
+    orc.potts_iterate(D, un, qn, 2, C_HAND, TAU_HAND, s_node=s, grad_source=orc.NORMALISED)
+    assert np.abs(qn[1, 0, 0, 0] - q1) > 1e-2 and np.abs(un - u).max() > 1e-3
+
+
+def test_potts_normalised_first_iteration_by_hand(orc):
+    """Algorithm 1 with the flow step on the normalised labelling (the
+    gradient of Eq. potts_bregmanopt), first iteration of the same example."""
+    D = np.array([[[0.0, 2 * LN2]], [[LN2, 0.0]]])
+    s = np.array([0.2, 1.0])
+    u, q = orc.potts_init((1, 2), 2)
+    orc.potts_iterate(D, u, q, 1, C_HAND, TAU_HAND, s_node=s, grad_source=orc.NORMALISED)
+    # u = (2/3, 1/5) and (1/3, 4/5); y_L = -1/4 (u_L(1) - u_L(0))
+    assert np.abs(u[:, 0] - [[2 / 3, 0.2], [1 / 3, 0.8]]).max() <= 1e-15
+    assert np.abs(q[:, 0, 0, 0] - [0.25 * (2 / 3 - 0.2), -0.25 * (0.8 - 1 / 3)]).max() <= 1e-15
+
+
+def test_dag_paper_literal_worked_by_hand(orc):
+    """Algorithm 2 on S -> A -> {L0, L1} (w = 1): the inner node's flow is
+    driven by g_A = sum of its end-labels' UNNORMALISED products, which is
+    the normaliser a(x) -- not 1, as it would be on the normalised labels
+    (where q_A stays zero)."""
+    dag = orc.Dag(3, [(-1, 0, 1.0), (0, 1, 1.0), (0, 2, 1.0)])
+    D = np.array([[[0.0, 2 * LN2]], [[LN2, 0.0]]])      # leaves L0 (node 1), L1 (node 2)
+    s = np.array([0.05, 0.2, 1.0])                       # A, L0, L1
+    # iteration 1: q = 0, d = D on the leaves, u = 1/2
+    ut0, ut1 = [0.5, 0.125], [0.25, 0.5]
+    qL0, _ = _clip(-STEP_HAND * (ut0[1] - ut0[0]), s[1])           # 0.09375
+    qL1, _ = _clip(-STEP_HAND * (ut1[1] - ut1[0]), s[2])           # -0.0625
+    gA = [ut0[0] + ut1[0], ut0[1] + ut1[1]]                        # 3/4, 5/8
+    qA, actA = _clip(-STEP_HAND * (gA[1] - gA[0]), s[0])           # 1/32
+    assert (qL0, qL1, qA, actA) == (0.09375, -0.0625, 0.03125, False)
+    u0, u1 = [ut0[0] / gA[0], ut0[1] / gA[1]], [ut1[0] / gA[0], ut1[1] / gA[1]]
+    u, q = orc.dag_init((1, 2), dag)
+    orc.dag_iterate(dag, D, u, q, 1, C_HAND, TAU_HAND, s_node=s, grad_source=orc.PAPER_LITERAL)
+    assert np.abs(u[:, 0] - [u0, u1]).max() <= 1e-15
+    assert np.array_equal(q[:, 0, 0], [[qA, 0.0], [qL0, 0.0], [qL1, 0.0]]) and not np.any(q[:, 1])
+    # iteration 2: top-down excess d_L = D_L + div q_L + d_A, d_A = div q_A
+    dA = [qA, -qA]
+    d0 = [0.0 + qL0 + dA[0], 2 * LN2 - qL0 + dA[1]]
+    d1 = [LN2 + qL1 + dA[0], 0.0 - qL1 + dA[1]]
+    ut0 = [u0[k] * math.exp(-d0[k]) for k in range(2)]
+    ut1 = [u1[k] * math.exp(-d1[k]) for k in range(2)]
+    qL0, _ = _clip(qL0 - STEP_HAND * (ut0[1] - ut0[0]), s[1])
+    qL1, _ = _clip(qL1 - STEP_HAND * (ut1[1] - ut1[0]), s[2])
+    gA = [ut0[0] + ut1[0], ut0[1] + ut1[1]]
+    qA, actA = _clip(qA - STEP_HAND * (gA[1] - gA[0]), s[0])
+    assert not actA and abs(qA) > 1e-3
+    u_hand = np.array([[ut0[0] / gA[0], ut0[1] / gA[1]], [ut1[0] / gA[0], ut1[1] / gA[1]]])
+    orc.dag_iterate(dag, D, u, q, 1, C_HAND, TAU_HAND, s_node=s, grad_source=orc.PAPER_LITERAL)
+    assert np.abs(u[:, 0] - u_hand).max() <= 1e-15
+    assert np.abs(q[:, 0, 0] - [[qA, 0.0], [qL0, 0.0], [qL1, 0.0]]).max() <= 1e-15 and not np.any(q[:, 1])
+    # on the normalised labels the inner flow never moves
+    un, qn = orc.dag_init((1, 2), dag)
+    orc.dag_iterate(dag, D, un, qn, 2, C_HAND, TAU_HAND, s_node=s, grad_source=orc.NORMALISED)
+    assert not np.any(qn[0])
+
+
+def test_ishikawa_paper_literal_worked_by_hand(orc):
+    """Algorithm 3 with N = 2 levels (labels L0, L1, L2): the cumulative
+    excess d_{L_i} = D_{L_i} + div q_1 + ... + div q_i, and the level flows
+    driven by the bottom-up sums g_1 = u~_1 + u~_2, g_2 = u~_2 of the
+    UNNORMALISED products."""
+    D = np.array([[[0.0, 2 * LN2]], [[LN2, LN2]], [[2 * LN2, 0.0]]])
+    s = np.array([0.2, 0.05])                            # levels 1, 2
+    # iteration 1: q = 0, u = 1/3
+    ut = [[1 / 3, 1 / 12], [1 / 6, 1 / 6], [1 / 12, 1 / 3]]
+    g1 = [ut[1][0] + ut[2][0], ut[1][1] + ut[2][1]]                 # 1/4, 1/2
+    g2 = ut[2]
+    q1, act1 = _clip(-STEP_HAND * (g1[1] - g1[0]), s[0])           # -1/16
+    q2, act2 = _clip(-STEP_HAND * (g2[1] - g2[0]), s[1])           # -1/16 -> -0.05
+    assert (q1, act1, q2, act2) == (-0.0625, False, -0.05, True)
+    a = [sum(ut[L][k] for L in range(3)) for k in range(2)]        # 7/12, 7/12
+    un = [[ut[L][k] / a[k] for k in range(2)] for L in range(3)]   # 4/7 1/7, 2/7 2/7, 1/7 4/7
+    u, q = orc.ishikawa_init((1, 2), 2)
+    orc.ishikawa_iterate(D, u, q, 1, C_HAND, TAU_HAND, s_level=s, grad_source=orc.PAPER_LITERAL)
+    assert np.abs(u[:, 0] - un).max() <= 1e-15
+    assert np.array_equal(q[:, 0, 0], [[q1, 0.0], [q2, 0.0]]) and not np.any(q[:, 1])
+    # iteration 2
+    e1, e2 = [q1, -q1], [q2, -q2]                        # div q_1, div q_2
+    d = [[D[0, 0, k] for k in range(2)],
+         [D[1, 0, k] + e1[k] for k in range(2)],
+         [D[2, 0, k] + e1[k] + e2[k] for k in range(2)]]
+    ut = [[un[L][k] * math.exp(-d[L][k]) for k in range(2)] for L in range(3)]
+    g1 = [ut[1][k] + ut[2][k] for k in range(2)]
+    g2 = ut[2]
+    q1, _ = _clip(q1 - STEP_HAND * (g1[1] - g1[0]), s[0])
+    q2, _ = _clip(q2 - STEP_HAND * (g2[1] - g2[0]), s[1])
+    a = [sum(ut[L][k] for L in range(3)) for k in range(2)]
+    u_hand = np.array([[ut[L][k] / a[k] for k in range(2)] for L in range(3)])
+    orc.ishikawa_iterate(D, u, q, 1, C_HAND, TAU_HAND, s_level=s, grad_source=orc.PAPER_LITERAL)
+    assert np.abs(u[:, 0] - u_hand).max() <= 1e-15
+    assert np.abs(q[:, 0, 0] - [[q1, 0.0], [q2, 0.0]]).max() <= 1e-15 and not np.any(q[:, 1])
+    un2, qn2 = orc.ishikawa_init((1, 2), 2)
+    orc.ishikawa_iterate(D, un2, qn2, 2, C_HAND, TAU_HAND, s_level=s, grad_source=orc.NORMALISED)
+    assert np.abs(qn2[0, 0, 0, 0] - q1) > 1e-2
