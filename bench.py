@@ -12,7 +12,8 @@ are larger than L2, so no flush is needed between steps.
 
 Multi-GPU (under torchrun): every rank solves its own independent volume
 (weak scaling, no collective on the data path).  --impl reference times the
-FP64 CPU oracle on the host cores (rank 0 only).
+FP64 CPU oracle on the host cores doing the same steps on the same full
+volume (rank 0 only).
 """
 import argparse
 import hashlib
@@ -34,11 +35,14 @@ CONFIGS = {
     "potts3d": ((256, 256, 256), 8, "potts3d", 0, 0),
     "potts3d_inplace": ((256, 256, 256), 8, "potts3d", 1, 0),
     "potts3d_bf16": ((256, 256, 256), 8, "potts3d", 0, 1),
+    "potts3d_f16": ((256, 256, 256), 8, "potts3d", 0, 2),
     "hmf": ((192, 192, 192), 12, "hmf", 0, 0),
     "hmf_bf16": ((192, 192, 192), 12, "hmf", 0, 1),
+    "hmf_f16": ((192, 192, 192), 12, "hmf", 0, 2),
     "dagmf_batched": (None, 10, "dagmf_batch", 0, 0),
     "ishikawa": ((256, 256, 256), 8, "ishikawa", 0, 0),
     "continuation": ((128, 128, 128), 8, "potts3d", 0, 0),
+    "potts3d_solve": ((256, 256, 256), 8, "potts3d", 0, 0),
     "fullflow": ((256, 256, 256), 8, "potts3d", 1, 0),
     "diff": ((128, 128, 128), 6, "potts3d", 0, 0),
     "capacity": ((512, 512, 512), 8, "potts3d", 1, 0),
@@ -59,6 +63,7 @@ def parse():
     ap.add_argument("--dims", type=int, default=0, help="cube edge override (profiling of small cases)")
     ap.add_argument("--volumes", type=int, default=32, help="volumes of the batched workload (profiling of small cases)")
     ap.add_argument("--zc", type=int, default=0, help="z-chunk length instead of the tuned one (profiling of small cases)")
+    ap.add_argument("--kernel", default="", help="kernel family instead of the most specialised one (comparisons)")
     return ap.parse_args()
 
 
@@ -225,27 +230,68 @@ def cpu_oracle_sample(cfg, min_seconds=10.0, max_iters=1000, zslab=64, seed=2000
                       % (its, "1" if flat else "2", slab[0], slab[1], slab[2], p.n_nodes, dt)}
 
 
+def metric_name(cfg):
+    """The metric string of a workload, shared by both arms."""
+    return ("voxel-label updates/s, 3-D Potts 256^3 x 8 labels" if cfg == "potts3d" else
+            "voxel-label updates/s (%s)" % cfg)
+
+
 def run_reference(args, rank, world):
+    """The FP64 oracle on the host cores, as it stands, doing exactly the work
+    of one GPU step per step: ITERS_PER_STEP iterations of Algorithm 1 / 2 on
+    the full volume of the same workload, the last preceded by E and P of its
+    input (the gap check).  ms_per_step is the measured wall time of that
+    work; rank 0 only (other ranks exit without work)."""
     if rank != 0:
         return
+    import oracle
     cfg = args.config
-    shape, nl, _, _, _ = CONFIGS[cfg]
-    samples = []
-    for s in range(args.warmup + args.steps):
-        r = cpu_oracle_sample(cfg, min_seconds=0.0, max_iters=1, zslab=32)
-        if s >= args.warmup:
-            samples.append(r)
-    vals = [r["value"] for r in samples]
-    v = statistics.median(vals)
-    nodes = nl if CONFIGS[cfg][2] == "potts3d" else 15
-    vlu_step = ITERS_PER_STEP * int(np.prod(shape)) * nodes
-    line = {"impl": "reference", "metric": "voxel-label updates/s (%s)" % cfg, "value": v, "unit": "VLU/s",
+    if cfg not in ("potts3d", "potts3d_inplace", "potts3d_bf16", "hmf", "hmf_bf16", "ishikawa"):
+        print(json.dumps({"impl": "reference", "unavailable": "the oracle arm covers the single-volume workloads only"}))
+        return
+    shape, nl, gen, _, _ = CONFIGS[cfg]
+    if args.dims:
+        shape = (args.dims,) * 3
+    prob = make_problem(cfg, seed=rank_seed(0), shape=shape)
+    D = prob.D.astype(np.float64)
+    S = None if prob.S_field is None else prob.S_field.astype(np.float64)
+    sn = None if prob.s_node is None else prob.s_node.astype(np.float64)
+    flat = gen == "potts3d"
+    if flat:
+        u, q = oracle.potts_init(prob.spatial, prob.n_leaf)
+    else:
+        dag = oracle.Dag(prob.n_nodes, prob.edges)
+        u, q = oracle.dag_init(prob.spatial, dag)
+
+    def step():
+        if flat:
+            oracle.potts_iterate(D, u, q, ITERS_PER_STEP - 1, prob.c, prob.tau, S_field=S, s_node=sn)
+            oracle.potts_energy(D, u, q, S_field=S, s_node=sn)
+            oracle.potts_iterate(D, u, q, 1, prob.c, prob.tau, S_field=S, s_node=sn)
+        else:
+            oracle.dag_iterate(dag, D, u, q, ITERS_PER_STEP - 1, prob.c, prob.tau, S_field=S, s_node=sn)
+            oracle.dag_energy(dag, D, u, q, S_field=S, s_node=sn)
+            oracle.dag_iterate(dag, D, u, q, 1, prob.c, prob.tau, S_field=S, s_node=sn)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    elapsed = time.perf_counter() - t0
+    vlu_step = ITERS_PER_STEP * int(np.prod(shape)) * prob.n_nodes
+    v = args.steps * vlu_step / elapsed
+    sample = ("each step: %d FP64 iterations of Algorithm %s on the full %s volume (%d nodes), the last preceded "
+              "by E and P of its input" % (ITERS_PER_STEP, "1" if flat else "2", "x".join(map(str, shape)),
+                                           prob.n_nodes))
+    line = {"impl": "reference", "metric": metric_name(cfg), "value": v, "unit": "VLU/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * vlu_step / v, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": cfg, "dims": list(shape), "labels": nl},
-            "cpu_baseline": {"value": v, "unit": "VLU/s", "cores": samples[0]["cores"], "kind": "oracle",
-                             "sample": "each step: " + samples[0]["sample"].split(", ")[0]},
+            "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded sphere phantom)",
+            "config": {"workload": cfg, "dims": list(shape), "labels": prob.n_leaf, "nodes": prob.n_nodes,
+                       "iters_per_step": ITERS_PER_STEP, "c": prob.c, "tau": prob.tau},
+            "cpu_baseline": {"value": v, "unit": "VLU/s", "cores": oracle.threads(), "kind": "oracle",
+                             "sample": sample},
             "e2e": {"value": v, "unit": "VLU/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -295,7 +341,8 @@ def run_batched(args, rank, world):
     del b
     torch.cuda.empty_cache()
     # the plain FP32 form on the same volumes: one single-problem solver per
-    # volume (fused TMA DAG kernel), stepped one after another on the stream
+    # volume (each on its most specialised fused kernel), stepped one after
+    # another on the stream
     singles = [pfm.Problem(p["D"], S_field=p["S_field"], s_node=p["s_node"], n_nodes=p["n_nodes"],
                            edges=p["edges"], c=0.5, tau=0.11, stream=stream.cuda_stream) for p in probs]
     for _ in range(args.warmup):
@@ -312,11 +359,12 @@ def run_batched(args, rank, world):
     s1.record(stream)
     torch.cuda.synchronize()
     single_elapsed = s0.elapsed_time(s1) / 1e3
+    single_kernels = sorted({sp.variant for sp in singles})
     for sp in singles:
         sp.close()
     singles_line = {"value": args.steps * vlu_step / single_elapsed, "unit": "VLU/s",
                     "ms_per_step": 1e3 * single_elapsed / args.steps,
-                    "kernel": "fused_dag_tma_kernel, one problem per volume",
+                    "kernel": "%s, one problem per volume" % "/".join(single_kernels),
                     "batched_over_singles": single_elapsed / elapsed}
     line = {"metric": "voxel-label updates/s (dagmf_batched)", "value": args.steps * vlu_step / elapsed, "unit": "VLU/s",
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps,
@@ -325,9 +373,11 @@ def run_batched(args, rank, world):
                        "iters_per_step": ITERS_PER_STEP, "tuned_zc": zc, "tuned_grid": grid,
                        "kernel_variant": variant,
                        "shapes": [list(p.spatial) for p in vols]},
-            "roofline": {"bound": "hbm", "kernel": {"batched_tma_dag": "batched_dag_tma_kernel"}.get(variant, "batched_step_kernel"), "achieved": achieved, "peak": peak,
+            "roofline": {"bound": "hbm", "kernel": {"batched_tma_dag": "batched_dag_tma_kernel",
+                                                    "batched_tma_dag4": "batched_dag4_tma_kernel"}.get(variant, "batched_step_kernel"),
+                         "achieved": achieved, "peak": peak,
                          "unit": "GB/s", "frac": achieved / peak, "peak_source": "measured",
-                         "traffic": load_traffic("dagmf_batched") if (variant == "batched_tma_dag" and len(vols) == 32) else None,
+                         "traffic": load_traffic("dagmf_batched") if len(vols) == 32 else None,
                          "algorithmic_bytes_per_launch": alg,
                          "kernel_ms_per_launch": it_ms},
             "gpu_launches": launches, "clocks": clk.summary(), "plain_fp32_singles": singles_line}
@@ -362,6 +412,41 @@ def run_continuation(args):
         gp.close()
     print(json.dumps({"metric": "iterations to relative gap 1e-4 (continuation)", "config": {"workload": "potts3d 128^3 x 8"},
                       "results": out}), flush=True)
+
+
+def run_solve(args):
+    """The 3-D Potts workload's stopping rule end to end: 500 fixed
+    iterations, then the relative primal-dual gap (E - P)/|E| checked every
+    10 iterations until it is <= 1e-4 (pfm_run_to_gap), from the initial
+    state; reports the iteration count and the device time (CUDA events),
+    median of three solves."""
+    import torch
+    import paper_1501_07844_gb300 as pfm
+    prob = make_problem("potts3d_solve", seed=2000)
+    D = torch.from_numpy(prob.D).cuda()
+    S = torch.from_numpy(prob.S_field).cuda()
+    stream = torch.cuda.current_stream()
+    gp = pfm.Problem(D, S_field=S, c=prob.c, tau=prob.tau, check_every=10, gap_tol=1e-4, stream=stream.cuda_stream)
+    zc = gp.tune(3)
+    runs = []
+    for rep in range(3):
+        gp.reset()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        gp.iterate(500)
+        it, gap, ok = gp.run_to_gap(20000)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        runs.append({"iterations": 500 + it, "rel_gap": gap, "converged": ok, "ms": e0.elapsed_time(e1)})
+    E, P = gp.energy()
+    gp.close()
+    ms = sorted(r["ms"] for r in runs)[1]
+    print(json.dumps({"metric": "time to the stopping rule (500 iterations, then gap <= 1e-4 every 10)",
+                      "config": {"workload": "potts3d 256^3 x 8", "tuned_zc": zc},
+                      "results": {"iterations": runs[0]["iterations"], "rel_gap": runs[0]["rel_gap"],
+                                  "converged": runs[0]["converged"], "ms_median": ms, "runs": runs,
+                                  "E": E, "P": P}}), flush=True)
 
 
 def run_fullflow(args):
@@ -527,6 +612,9 @@ def main():
     if args.config == "fullflow":
         run_fullflow(args)
         return
+    if args.config == "potts3d_solve":
+        run_solve(args)
+        return
     if args.config == "diff":
         run_diff(args)
         return
@@ -554,6 +642,8 @@ def main():
     gp = pfm.Problem(D, S_field=S, s_node=prob.s_node, n_nodes=prob.n_nodes, edges=prob.edges,
                      c=prob.c, tau=prob.tau, schedule=schedule, storage=storage,
                      stream=stream.cuda_stream)
+    if args.kernel:
+        gp.select_kernel(args.kernel)
     # z-chunk length of the plane-marching kernels picked by the autotuner
     # (the trials are discarded: the state starts from the initial one)
     zc = gp.tune(3)
@@ -644,11 +734,13 @@ def main():
     achieved = alg_bytes / (kern_ms / 1e3) / 1e9
     traffic = load_traffic(cfg)
     # 3-D Potts iterations with BF16 storage run the voxel-pair kernel
-    kname = {"fused_tma": "fused_tma_x2_kernel" if (len(shape) == 3 and storage == 1) else "fused_tma_kernel",
+    kname = {"fused_tma": "fused_tma_x2_kernel" if (len(shape) == 3 and storage != 0) else "fused_tma_kernel",
              "fused_tma_dag": "fused_dag_tma_kernel", "fused_tma_ishikawa": "ishikawa_tma_kernel",
+             "fused_tma_tree": "tree_tma_kernel", "fused_tma_dag4": "dag4_tma_kernel",
              "fused": "fused_step_kernel",
              "inplace": "prox_inplace_kernel+flow_inplace_kernel",
              "inplace_tma": "prox_inplace_tma_kernel+flow_inplace_tma_kernel"}.get(gp.variant, gp.variant)
+    gp_variant = gp.variant
 
     gp.close()
     if rank != 0:
@@ -659,15 +751,14 @@ def main():
     if world == 1 and not args.no_cpu_baseline:
         cpu = cpu_oracle_sample(cfg)
     line = {
-        "metric": "voxel-label updates/s, 3-D Potts 256^3 x 8 labels" if cfg == "potts3d" else
-                  "voxel-label updates/s (%s)" % cfg,
+        "metric": metric_name(cfg),
         "value": value, "unit": "VLU/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32" if storage == 0 else "f32 math, bf16 u/q storage",
+        "vs_baseline": None, "dtype": ("f32", "f32 math, bf16 u/q storage", "f32 math, f16 u/q storage")[storage],
         "data": "synthetic (seeded sphere phantom)",
         "config": {"workload": cfg, "dims": list(shape), "labels": prob.n_leaf, "nodes": prob.n_nodes,
                    "iters_per_step": ITERS_PER_STEP, "schedule": "fused" if schedule == 0 else "in-place",
-                   "tuned_zc": zc,
+                   "tuned_zc": zc, "kernel_family": gp_variant,
                    "c": prob.c, "tau": prob.tau, "norm": "iso", "grad_source": "normalised",
                    "l2": "inputs larger than L2 (%.2f GB moved per iteration)" % (alg_bytes / 1e9),
                    "parallelism": "independent volume per GPU" if world > 1 else "single GPU"},

@@ -76,8 +76,14 @@ enum { PFM_NORM_ISO = 0, PFM_NORM_ANISO = 1 };
 enum { PFM_GRAD_NORMALISED = 0, PFM_GRAD_PAPER_LITERAL = 1 };
 
 /* Storage type of the labelling u and the flows q (arithmetic is FP32;
- * D and S are always stored in FP32). */
-enum { PFM_STORAGE_F32 = 0, PFM_STORAGE_BF16 = 1 };
+ * D and S are always stored in FP32).  BF16 keeps FP32's exponent range
+ * with 8 significant bits; F16 has 11 significant bits but its smallest
+ * positive value is 2^-24, below which the multiplicative label update
+ * would store an exact zero that never recovers: with F16 storage every
+ * labelling value is stored as max(u, 2^-24) (a deviation from the method,
+ * at most n_leaf * 2^-24 in the simplex sum), and flows saturate at the
+ * largest finite F16, +-65504. */
+enum { PFM_STORAGE_F32 = 0, PFM_STORAGE_BF16 = 1, PFM_STORAGE_F16 = 2 };
 
 /* PFM_SCHEDULE_FUSED: one kernel per iteration, u and q double-buffered
  * (fewest bytes moved); operands are staged by TMA when the problem allows
@@ -244,12 +250,49 @@ PFM_API pfm_status pfm_readback_wait(pfm_problem* pb);
 PFM_API pfm_status pfm_set_labels(pfm_problem* pb, const float* src);
 PFM_API pfm_status pfm_set_flows(pfm_problem* pb, const float* src);
 
+/* Checkpoint / resume as one caller-held blob (the paper's state between
+ * iterations of Algorithms 1-3 is the pair (u, q); the blob adds what a
+ * resumed run needs to continue exactly: the iteration counter and the
+ * current c, tau, which continuation schedules change).  Layout: a
+ * pfm_state_header of PFM_STATE_HEADER_BYTES bytes, then u and q in the
+ * problem's STORAGE type (F32: 4 bytes, BF16: 2 bytes per value) as dense
+ * arrays in the getters' layouts (u [n_leaf][z][y][x], then q
+ * [n_nodes][ndim][z][y][x]) -- bit for bit what the solver holds.
+ * pfm_get_state: with dst == NULL only writes the blob size to *size;
+ * otherwise *size must be at least that size (PFM_EINVAL otherwise) and the
+ * blob is written to dst (host or device memory).  (sync)
+ * pfm_set_state: imports a blob written by pfm_get_state of a problem with
+ * the same grid, n_leaf, n_nodes and storage (PFM_EINVAL on a size, magic,
+ * version, shape or storage mismatch, before anything is changed): u and q
+ * are copied bit for bit, the iteration counter, c and tau restored, so the
+ * iterations that follow equal those the saved problem would have run.
+ * The data terms D, S are not part of the state.  (sync) */
+#define PFM_STATE_HEADER_BYTES 128
+typedef struct {
+    char magic[8];          /* "PFMSTATE" */
+    int32_t version;        /* PFM_VERSION of the writer */
+    int32_t storage;        /* PFM_STORAGE_* of u and q in the blob */
+    int32_t ndim;
+    int32_t n_leaf;
+    int32_t n_nodes;
+    int32_t reserved0;
+    int64_t dims[3];        /* nx, ny, nz */
+    int64_t iterations;     /* pfm_iterations_done at the save */
+    double c, tau;          /* the step parameters in force at the save */
+    uint8_t reserved[48];   /* zero */
+} pfm_state_header;
+PFM_API pfm_status pfm_get_state(pfm_problem* pb, void* dst, size_t* size);
+PFM_API pfm_status pfm_set_state(pfm_problem* pb, const void* src, size_t size);
+
 /* Problem shape queries. */
 PFM_API pfm_status pfm_shape(const pfm_problem* pb, int* ndim, int64_t dims[3], int* n_leaf, int* n_nodes);
 
 /* Kernel family pfm_iterate launches for this problem: "fused_tma"
- * (TMA-staged fused iteration), "fused" (register-staged fused iteration)
- * or "inplace" (two in-place kernels).  Static string; "" for NULL. */
+ * (TMA-staged fused Potts iteration), "fused_tma_ishikawa",
+ * "fused_tma_tree", "fused_tma_dag" (TMA-staged DAG iterations: Ishikawa
+ * chain, two-level tree, general DAG), "fused" (register-staged fused
+ * iteration), "inplace_tma" or "inplace" (two in-place kernels).  Static
+ * string; "" for NULL. */
 PFM_API const char* pfm_kernel_variant(const pfm_problem* pb);
 
 /* Iterations run since creation or the last reset, and kernels this problem
@@ -282,6 +325,17 @@ PFM_API pfm_status pfm_tune(pfm_problem* pb, int trial_iters, int* zc_out);
  * synchronises the stream).  pfm_chunk_length returns it (-1 for NULL). */
 PFM_API pfm_status pfm_set_chunk_length(pfm_problem* pb, int zc);
 PFM_API int pfm_chunk_length(const pfm_problem* pb);
+
+/* Forces the kernel family of the fused schedule (a launch choice, not part
+ * of the paper's method; the iterates agree to FP32 rounding across
+ * families): "fused_tma" (Potts), "fused_tma_ishikawa" (Ishikawa chains),
+ * "fused_tma_tree" (two-level label trees: source, inner nodes, end-labels),
+ * "fused_tma_dag" (the general TMA-staged DAG kernel) or "fused" (the
+ * register-staged kernel).  pfm_create picks the most specialised family the
+ * problem allows; this call serves comparisons.  Resets the chunk length to
+ * the cost model's choice for the family's tile.  PFM_EUNSUPPORTED if the
+ * problem cannot run the family or uses the in-place schedule. */
+PFM_API pfm_status pfm_select_kernel(pfm_problem* pb, const char* family);
 
 /* Reverse-mode step of one Potts iteration (the paper has no gradient; this differentiates the unrolled iteration of
  * Algorithm 1, NORMALISED gradient source, ISO or ANISO, flat label set).
@@ -393,8 +447,13 @@ PFM_API int64_t pfm_alm_iterations_done(const pfm_alm* m);
  * a device shares that array, so calls that overlap on the GPU (different
  * streams, or threads) race and give wrong results; serialise them.  The
  * first call on each device looks up the array's device address (with that
- * device current); make that first call before any stream capture.
- * Asynchronous on `stream` (a cudaStream_t, NULL = legacy default). */
+ * device current) and keeps it for the life of the process; make that first
+ * call before any stream capture, and do not call this entry point after
+ * cudaDeviceReset or anything else that destroys the device's primary
+ * context (the kept address is then stale).
+ * Asynchronous on `stream` (a cudaStream_t, NULL = legacy default): the
+ * status covers the arguments and the launches only, so a non-finite E or P
+ * is not reported as PFM_ENONFINITE -- it appears as NaN or Inf in out. */
 #define PFM_NOALLOC_MAX_VOXELS 16777216LL
 PFM_API pfm_status pfm_potts_energy_noalloc(int ndim, const int64_t dims[3], int n_labels, const float* u,
                                             const float* q, const float* D, const float* S_field,

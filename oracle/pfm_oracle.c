@@ -8,9 +8,11 @@
  * no blocking or fusion, so that each line can be checked against the paper
  * by eye.  The conventions are listed in pfm_oracle.h.
  *
- * Parity-unpinned part: the ORC_PAPER_LITERAL variant (flow step on the
- * unnormalised labelling) has no independent pin; only its invariants
- * (simplex, capacity) and its S = 0 closed form are pinned.
+ * Parity-unpinned part: the LIMIT POINT of the ORC_PAPER_LITERAL variant
+ * (flow step on the unnormalised labelling), where that iteration stalls
+ * short of the optimum.  Its iterations themselves are pinned by
+ * hand-worked two-voxel examples of Algorithms 1, 2 and 3, its invariants
+ * (simplex, capacity) and its S = 0 closed form.
  */
 #include "pfm_oracle.h"
 

@@ -12,6 +12,7 @@ from .binding import (  # noqa: F401
     ANISO,
     AlmProblem,
     BF16,
+    F16,
     Batch,
     F32,
     FUSED,

@@ -36,6 +36,22 @@ class PottsSolve(torch.autograd.Function):
     @staticmethod
     def backward(ctx, grad_u):
         prob = ctx.prob
+        # the segment states below are read on the problem's stream, which the
+        # forward pass captured; allocating them under that stream makes the
+        # caching allocator reuse their memory only after those reads
+        cur = torch.cuda.current_stream()
+        stream = torch.cuda.ExternalStream(prob.stream) if prob.stream else cur
+        if stream.cuda_stream != cur.cuda_stream:
+            stream.wait_stream(cur)      # grad_u was produced on the caller's stream
+        with torch.cuda.stream(stream):
+            grads = PottsSolve._backward(ctx, grad_u)
+        if stream.cuda_stream != cur.cuda_stream:
+            cur.wait_stream(stream)      # the gradients are consumed there
+        return grads
+
+    @staticmethod
+    def _backward(ctx, grad_u):
+        prob = ctx.prob
         ubar = grad_u.detach().to(torch.float32).contiguous().clone()
         q_shape = (prob.n_nodes, prob.ndim) + prob.spatial
         qbar = torch.zeros(q_shape, dtype=torch.float32, device=ubar.device)

@@ -16,7 +16,7 @@ from . import build as _build
 
 ISO, ANISO = 0, 1
 NORMALISED, PAPER_LITERAL = 0, 1
-F32, BF16 = 0, 1
+F32, BF16, F16 = 0, 1, 2
 FUSED, INPLACE, FUSED_PLAIN = 0, 1, 2
 
 _STATUS = {0: "PFM_OK", 1: "PFM_EINVAL", 2: "PFM_EDAG", 3: "PFM_ENOMEM", 4: "PFM_ECUDA", 5: "PFM_ENONFINITE",
@@ -55,6 +55,8 @@ _SIGS = {
     "pfm_prefetch_data": (C.c_int, [_P, _P, _P]),
     "pfm_commit_data": (C.c_int, [_P]),
     "pfm_get_state_async": (C.c_int, [_P, _P, _P]),
+    "pfm_get_state": (C.c_int, [_P, _P, C.POINTER(C.c_size_t)]),
+    "pfm_set_state": (C.c_int, [_P, _P, C.c_size_t]),
     "pfm_get_argmax_async": (C.c_int, [_P, _P]),
     "pfm_readback_wait": (C.c_int, [_P]),
     "pfm_reset": (C.c_int, [_P]),
@@ -77,6 +79,7 @@ _SIGS = {
     "pfm_selftest_timeout": (C.c_int, [_P]),
     "pfm_set_chunk_length": (C.c_int, [_P, C.c_int]),
     "pfm_chunk_length": (C.c_int, [_P]),
+    "pfm_select_kernel": (C.c_int, [_P, C.c_char_p]),
     "pfm_adjoint_step": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "pfm_adjoint_steps": (C.c_int, [_P, C.c_int, _P, _P, _P, _P, _P, _P, _P]),
     "pfm_batch_create": (C.c_int, [C.c_int, C.c_void_p, C.POINTER(pfm_params), _P, C.POINTER(_P)]),
@@ -305,6 +308,10 @@ class Problem:
     def chunk_length(self, zc):
         check(lib().pfm_set_chunk_length(self._h, int(zc)))
 
+    def select_kernel(self, family):
+        """pfm_select_kernel: force the fused schedule's kernel family."""
+        check(lib().pfm_select_kernel(self._h, family.encode()))
+
     def run_to_gap(self, max_iters):
         it, gap = C.c_int(), C.c_double()
         st = lib().pfm_run_to_gap(self._h, int(max_iters), C.byref(it), C.byref(gap))
@@ -369,6 +376,28 @@ class Problem:
                                                             dtype=torch.float32, device="cuda")
         check(lib().pfm_get_state_async(self._h, _ptr(u_out), _ptr(q_out)))
         return u_out, q_out
+
+    def state_size(self):
+        """Bytes of the checkpoint blob (pfm_get_state with no destination)."""
+        n = C.c_size_t(0)
+        check(lib().pfm_get_state(self._h, None, C.byref(n)))
+        return n.value
+
+    def get_state(self, out=None):
+        """pfm_get_state: the solver state (iteration counter, c, tau, u, q in
+        the storage type) as one blob; a host uint8 numpy array unless `out`
+        (a uint8 numpy array or torch tensor, host or device) is given."""
+        size = self.state_size()
+        if out is None:
+            out = np.empty(size, dtype=np.uint8)
+        n = C.c_size_t(out.nbytes if isinstance(out, np.ndarray) else out.numel() * out.element_size())
+        check(lib().pfm_get_state(self._h, _ptr(out), C.byref(n)))
+        return out
+
+    def set_state(self, blob):
+        """pfm_set_state from a blob written by get_state (host or device)."""
+        n = blob.nbytes if isinstance(blob, np.ndarray) else blob.numel() * blob.element_size()
+        check(lib().pfm_set_state(self._h, _ptr(blob), C.c_size_t(n)))
 
     def set_labels(self, u):
         u = _as_f32(u)

@@ -163,7 +163,8 @@ pfm_status check_params(const pfm_params* p) {
     if (p->norm != PFM_NORM_ISO && p->norm != PFM_NORM_ANISO) return fail(PFM_EINVAL, "bad norm");
     if (p->grad_source != PFM_GRAD_NORMALISED && p->grad_source != PFM_GRAD_PAPER_LITERAL)
         return fail(PFM_EINVAL, "bad grad_source");
-    if (p->storage != PFM_STORAGE_F32 && p->storage != PFM_STORAGE_BF16) return fail(PFM_EINVAL, "bad storage");
+    if (p->storage != PFM_STORAGE_F32 && p->storage != PFM_STORAGE_BF16 && p->storage != PFM_STORAGE_F16)
+        return fail(PFM_EINVAL, "bad storage");
     if (p->schedule != PFM_SCHEDULE_FUSED && p->schedule != PFM_SCHEDULE_INPLACE &&
         p->schedule != PFM_SCHEDULE_FUSED_PLAIN)
         return fail(PFM_EINVAL, "bad schedule");
@@ -293,7 +294,9 @@ namespace {
 // tiles of one z-chunk row of the grid: 32 x 4 for the TMA DAG kernel,
 // 32 x 8 for every other kernel
 long long zc_tiles(const pfm_problem* pb) {
-    const int ty = strcmp(pb->solver->variant(pb->prm.schedule != PFM_SCHEDULE_INPLACE), "fused_tma_dag") == 0
+    const char* v = pb->solver->variant(pb->prm.schedule != PFM_SCHEDULE_INPLACE);
+    const int ty = (strcmp(v, "fused_tma_dag") == 0 || strcmp(v, "fused_tma_tree") == 0 ||
+                    strcmp(v, "fused_tma_dag4") == 0)
                        ? pfm::DTY
                        : pfm::FTY;
     return (long long)((pb->nx + pfm::FTX - 1) / pfm::FTX) * ((pb->ny + ty - 1) / ty);
@@ -522,14 +525,18 @@ static pfm_status create_impl(const pfm_desc* desc, const pfm_params* params, vo
     pb->launches++;
 
     const pfm::ProblemView v = view_of(pb);
-    const bool bf16 = params->storage == PFM_STORAGE_BF16;
+    const int stor = params->storage;
     if (pb->flat) {
         const int ml = potts_bucket(pb->nl);
-        pb->solver = bf16 ? pfm::make_potts_bf16(ml, pb->ndim, v) : pfm::make_potts_f32(ml, pb->ndim, v);
+        pb->solver = stor == PFM_STORAGE_BF16  ? pfm::make_potts_bf16(ml, pb->ndim, v)
+                     : stor == PFM_STORAGE_F16 ? pfm::make_potts_f16(ml, pb->ndim, v)
+                                               : pfm::make_potts_f32(ml, pb->ndim, v);
     } else {
         int ml, mn;
         dag_bucket(pb->nl, pb->nn, &ml, &mn);
-        pb->solver = bf16 ? pfm::make_dag_bf16(ml, mn, pb->ndim, v) : pfm::make_dag_f32(ml, mn, pb->ndim, v);
+        pb->solver = stor == PFM_STORAGE_BF16  ? pfm::make_dag_bf16(ml, mn, pb->ndim, v)
+                     : stor == PFM_STORAGE_F16 ? pfm::make_dag_f16(ml, mn, pb->ndim, v)
+                                               : pfm::make_dag_f32(ml, mn, pb->ndim, v);
     }
     if (!pb->solver) return bail(fail(PFM_EUNSUPPORTED, "no kernel bucket for this problem"));
     // TMA descriptors serve the fused iteration (PFM_SCHEDULE_FUSED only) and
@@ -918,6 +925,88 @@ pfm_status pfm_set_flows(pfm_problem* pb, const float* src) {
     return PFM_OK;
 }
 
+static size_t state_bytes(const pfm_problem* pb) {
+    const size_t es = elem_size(pb->prm.storage);
+    return PFM_STATE_HEADER_BYTES + es * ((size_t)pb->nl * pb->nv + (size_t)pb->nn * pb->ndim * pb->nv);
+}
+
+// Copy rows of nx values of es bytes between a dense array and a pitched one.
+static cudaError_t copy_rows_es(void* dst, int dpitch, const void* src, int spitch, int nx, long long rows, size_t es,
+                                cudaStream_t s) {
+    return cudaMemcpy2DAsync(dst, (size_t)dpitch * es, src, (size_t)spitch * es, (size_t)nx * es, (size_t)rows,
+                             cudaMemcpyDefault, s);
+}
+
+pfm_status pfm_get_state(pfm_problem* pb, void* dst, size_t* size) {
+    if (!pb || !size) return fail(PFM_EINVAL, "NULL argument");
+    const size_t need = state_bytes(pb);
+    if (!dst) {
+        *size = need;
+        return PFM_OK;
+    }
+    if (*size < need) return fail(PFM_EINVAL, "state blob needs %zu bytes, %zu given", need, *size);
+    pfm_state_header h;
+    memset(&h, 0, sizeof h);
+    memcpy(h.magic, "PFMSTATE", 8);
+    h.version = PFM_VERSION;
+    h.storage = pb->prm.storage;
+    h.ndim = pb->ndim;
+    h.n_leaf = pb->nl;
+    h.n_nodes = pb->nn;
+    h.dims[0] = pb->nx;
+    h.dims[1] = pb->ny;
+    h.dims[2] = pb->nz;
+    h.iterations = pb->iters;
+    h.c = pb->prm.c;
+    h.tau = pb->prm.tau;
+    const size_t es = elem_size(pb->prm.storage);
+    unsigned char* out = static_cast<unsigned char*>(dst);
+    const long long zy = (long long)pb->ny * pb->nz;
+    PFM_CUDA(cudaMemcpyAsync(out, &h, sizeof h, cudaMemcpyDefault, pb->stream), "write state header");
+    unsigned char* uo = out + PFM_STATE_HEADER_BYTES;
+    unsigned char* qo = uo + es * (size_t)pb->nl * pb->nv;
+    PFM_CUDA(copy_rows_es(uo, pb->nx, pb->u[pb->cur], pb->px, pb->nx, (long long)pb->nl * zy, es, pb->stream),
+             "copy labels");
+    PFM_CUDA(copy_rows_es(qo, pb->nx, pb->q[pb->cur], pb->px, pb->nx, (long long)pb->nn * pb->ndim * zy, es,
+                          pb->stream),
+             "copy flows");
+    PFM_CUDA(cudaStreamSynchronize(pb->stream), "stream sync");
+    *size = need;
+    return PFM_OK;
+}
+
+pfm_status pfm_set_state(pfm_problem* pb, const void* src, size_t size) {
+    if (!pb || !src) return fail(PFM_EINVAL, "NULL argument");
+    const size_t need = state_bytes(pb);
+    if (size < need) return fail(PFM_EINVAL, "state blob of %zu bytes, this problem's state needs %zu", size, need);
+    pfm_state_header h;
+    PFM_CUDA(cudaMemcpyAsync(&h, src, sizeof h, cudaMemcpyDefault, pb->stream), "read state header");
+    PFM_CUDA(cudaStreamSynchronize(pb->stream), "stream sync");
+    if (memcmp(h.magic, "PFMSTATE", 8) != 0) return fail(PFM_EINVAL, "not a state blob (magic)");
+    if (h.version != PFM_VERSION) return fail(PFM_EINVAL, "state blob version %d, library %d", h.version, PFM_VERSION);
+    if (h.storage != pb->prm.storage) return fail(PFM_EINVAL, "state blob storage %d, problem %d", h.storage,
+                                                  pb->prm.storage);
+    if (h.ndim != pb->ndim || h.n_leaf != pb->nl || h.n_nodes != pb->nn || h.dims[0] != pb->nx ||
+        h.dims[1] != pb->ny || h.dims[2] != pb->nz)
+        return fail(PFM_EINVAL, "state blob shape differs from the problem's");
+    if (h.iterations < 0 || !(h.c > 0) || !isfinite(h.c) || !(h.tau > 0) || !isfinite(h.tau))
+        return fail(PFM_EINVAL, "state blob header out of range");
+    const size_t es = elem_size(pb->prm.storage);
+    const unsigned char* in = static_cast<const unsigned char*>(src);
+    const unsigned char* ui = in + PFM_STATE_HEADER_BYTES;
+    const unsigned char* qi = ui + es * (size_t)pb->nl * pb->nv;
+    const long long zy = (long long)pb->ny * pb->nz;
+    // only the nx columns of each row are written: the row padding keeps its zeros
+    PFM_CUDA(copy_rows_es(pb->u[pb->cur], pb->px, ui, pb->nx, pb->nx, (long long)pb->nl * zy, es, pb->stream),
+             "copy labels");
+    PFM_CUDA(copy_rows_es(pb->q[pb->cur], pb->px, qi, pb->nx, pb->nx, (long long)pb->nn * pb->ndim * zy, es,
+                          pb->stream),
+             "copy flows");
+    PFM_CUDA(cudaStreamSynchronize(pb->stream), "stream sync");
+    pb->iters = h.iterations;
+    return pfm_set_step(pb, h.c, h.tau);
+}
+
 pfm_status pfm_shape(const pfm_problem* pb, int* ndim, int64_t dims[3], int* n_leaf, int* n_nodes) {
     if (!pb) return fail(PFM_EINVAL, "NULL problem");
     if (ndim) *ndim = pb->ndim;
@@ -1059,7 +1148,8 @@ struct pfm_batch {
     int sms = 0;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     int64_t launches = 0;
-    bool tma = false;  // members run the TMA-staged DAG kernel
+    bool tma = false;   // members run a TMA-staged DAG kernel
+    bool dag4 = false;  // ... the four-inner-node one
 };
 
 namespace {
@@ -1155,21 +1245,34 @@ pfm_status pfm_batch_create(int n, const pfm_desc* descs, const pfm_params* para
         }
         b->members.push_back(m);
     }
-    const bool bf16 = params->storage == PFM_STORAGE_BF16;
+    const int stor = params->storage;
     // DAG members on the TMA-staged kernel when every member fits it (the
     // default schedule); PFM_SCHEDULE_FUSED_PLAIN keeps the register-staged one
     if (any_dag && params->schedule == PFM_SCHEDULE_FUSED) {
-        b->runner = bf16 ? pfm::make_batch_dag_tma_bf16(b->members.data(), n, ndim)
-                         : pfm::make_batch_dag_tma_f32(b->members.data(), n, ndim);
+        // the four-inner-node kernel when every member has at most four
+        // non-end-label nodes, else the general TMA DAG kernel
+        b->runner = stor == PFM_STORAGE_BF16  ? pfm::make_batch_dag4_tma_bf16(b->members.data(), n, ndim)
+                    : stor == PFM_STORAGE_F16 ? pfm::make_batch_dag4_tma_f16(b->members.data(), n, ndim)
+                                              : pfm::make_batch_dag4_tma_f32(b->members.data(), n, ndim);
+        b->dag4 = b->runner != nullptr;
+        if (!b->runner)
+            b->runner = stor == PFM_STORAGE_BF16  ? pfm::make_batch_dag_tma_bf16(b->members.data(), n, ndim)
+                        : stor == PFM_STORAGE_F16 ? pfm::make_batch_dag_tma_f16(b->members.data(), n, ndim)
+                                                  : pfm::make_batch_dag_tma_f32(b->members.data(), n, ndim);
         b->tma = b->runner != nullptr;
     }
     if (!b->runner && !any_dag) {
         const int ml = potts_bucket(maxl);
-        b->runner = bf16 ? pfm::make_batch_potts_bf16(ml, ndim) : pfm::make_batch_potts_f32(ml, ndim);
+        b->runner = stor == PFM_STORAGE_BF16  ? pfm::make_batch_potts_bf16(ml, ndim)
+                    : stor == PFM_STORAGE_F16 ? pfm::make_batch_potts_f16(ml, ndim)
+                                              : pfm::make_batch_potts_f32(ml, ndim);
     } else if (!b->runner) {
         int ml, mn;
         dag_bucket(maxl, maxn, &ml, &mn);
-        if (ml) b->runner = bf16 ? pfm::make_batch_dag_bf16(ml, mn, ndim) : pfm::make_batch_dag_f32(ml, mn, ndim);
+        if (ml)
+            b->runner = stor == PFM_STORAGE_BF16  ? pfm::make_batch_dag_bf16(ml, mn, ndim)
+                        : stor == PFM_STORAGE_F16 ? pfm::make_batch_dag_f16(ml, mn, ndim)
+                                                  : pfm::make_batch_dag_f32(ml, mn, ndim);
     }
     if (!b->runner) {
         batch_free(b);
@@ -1195,7 +1298,7 @@ int pfm_batch_size(const pfm_batch* b) { return b ? (int)b->probs.size() : 0; }
 
 const char* pfm_batch_kernel_variant(const pfm_batch* b) {
     if (!b) return "";
-    return b->tma ? "batched_tma_dag" : "batched";
+    return b->dag4 ? "batched_tma_dag4" : b->tma ? "batched_tma_dag" : "batched";
 }
 
 pfm_status pfm_batch_member(pfm_batch* b, int index, pfm_problem** out) {
@@ -1216,11 +1319,11 @@ pfm_status pfm_batch_iterate(pfm_batch* b, int n_iters) {
             cudaError_t e = cudaSuccess;
             for (int i = 0; i < kGraphIters && e == cudaSuccess; ++i) e = b->runner->launch((parity + i) & 1, b->grid, b->stream);
             cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
-            if (e != cudaSuccess) return cuda_fail(e, "graph capture");
+            if (e == cudaSuccess && e2 == cudaSuccess) e = cudaGraphInstantiate(&b->graph[parity], g, 0);
+            // the captured graph is released on every path (instantiated or not)
+            if (g) cudaGraphDestroy(g);
             if (e2 != cudaSuccess) return cuda_fail(e2, "graph capture");
-            e = cudaGraphInstantiate(&b->graph[parity], g, 0);
-            cudaGraphDestroy(g);
-            if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");
+            if (e != cudaSuccess) return cuda_fail(e, "graph capture / instantiate");
         }
         while (left >= kGraphIters) {
             PFM_CUDA(cudaGraphLaunch(b->graph[parity], b->stream), "graph launch");
@@ -1363,6 +1466,16 @@ pfm_status pfm_set_chunk_length(pfm_problem* pb, int zc) {
 }
 
 int pfm_chunk_length(const pfm_problem* pb) { return pb ? pb->zc : -1; }
+
+pfm_status pfm_select_kernel(pfm_problem* pb, const char* family) {
+    if (!pb || !family) return fail(PFM_EINVAL, "NULL argument");
+    if (pb->prm.schedule == PFM_SCHEDULE_INPLACE)
+        return fail(PFM_EUNSUPPORTED, "kernel families are selectable for the fused schedule only");
+    if (!pb->solver->select(family))
+        return fail(PFM_EUNSUPPORTED, "kernel family '%s' cannot run this problem", family);
+    // the chunk-length model depends on the family's tile
+    return pfm_set_chunk_length(pb, model_zc(zc_tiles(pb), pb->nz, device_sms()));
+}
 
 // ---------------------------------------------------------------------------
 // Explicit-flow ("full-flow") augmented-Lagrangian solver (comparison path).

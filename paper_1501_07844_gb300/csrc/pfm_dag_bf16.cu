@@ -25,4 +25,10 @@ BatchBase* make_batch_dag_tma_bf16(const BatchMember* m, int n, int dim) {
     return nullptr;
 }
 
+BatchBase* make_batch_dag4_tma_bf16(const BatchMember* m, int n, int dim) {
+    if (dim == 3) return BatchDag4Tma<3, __nv_bfloat16>::fits(m, n) ? new BatchDag4Tma<3, __nv_bfloat16>() : nullptr;
+    if (dim == 2) return BatchDag4Tma<2, __nv_bfloat16>::fits(m, n) ? new BatchDag4Tma<2, __nv_bfloat16>() : nullptr;
+    return nullptr;
+}
+
 }  // namespace pfm

@@ -25,4 +25,10 @@ BatchBase* make_batch_dag_tma_f32(const BatchMember* m, int n, int dim) {
     return nullptr;
 }
 
+BatchBase* make_batch_dag4_tma_f32(const BatchMember* m, int n, int dim) {
+    if (dim == 3) return BatchDag4Tma<3, float>::fits(m, n) ? new BatchDag4Tma<3, float>() : nullptr;
+    if (dim == 2) return BatchDag4Tma<2, float>::fits(m, n) ? new BatchDag4Tma<2, float>() : nullptr;
+    return nullptr;
+}
+
 }  // namespace pfm

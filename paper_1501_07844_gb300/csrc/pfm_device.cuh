@@ -2,13 +2,13 @@
 //
 // Layouts are label-major structure-of-arrays, x fastest, as in pfm.h, with
 // rows padded to a pitch px >= nx (a multiple of 8 elements, so that every
-// row of the FP32 and BF16 arrays starts on a 16-byte boundary, as TMA
-// requires):
+// row of the FP32 and 16-bit (BF16, F16) arrays starts on a 16-byte
+// boundary, as TMA requires):
 //   u[leaf][n], D[leaf][n], q[node][comp][n], S[n];  n = px*ny*nz slots,
 //   voxel (x, y, z) at (z*ny + y)*px + x; slots x >= nx are padding that no
 //   kernel reads as a voxel.
 // A warp covers consecutive x, so every per-label load or store of a warp
-// is one contiguous 128-byte (FP32) or 64-byte (BF16) segment.
+// is one contiguous 128-byte (FP32) or 64-byte (BF16, F16) segment.
 //
 // One iteration at voxel x (Algorithm 1 / Algorithm 2):
 //   e_A   = div q_A (+ D_A on end-labels)                    (Section 3.3, d_L)
@@ -23,8 +23,11 @@
 #pragma once
 
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <type_traits>
 
 namespace pfm {
 
@@ -71,6 +74,7 @@ template <> __device__ __forceinline__ float ldv<float>(const float* p) { return
 template <> __device__ __forceinline__ float ldv<__nv_bfloat16>(const __nv_bfloat16* p) {
     return __bfloat162float(__ldg(p));
 }
+template <> __device__ __forceinline__ float ldv<__half>(const __half* p) { return __half2float(__ldg(p)); }
 // (x, y, z) of slot i of a volume with rows of `row` slots (nx, or the pitch
 // px) and ny rows per plane.  32-bit divisions whenever the index fits: the
 // 64-bit division is a long instruction sequence, and a per-element kernel
@@ -93,6 +97,23 @@ template <typename T> __device__ __forceinline__ void stv(T* p, float v);
 template <> __device__ __forceinline__ void stv<float>(float* p, float v) { *p = v; }
 template <> __device__ __forceinline__ void stv<__nv_bfloat16>(__nv_bfloat16* p, float v) {
     *p = __float2bfloat16_rn(v);
+}
+// F16 storage: values beyond the largest finite F16 (65504) are stored as
+// +-65504 (a capacity that large bounds no flow of a labelling in [0, 1]).
+constexpr float F16_MAX = 65504.0f;
+template <> __device__ __forceinline__ void stv<__half>(__half* p, float v) {
+    *p = __float2half_rn(fminf(fmaxf(v, -F16_MAX), F16_MAX));
+}
+
+// Store of a labelling value.  With F16 storage a value below the smallest
+// positive F16 subnormal (2^-24) would round to zero, and the multiplicative
+// label update never brings a zero back (FP32 and FP64 reach zero only some
+// hundred orders of magnitude later): u is stored as max(u, 2^-24) there.
+// This floor is a deviation from the method, stated with its results.
+constexpr float F16_U_FLOOR = 5.9604644775390625e-08f;
+template <typename T> __device__ __forceinline__ void stu(T* p, float v) {
+    if constexpr (std::is_same<T, __half>::value) v = fmaxf(v, F16_U_FLOOR);
+    stv<T>(p, v);
 }
 
 // Projection onto {|y| <= s}: Euclidean ball (ISO) or box (ANISO).  A zero
@@ -258,7 +279,7 @@ __device__ __forceinline__ void fused_tile(const StepArgs<MAXL, MAXN>& a, int bx
             if (owner && p < z1) {
 #pragma unroll
                 for (int j = 0; j < MAXL; ++j)
-                    if (j < a.nl) stv<T>(uout + (long long)j * n + i, u[j]);
+                    if (j < a.nl) stu<T>(uout + (long long)j * n + i, u[j]);
             }
         } else {
 #pragma unroll
@@ -395,7 +416,7 @@ prox_inplace_kernel(const StepArgs<MAXL, MAXN> a) {
     const bool ok = label_prox<MAXL, MAXN, IS_DAG>(a, e, Dv, uv, g, nrm);
 #pragma unroll
     for (int j = 0; j < MAXL; ++j)
-        if (j < a.nl) stv<T>(u + (long long)j * n + i, uv[j]);
+        if (j < a.nl) stu<T>(u + (long long)j * n + i, uv[j]);
     if (a.literal) a.abuf[i] = nrm;
     if (!ok) atomicOr(a.flags, FLAG_NONFINITE);
 }

@@ -29,7 +29,7 @@ template <typename T>
 __global__ void init_labels_kernel(T* u, int nl, long long n) {
     const long long i = (long long)blockIdx.x * NT + threadIdx.x;
     if (i >= (long long)nl * n) return;
-    stv<T>(u + i, 1.0f / nl);
+    stu<T>(u + i, 1.0f / nl);
 }
 
 // Thresholding of the relaxed labelling: index of the largest u_L, ties to
@@ -79,7 +79,7 @@ __global__ void set_labels_kernel(const float* src, int nl, long long nv, int nx
         return;
     }
     const long long pi = slot(i, nx, px);
-    for (int j = 0; j < nl; ++j) stv<T>(dst + (long long)j * n + pi, src[(long long)j * nv + i]);
+    for (int j = 0; j < nl; ++j) stu<T>(dst + (long long)j * n + pi, src[(long long)j * nv + i]);
 }
 
 // Checkpoint import of flows: zero normal flux at the last index of each
@@ -111,7 +111,7 @@ __global__ void set_flows_kernel(const float* src, int nn, int nx, int ny, int n
         // a flow that is feasible up to the rounding of the storage type (e.g.
         // read back from a solver) is kept bit for bit; anything outside is
         // scaled onto the ball
-        const float slack = sizeof(T) == 4 ? 1.000001f : 1.02f;
+        const float slack = sizeof(T) == 4 ? 1.000001f : 1.02f;  // 16-bit storage: a few ulps
         float r2 = 0.f;
 #pragma unroll
         for (int k = 0; k < DIM; ++k) r2 = fmaf(yv[k], yv[k], r2);
@@ -177,60 +177,66 @@ __global__ void energy_final_kernel(const double* partial, int blocks, double* o
 
 }  // namespace
 
-#define PFM_BY_STORAGE(storage, CALL_F32, CALL_BF16) \
-    do {                                             \
-        if ((storage) == 0) {                        \
-            CALL_F32;                                \
-        } else {                                     \
-            CALL_BF16;                               \
-        }                                            \
-    } while (0)
+// Runs f(Tag<T>{}) with T the storage type of u and q (0 FP32, 1 BF16, 2 F16).
+template <typename T> struct Tag { using type = T; };
+template <typename F> void by_storage(int storage, F&& f) {
+    if (storage == 0)
+        f(Tag<float>{});
+    else if (storage == 1)
+        f(Tag<__nv_bfloat16>{});
+    else
+        f(Tag<__half>{});
+}
 
 cudaError_t launch_init_labels(void* u, int storage, int nl, long long n, cudaStream_t s) {
     const unsigned b = blocks_for((long long)nl * n);
-    PFM_BY_STORAGE(storage, (init_labels_kernel<float><<<b, NT, 0, s>>>((float*)u, nl, n)),
-                   (init_labels_kernel<__nv_bfloat16><<<b, NT, 0, s>>>((__nv_bfloat16*)u, nl, n)));
+    by_storage(storage, [&](auto tag) {
+        using T = typename decltype(tag)::type;
+        init_labels_kernel<T><<<b, NT, 0, s>>>((T*)u, nl, n);
+    });
     return cudaGetLastError();
 }
 
 cudaError_t launch_argmax(const void* u, int storage, int nl, long long n, int nx, int px, long long nv, int* out,
                           cudaStream_t s) {
     const unsigned b = blocks_for(nv);
-    PFM_BY_STORAGE(storage, (argmax_kernel<float><<<b, NT, 0, s>>>((const float*)u, nl, n, nx, px, nv, out)),
-                   (argmax_kernel<__nv_bfloat16><<<b, NT, 0, s>>>((const __nv_bfloat16*)u, nl, n, nx, px, nv, out)));
+    by_storage(storage, [&](auto tag) {
+        using T = typename decltype(tag)::type;
+        argmax_kernel<T><<<b, NT, 0, s>>>((const T*)u, nl, n, nx, px, nv, out);
+    });
     return cudaGetLastError();
 }
 
 cudaError_t launch_to_f32(const void* src, int storage, long long rows, int nx, int px, float* dst, cudaStream_t s) {
     const long long count = rows * nx;
     const unsigned b = blocks_for(count);
-    PFM_BY_STORAGE(storage, (to_f32_kernel<float><<<b, NT, 0, s>>>((const float*)src, count, nx, px, dst)),
-                   (to_f32_kernel<__nv_bfloat16><<<b, NT, 0, s>>>((const __nv_bfloat16*)src, count, nx, px, dst)));
+    by_storage(storage, [&](auto tag) {
+        using T = typename decltype(tag)::type;
+        to_f32_kernel<T><<<b, NT, 0, s>>>((const T*)src, count, nx, px, dst);
+    });
     return cudaGetLastError();
 }
 
 cudaError_t launch_set_labels(const float* src, int storage, int nl, long long nv, int nx, int px, long long n,
                               void* dst, unsigned* flags, cudaStream_t s) {
     const unsigned b = blocks_for(nv);
-    PFM_BY_STORAGE(storage,
-                   (set_labels_kernel<float><<<b, NT, 0, s>>>(src, nl, nv, nx, px, n, (float*)dst, flags)),
-                   (set_labels_kernel<__nv_bfloat16><<<b, NT, 0, s>>>(src, nl, nv, nx, px, n, (__nv_bfloat16*)dst,
-                                                                      flags)));
+    by_storage(storage, [&](auto tag) {
+        using T = typename decltype(tag)::type;
+        set_labels_kernel<T><<<b, NT, 0, s>>>(src, nl, nv, nx, px, n, (T*)dst, flags);
+    });
     return cudaGetLastError();
 }
 
 cudaError_t launch_set_flows(const float* src, int storage, int nn, int ndim, int nx, int ny, int nz, int px,
                              const float* s_node_dev, const float* S, int aniso, void* dst, cudaStream_t s) {
     const dim3 b(blocks_for((long long)nx * ny * nz), (unsigned)nn);  // voxels x nodes (nn <= 16)
-    PFM_BY_STORAGE(storage,
-                   (ndim == 3 ? set_flows_kernel<float, 3><<<b, NT, 0, s>>>(src, nn, nx, ny, nz, px, s_node_dev, S,
-                                                                           aniso, (float*)dst)
-                              : set_flows_kernel<float, 2><<<b, NT, 0, s>>>(src, nn, nx, ny, nz, px, s_node_dev, S,
-                                                                           aniso, (float*)dst)),
-                   (ndim == 3 ? set_flows_kernel<__nv_bfloat16, 3><<<b, NT, 0, s>>>(src, nn, nx, ny, nz, px, s_node_dev,
-                                                                                   S, aniso, (__nv_bfloat16*)dst)
-                              : set_flows_kernel<__nv_bfloat16, 2><<<b, NT, 0, s>>>(src, nn, nx, ny, nz, px, s_node_dev,
-                                                                                   S, aniso, (__nv_bfloat16*)dst)));
+    by_storage(storage, [&](auto tag) {
+        using T = typename decltype(tag)::type;
+        if (ndim == 3)
+            set_flows_kernel<T, 3><<<b, NT, 0, s>>>(src, nn, nx, ny, nz, px, s_node_dev, S, aniso, (T*)dst);
+        else
+            set_flows_kernel<T, 2><<<b, NT, 0, s>>>(src, nn, nx, ny, nz, px, s_node_dev, S, aniso, (T*)dst);
+    });
     return cudaGetLastError();
 }
 

@@ -25,8 +25,10 @@ constexpr long long kMaxBlocks = 65536;              // => at most 16,777,216 vo
 constexpr int kMaxDevices = 64;
 
 // Scratch shared by every call on a device: 2 doubles (E, P) per block, then
-// one word for the non-finite flag of the final reduction.  Every GPU that
-// loads the library holds it (1 MiB) until the process exits.
+// one word the final reduction ORs its non-finite flag into (never read: the
+// call is asynchronous, so a non-finite E or P reaches the caller as NaN or
+// Inf in out).  Every GPU that loads the library holds it (1 MiB) until the
+// process exits.
 static __device__ __align__(256) double g_scratch[2 * kMaxBlocks + 1];
 
 std::mutex g_mu;

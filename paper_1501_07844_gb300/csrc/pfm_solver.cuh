@@ -7,6 +7,8 @@
 
 #include <cuda_runtime.h>
 
+#include <string.h>
+
 #include <algorithm>
 #include <vector>
 
@@ -15,6 +17,8 @@
 #include "pfm_tma_dag.cuh"
 #include "pfm_tma_inplace.cuh"
 #include "pfm_tma_ishikawa.cuh"
+#include "pfm_tma_dag4.cuh"
+#include "pfm_tma_tree.cuh"
 #include "pfm_tma_x2.cuh"
 
 namespace pfm {
@@ -64,6 +68,133 @@ inline bool build_dag_lists(const StepArgs<DMAX, DMAX>& a, int dim, int es, DagL
     return true;
 }
 
+// Two-level label trees (source -> inner nodes -> end-labels), recognised
+// from the path weights W_(A,j) (node A, end-label j): an inner node's row
+// has two or more nonzeros (its end-labels); the own node of end-label j has
+// W = 1 at j only; an end-label under an inner node with no other child
+// shares its one-entry row with that node (the two are interchangeable:
+// same excess, same driving field); one under the source alone has no
+// parent node.  Groups: the inner nodes with their end-labels (at most
+// four each), single-child chains, and the source's own end-labels packed
+// four to a group; at most four groups.  False for anything else (deeper
+// trees, end-labels with two parents) and when three stages of every
+// node's flows do not fit in shared memory.
+inline bool build_tree_shape(const StepArgs<DMAX, DMAX>& a, int dim, int es, TreeShape* ts) {
+    const int nl = a.nl, nn = a.nn;
+    if (nl < 1 || nn > DMAX || nl > DMAX) return false;
+    const TreeTmaLayout lay(nl, nn, dim, es);
+    if (lay.total + 64 > 227 * 1024) return false;
+    int cnt[DMAX] = {0};
+    for (int A = 0; A < nn; ++A)
+        for (int j = 0; j < nl; ++j) cnt[A] += a.W[A][j] != 0.f;
+    int cover[DMAX];  // inner node (>= 2 end-labels) above end-label j, or -1
+    for (int j = 0; j < nl; ++j) cover[j] = -1;
+    bool used[DMAX] = {false};
+    *ts = TreeShape{};
+    int ng = 0;
+    auto add_group = [&](int inner) {
+        if (ng >= TREE_MAXG) return -1;
+        ts->inner[ng] = inner;
+        ts->n[ng] = 0;
+        return ng++;
+    };
+    // inner nodes with two or more end-labels: disjoint supports
+    for (int A = 0; A < nn; ++A) {
+        if (cnt[A] < 2) continue;
+        if (cnt[A] > TREE_FAN) return false;
+        const int g = add_group(A);
+        if (g < 0) return false;
+        used[A] = true;
+        for (int j = 0; j < nl; ++j)
+            if (a.W[A][j] != 0.f) {
+                if (cover[j] >= 0) return false;  // two parents, or nested inner nodes
+                cover[j] = A;
+            }
+    }
+    // the own node of every end-label (and single-child chains)
+    int lnode_of[DMAX], chain_of[DMAX];
+    for (int j = 0; j < nl; ++j) {
+        lnode_of[j] = chain_of[j] = -1;
+        for (int A = 0; A < nn; ++A) {
+            if (cnt[A] != 1 || a.W[A][j] == 0.f) continue;
+            if (lnode_of[j] < 0 && a.W[A][j] == 1.0f)
+                lnode_of[j] = A;
+            else if (chain_of[j] < 0)
+                chain_of[j] = A;
+            else
+                return false;  // a chain of three or more nodes above j
+        }
+        if (lnode_of[j] < 0) return false;
+        if (chain_of[j] >= 0 && cover[j] >= 0) return false;
+        used[lnode_of[j]] = true;
+        if (chain_of[j] >= 0) used[chain_of[j]] = true;
+    }
+    for (int A = 0; A < nn; ++A)
+        if (!used[A]) return false;
+    auto add_leaf = [&](int g, int j, float w) {
+        const int h = ts->n[g]++;
+        ts->leaf[g][h] = j;
+        ts->lnode[g][h] = lnode_of[j];
+        ts->w[g][h] = w;
+    };
+    for (int g = 0; g < ng; ++g)
+        for (int j = 0; j < nl; ++j)
+            if (cover[j] == ts->inner[g]) add_leaf(g, j, a.W[ts->inner[g]][j]);
+    int direct = -1;  // group of end-labels under the source (no parent flow)
+    for (int j = 0; j < nl; ++j) {
+        if (cover[j] >= 0) continue;
+        if (chain_of[j] >= 0) {
+            const int g = add_group(chain_of[j]);
+            if (g < 0) return false;
+            add_leaf(g, j, a.W[chain_of[j]][j]);
+        } else {
+            if (direct < 0 || ts->n[direct] == TREE_FAN) direct = add_group(-1);
+            if (direct < 0) return false;
+            add_leaf(direct, j, 0.f);
+        }
+    }
+    ts->ng = ng;
+    return true;
+}
+
+// DAGs with at most four non-end-label nodes, recognised from the path
+// weights W_(A,j): every end-label j has its own node (a row with W = 1 at j
+// and zero elsewhere; of a single-child chain, whose two rows are equal, one
+// node is taken as the end-label's and the other as an inner node -- they
+// enter the excess and the accumulation alike); every other node is an inner
+// node, at most four, and at most twelve end-labels.  False otherwise, and
+// when three stages of every node's flows do not fit in shared memory.
+inline bool build_dag4_shape(const StepArgs<DMAX, DMAX>& a, int dim, int es, Dag4Shape* sh) {
+    const int nl = a.nl, nn = a.nn;
+    if (nl < 1 || nl > DAG4_MAXL || nn > DMAX) return false;
+    const TreeTmaLayout lay(nl, nn, dim, es);
+    if (lay.total + 64 > 227 * 1024) return false;
+    *sh = Dag4Shape{};
+    bool own[DMAX] = {false};
+    for (int j = 0; j < nl; ++j) {
+        int pick = -1;
+        for (int A = nn - 1; A >= 0 && pick < 0; --A) {
+            if (own[A] || a.W[A][j] != 1.0f) continue;
+            bool single = true;
+            for (int i = 0; i < nl && single; ++i) single = i == j || a.W[A][i] == 0.f;
+            if (single) pick = A;
+        }
+        if (pick < 0) return false;
+        own[pick] = true;
+        sh->lnode[j] = pick;
+    }
+    sh->ni = 0;
+    for (int k = 0; k < DAG4_INNER; ++k) sh->inner[k] = -1;
+    for (int A = 0; A < nn; ++A) {
+        if (own[A]) continue;
+        if (sh->ni == DAG4_INNER) return false;
+        const int k = sh->ni++;
+        sh->inner[k] = A;
+        for (int j = 0; j < nl; ++j) sh->w[j][k] = a.W[A][j];
+    }
+    return true;
+}
+
 // Tensor maps of one parity of a DAG problem: logical extents, pitched
 // strides; the flow box covers the nf flow-carrying nodes.
 // The flow-carrying nodes 0..nf-1 are the N = nl - 1 levels of an Ishikawa
@@ -107,8 +238,8 @@ inline bool encode_ishikawa_maps(const StepArgs<MAXL, MAXN>& a, int es, const vo
 }
 
 inline bool encode_dag_maps(const StepArgs<DMAX, DMAX>& a, int dim, int es, int nf, const void* u, const void* q,
-                            const float* D, const float* S, TmaMaps* m) {
-    const int qbx = FTX + 2 * (16 / es);
+                            const float* D, const float* S, TmaMaps* m, int qbx = 0) {
+    if (qbx == 0) qbx = FTX + 2 * (16 / es);
     const unsigned long long nx = a.nx, ny = a.ny, nz = a.nz, px = a.px;
     const unsigned long long dims_u[4] = {nx, ny, nz, (unsigned long long)a.nl};
     const unsigned long long dims_q[4] = {nx, ny, nz, (unsigned long long)dim * a.nn};
@@ -152,6 +283,40 @@ StepArgs<MAXL, MAXN> make_step_args(const ProblemView& v, int zc) {
     return a;
 }
 
+// The TMA DAG kernels (general, tree) take the arguments of the largest
+// bucket; a problem of a smaller bucket is widened (entries past its counts
+// are zero).
+template <int MAXL, int MAXN>
+StepArgs<DMAX, DMAX> widen_args(const StepArgs<MAXL, MAXN>& a) {
+    static_assert(MAXL <= DMAX && MAXN <= DMAX, "bucket wider than the TMA DAG kernels");
+    StepArgs<DMAX, DMAX> w{};
+    w.u_in = a.u_in;
+    w.u_out = a.u_out;
+    w.q_in = a.q_in;
+    w.q_out = a.q_out;
+    w.D = a.D;
+    w.S = a.S;
+    w.abuf = a.abuf;
+    w.flags = a.flags;
+    w.nx = a.nx;
+    w.ny = a.ny;
+    w.nz = a.nz;
+    w.nl = a.nl;
+    w.nn = a.nn;
+    w.px = a.px;
+    w.literal = a.literal;
+    w.aniso = a.aniso;
+    w.zc = a.zc;
+    w.n = a.n;
+    w.inv_c = a.inv_c;
+    w.ctau = a.ctau;
+    for (int A = 0; A < MAXN; ++A) {
+        w.s_node[A] = a.s_node[A];
+        for (int j = 0; j < MAXL; ++j) w.W[A][j] = a.W[A][j];
+    }
+    return w;
+}
+
 struct SolverBase {
     virtual ~SolverBase() {}
     // One iteration reading (u_in, q_in) and writing (u_out, q_out); for the
@@ -173,6 +338,14 @@ struct SolverBase {
     // TMA-pipelined fused kernel can run on this problem.
     virtual bool prepare_tma(void* const* u, void* const* q, const float* D, const float* S) { return false; }
     bool use_tma = true;  // cleared to force the register-staged fused kernel
+    bool use_tree = true;  // cleared to run a two-level tree on the general TMA DAG kernel
+    bool use_ishi = true;  // cleared to run an Ishikawa chain on the general TMA DAG kernel
+    bool use_dag4 = true;  // cleared to run a DAG with <= 4 inner nodes on the general TMA DAG kernel
+    // Forces the kernel family of the fused schedule ("fused_tma",
+    // "fused_tma_ishikawa", "fused_tma_tree", "fused_tma_dag4",
+    // "fused_tma_dag" or "fused", the register-staged kernel); false if the
+    // problem cannot run it.
+    virtual bool select(const char* name) = 0;
     bool use_tma_inplace = false;  // PFM_SCHEDULE_INPLACE: TMA-staged sweeps where available
     // Name of the kernel family step() launches for the given schedule.
     virtual const char* variant(bool fused) const = 0;
@@ -187,7 +360,7 @@ struct Solver final : SolverBase {
     StepArgs<MAXL, MAXN> base{};
     size_t fused_smem = 0;
     static constexpr bool kTmaCapable = !IS_DAG && MAXL <= 8;
-    static constexpr bool kDagTmaCapable = IS_DAG && MAXL == DMAX && MAXN == DMAX;
+    static constexpr bool kDagTmaCapable = IS_DAG;  // every DAG bucket (arguments widened)
     bool tma_ready = false;
     const void* tma_u[2] = {nullptr, nullptr};
     TmaMaps tma_maps[2];
@@ -195,6 +368,11 @@ struct Solver final : SolverBase {
     DagLists lists{};
     bool ishi_ready = false;  // the DAG is an Ishikawa chain: chain-specialised kernel
     TmaMaps ishi_maps[2];
+    bool tree_ready = false;  // the DAG is a two-level tree: tree-specialised kernel
+    TreeShape tree{};
+    TmaMaps tree_maps[2];     // every node's flows (tree and four-inner-node kernels)
+    bool dag4_ready = false;  // at most four non-end-label nodes: the four-inner-node kernel
+    Dag4Shape dag4{};
     bool inplace_ready = false;
     InplaceMaps inplace_maps{};
 
@@ -242,8 +420,42 @@ struct Solver final : SolverBase {
         }
     }
 
+    template <bool IDX32, int G>
+    cudaError_t launch_tree_g(const StepArgs<DMAX, DMAX>& a, const TmaMaps& m, dim3 grid, cudaStream_t s) {
+        const TreeTmaLayout lay(a.nl, a.nn, DIM, (int)sizeof(T));
+        cudaError_t e = cudaFuncSetAttribute(tree_tma_kernel<DIM, T, IDX32, G>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, lay.total);
+        if (e != cudaSuccess) return e;
+        tree_tma_kernel<DIM, T, IDX32, G><<<grid, DAG_TMA_NT, lay.total, s>>>(a, m, tree);
+        return cudaGetLastError();
+    }
+
     template <bool IDX32>
-    cudaError_t launch_dag(const StepArgs<MAXL, MAXN>& a, const TmaMaps& m, dim3 grid, int smem, cudaStream_t s) {
+    cudaError_t launch_tree(const StepArgs<DMAX, DMAX>& a, const TmaMaps& m, dim3 grid, cudaStream_t s) {
+        if constexpr (kDagTmaCapable) {
+            // the kernel keeps per-group state in registers: compiled for 3 or 4 groups
+            return tree.ng <= 3 ? launch_tree_g<IDX32, 3>(a, m, grid, s) : launch_tree_g<IDX32, 4>(a, m, grid, s);
+        } else {
+            return cudaErrorInvalidValue;
+        }
+    }
+
+    template <bool IDX32>
+    cudaError_t launch_dag4(const StepArgs<DMAX, DMAX>& a, const TmaMaps& m, dim3 grid, cudaStream_t s) {
+        if constexpr (kDagTmaCapable) {
+            const TreeTmaLayout lay(a.nl, a.nn, DIM, (int)sizeof(T));
+            cudaError_t e = cudaFuncSetAttribute(dag4_tma_kernel<DIM, T, IDX32>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, lay.total);
+            if (e != cudaSuccess) return e;
+            dag4_tma_kernel<DIM, T, IDX32><<<grid, DAG_TMA_NT, lay.total, s>>>(a, m, dag4);
+            return cudaGetLastError();
+        } else {
+            return cudaErrorInvalidValue;
+        }
+    }
+
+    template <bool IDX32>
+    cudaError_t launch_dag(const StepArgs<DMAX, DMAX>& a, const TmaMaps& m, dim3 grid, int smem, cudaStream_t s) {
         if constexpr (kDagTmaCapable) {
             cudaError_t e = cudaFuncSetAttribute(fused_dag_tma_kernel<DIM, T, IDX32>,
                                                  cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -260,7 +472,7 @@ struct Solver final : SolverBase {
                             cudaStream_t s) {
         using Lay = TmaLayout<MAXL, DIM, T>;
         if constexpr (DIM == 3 && sizeof(T) == 2) {
-            // 3-D, BF16 storage: voxel pairs with packed FP32 arithmetic (the
+            // 3-D, 16-bit storage: voxel pairs with packed FP32 arithmetic (the
             // one-voxel kernel is issue-bound there; with FP32 storage it is
             // at the bandwidth roof and the pair kernel measured slower)
             cudaError_t e = cudaFuncSetAttribute(fused_tma_x2_kernel<MAXL, T, EXACT, WITH_E, IDX32>,
@@ -269,7 +481,7 @@ struct Solver final : SolverBase {
             fused_tma_x2_kernel<MAXL, T, EXACT, WITH_E, IDX32><<<grid, X2_NT, Lay::total_bytes, s>>>(a, m, partial);
             return cudaGetLastError();
         } else {
-            // the one-voxel kernel (not instantiated for 3-D BF16, which never runs it)
+            // the one-voxel kernel (not instantiated for 3-D 16-bit storage, which never runs it)
             cudaError_t e = cudaFuncSetAttribute(fused_tma_kernel<MAXL, DIM, T, EXACT, WITH_E, IDX32>,
                                                  cudaFuncAttributeMaxDynamicSharedMemorySize, Lay::total_bytes);
             if (e != cudaSuccess) return e;
@@ -314,7 +526,7 @@ struct Solver final : SolverBase {
             }
         }
         if constexpr (IS_DAG && DIM == 3) {
-            if (fused && ishi_ready && use_tma) {
+            if (fused && ishi_ready && use_tma && use_ishi) {
                 const int k = (u_in == tma_u[0]) ? 0 : 1;
                 a.zc = zc < 1 ? 1 : zc;
                 dim3 grid((a.nx + FTX - 1) / FTX, (a.ny + FTY - 1) / FTY, (a.nz + a.zc - 1) / a.zc);
@@ -330,6 +542,24 @@ struct Solver final : SolverBase {
             }
         }
         if constexpr (kDagTmaCapable) {
+            if (fused && tree_ready && use_tma && use_tree) {
+                const int k = (u_in == tma_u[0]) ? 0 : 1;
+                a.zc = zc < 1 ? 1 : zc;
+                dim3 grid((a.nx + FTX - 1) / FTX, (a.ny + DTY - 1) / DTY, (a.nz + a.zc - 1) / a.zc);
+                *launches = 1;
+                const StepArgs<DMAX, DMAX> w = widen_args(a);
+                if ((long long)DIM * a.nn * a.n <= 0xFFFFFFFFll) return launch_tree<true>(w, tree_maps[k], grid, s);
+                return launch_tree<false>(w, tree_maps[k], grid, s);
+            }
+            if (fused && dag4_ready && use_tma && use_dag4) {
+                const int k = (u_in == tma_u[0]) ? 0 : 1;
+                a.zc = zc < 1 ? 1 : zc;
+                dim3 grid((a.nx + FTX - 1) / FTX, (a.ny + DTY - 1) / DTY, (a.nz + a.zc - 1) / a.zc);
+                *launches = 1;
+                const StepArgs<DMAX, DMAX> w = widen_args(a);
+                if ((long long)DIM * a.nn * a.n <= 0xFFFFFFFFll) return launch_dag4<true>(w, tree_maps[k], grid, s);
+                return launch_dag4<false>(w, tree_maps[k], grid, s);
+            }
             if (fused && dag_tma_ready && use_tma) {
                 const int k = (u_in == tma_u[0]) ? 0 : 1;
                 a.zc = zc < 1 ? 1 : zc;
@@ -337,8 +567,9 @@ struct Solver final : SolverBase {
                 dim3 grid((a.nx + FTX - 1) / FTX, (a.ny + DTY - 1) / DTY, (a.nz + a.zc - 1) / a.zc);
                 *launches = 1;
                 // 32-bit slot offsets when every offset of the flow array fits
-                if ((long long)DIM * a.nn * a.n <= 0xFFFFFFFFll) return launch_dag<true>(a, tma_maps[k], grid, lay.total, s);
-                return launch_dag<false>(a, tma_maps[k], grid, lay.total, s);
+                const StepArgs<DMAX, DMAX> w = widen_args(a);
+                if ((long long)DIM * a.nn * a.n <= 0xFFFFFFFFll) return launch_dag<true>(w, tma_maps[k], grid, lay.total, s);
+                return launch_dag<false>(w, tma_maps[k], grid, lay.total, s);
             }
         }
         if (fused) {
@@ -391,14 +622,27 @@ struct Solver final : SolverBase {
     bool prepare_tma(void* const* u, void* const* q, const float* D, const float* S) override {
         if constexpr (kDagTmaCapable) {
             const int es = (int)sizeof(T);
+            const StepArgs<DMAX, DMAX> w = widen_args(base);
             DagTmaLayout lay(1, 1, DIM, es);
-            if (!build_dag_lists(base, DIM, es, &lists, &lay)) return false;
+            if (!build_dag_lists(w, DIM, es, &lists, &lay)) return false;
             for (int k = 0; k < 2; ++k) {
-                if (!encode_dag_maps(base, DIM, es, lists.nf, u[k], q[k], D, S, &tma_maps[k])) return false;
+                if (!encode_dag_maps(w, DIM, es, lists.nf, u[k], q[k], D, S, &tma_maps[k], lay.qbx)) return false;
                 tma_u[k] = u[k];
             }
             dag_tma_ready = true;
             prepare_ishikawa(u, q, D, S);
+            // two-level trees and DAGs with at most four inner nodes: maps over
+            // every node's flows
+            const bool is_tree = build_tree_shape(w, DIM, es, &tree);
+            const bool is_dag4 = build_dag4_shape(w, DIM, es, &dag4);
+            if (is_tree || is_dag4) {
+                bool ok = true;
+                const TreeTmaLayout tl(w.nl, w.nn, DIM, es);
+                for (int k = 0; k < 2 && ok; ++k)
+                    ok = encode_dag_maps(w, DIM, es, w.nn, u[k], q[k], D, S, &tree_maps[k], tl.qbx);
+                tree_ready = ok && is_tree;
+                dag4_ready = ok && is_dag4;
+            }
             return false;  // the energy reduction keeps its own (non-TMA) kernel
         } else if constexpr (!kTmaCapable) {
             prepare_ishikawa(u, q, D, S);
@@ -448,7 +692,7 @@ struct Solver final : SolverBase {
     }
 
     bool fuses_energy(bool fused) const override {
-        return fused && use_tma && ((kTmaCapable && tma_ready) || (IS_DAG && ishi_ready));
+        return fused && use_tma && ((kTmaCapable && tma_ready) || (IS_DAG && ishi_ready && use_ishi));
     }
 
     void set_step(float c, float tau) override {
@@ -456,10 +700,44 @@ struct Solver final : SolverBase {
         base.ctau = c * tau;
     }
 
+    bool select(const char* name) override {
+        const auto is = [&](const char* v) { return strcmp(name, v) == 0; };
+        if (is("fused")) {
+            use_tma = false;
+            return true;
+        }
+        if (is("fused_tma") && kTmaCapable && tma_ready) {
+            use_tma = true;
+            return true;
+        }
+        if (is("fused_tma_ishikawa") && IS_DAG && ishi_ready) {
+            use_tma = use_ishi = true;
+            return true;
+        }
+        if (is("fused_tma_tree") && kDagTmaCapable && tree_ready) {
+            use_tma = use_tree = true;
+            use_ishi = false;
+            return true;
+        }
+        if (is("fused_tma_dag4") && kDagTmaCapable && dag4_ready) {
+            use_tma = use_dag4 = true;
+            use_tree = use_ishi = false;
+            return true;
+        }
+        if (is("fused_tma_dag") && kDagTmaCapable && dag_tma_ready) {
+            use_tma = true;
+            use_tree = use_ishi = use_dag4 = false;
+            return true;
+        }
+        return false;
+    }
+
     const char* variant(bool fused) const override {
         if (!fused) return inplace_tma() ? "inplace_tma" : "inplace";
         if (kTmaCapable && tma_ready && use_tma) return "fused_tma";
-        if (IS_DAG && ishi_ready && use_tma) return "fused_tma_ishikawa";
+        if (IS_DAG && ishi_ready && use_tma && use_ishi) return "fused_tma_ishikawa";
+        if (kDagTmaCapable && tree_ready && use_tma && use_tree) return "fused_tma_tree";
+        if (kDagTmaCapable && dag4_ready && use_tma && use_dag4) return "fused_tma_dag4";
         if (kDagTmaCapable && dag_tma_ready && use_tma) return "fused_tma_dag";
         return "fused";
     }
@@ -656,7 +934,8 @@ struct BatchDagTma final : BatchBase {
                 a.q_in = m[k].q[p];
                 a.q_out = m[k].q[1 - p];
                 ha[(size_t)p * n + k] = a;
-                if (!encode_dag_maps(base, DIM, es, hl[k].nf, m[k].u[p], m[k].q[p], v.D, v.S, &hm[(size_t)p * n + k]))
+                if (!encode_dag_maps(base, DIM, es, hl[k].nf, m[k].u[p], m[k].q[p], v.D, v.S, &hm[(size_t)p * n + k],
+                                     lay.qbx))
                     return cudaErrorInvalidValue;
             }
             // x tiles fastest, so the CTAs that run together are neighbours
@@ -703,18 +982,141 @@ struct BatchDagTma final : BatchBase {
     int ctas_per_sm() const override { return 1; }
 };
 
+// Batched iteration on the four-inner-node kernel (every member a DAG with
+// at most four non-end-label nodes and twelve end-labels): one persistent
+// launch per iteration over (member, x tile, y tile, z chunk) items; per
+// member and parity the arguments and tensor maps (every node's flows) in
+// device memory, the shapes once per member.
+template <int DIM, typename T>
+struct BatchDag4Tma final : BatchBase {
+    using Args = StepArgs<DMAX, DMAX>;
+    Args* args = nullptr;       // [2][nvol]
+    TmaMaps* maps = nullptr;    // [2][nvol]
+    Dag4Shape* shapes = nullptr;
+    int4* items = nullptr;
+    int* counter = nullptr;     // next work item of the running launch
+    int nvol = 0, nitems = 0, smem = 0, bar_off = 0;
+    bool idx32 = true;
+
+    ~BatchDag4Tma() override { release(); }
+
+    void release() {
+        void* ptrs[] = {args, maps, shapes, items, counter};
+        for (void* p : ptrs)
+            if (p) cudaFree(p);
+        args = nullptr;
+        maps = nullptr;
+        shapes = nullptr;
+        items = nullptr;
+        counter = nullptr;
+    }
+
+    // True if every member can run the four-inner-node kernel.
+    static bool fits(const BatchMember* m, int n) {
+        for (int k = 0; k < n; ++k) {
+            if (m[k].view.nl > DMAX || m[k].view.nn > DMAX) return false;
+            Dag4Shape sh;
+            if (!build_dag4_shape(make_step_args<DMAX, DMAX, true>(m[k].view, 1), DIM, (int)sizeof(T), &sh))
+                return false;
+        }
+        return true;
+    }
+
+    cudaError_t setup(const BatchMember* m, int n, int zc) override {
+        release();
+        nvol = n;
+        const int es = (int)sizeof(T);
+        std::vector<Args> ha(2 * (size_t)n);
+        std::vector<TmaMaps> hm(2 * (size_t)n);
+        std::vector<Dag4Shape> hs((size_t)n);
+        std::vector<int4> work;
+        smem = 0;
+        bar_off = 0;
+        idx32 = true;
+        for (int k = 0; k < n; ++k) {
+            const ProblemView& v = m[k].view;
+            idx32 = idx32 && (long long)DIM * v.nn * v.n <= 0xFFFFFFFFll;
+            const Args base = make_step_args<DMAX, DMAX, true>(v, zc);
+            if (!build_dag4_shape(base, DIM, es, &hs[k])) return cudaErrorInvalidValue;
+            const TreeTmaLayout lay(v.nl, v.nn, DIM, es);
+            smem = std::max(smem, lay.total);
+            bar_off = std::max(bar_off, lay.bar_off);
+            for (int p = 0; p < 2; ++p) {
+                Args a = base;
+                a.u_in = m[k].u[p];
+                a.u_out = m[k].u[1 - p];
+                a.q_in = m[k].q[p];
+                a.q_out = m[k].q[1 - p];
+                ha[(size_t)p * n + k] = a;
+                if (!encode_dag_maps(base, DIM, es, v.nn, m[k].u[p], m[k].q[p], v.D, v.S, &hm[(size_t)p * n + k],
+                                     lay.qbx))
+                    return cudaErrorInvalidValue;
+            }
+            // x tiles fastest, so the CTAs that run together are neighbours
+            for (int bz = 0; bz < (v.nz + zc - 1) / zc; ++bz)
+                for (int by = 0; by < (v.ny + DTY - 1) / DTY; ++by)
+                    for (int bx = 0; bx < (v.nx + FTX - 1) / FTX; ++bx) work.push_back(make_int4(k, bx, by, bz));
+        }
+        // the barriers sit past every member's buffers
+        smem = std::max(smem, bar_off + 64 + 128);
+        nitems = (int)work.size();
+        cudaError_t e;
+        if ((e = cudaMalloc(&args, sizeof(Args) * ha.size())) != cudaSuccess) return e;
+        if ((e = cudaMalloc(&maps, sizeof(TmaMaps) * hm.size())) != cudaSuccess) return e;
+        if ((e = cudaMalloc(&shapes, sizeof(Dag4Shape) * hs.size())) != cudaSuccess) return e;
+        if ((e = cudaMalloc(&items, sizeof(int4) * work.size())) != cudaSuccess) return e;
+        if ((e = cudaMalloc(&counter, sizeof(int))) != cudaSuccess) return e;
+        if ((e = cudaMemcpy(args, ha.data(), sizeof(Args) * ha.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return e;
+        if ((e = cudaMemcpy(maps, hm.data(), sizeof(TmaMaps) * hm.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
+            return e;
+        if ((e = cudaMemcpy(shapes, hs.data(), sizeof(Dag4Shape) * hs.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
+            return e;
+        if ((e = cudaMemcpy(items, work.data(), sizeof(int4) * work.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
+            return e;
+        if ((e = cudaFuncSetAttribute(batched_dag4_tma_kernel<DIM, T, true>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess)
+            return e;
+        return cudaFuncSetAttribute(batched_dag4_tma_kernel<DIM, T, false>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    }
+
+    cudaError_t launch(int parity, int grid, cudaStream_t s) override {
+        cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), s);
+        if (e != cudaSuccess) return e;
+        if (idx32)
+            batched_dag4_tma_kernel<DIM, T, true><<<grid, DAG_TMA_NT, smem, s>>>(
+                args + (size_t)parity * nvol, maps + (size_t)parity * nvol, shapes, items, nitems, bar_off, counter);
+        else
+            batched_dag4_tma_kernel<DIM, T, false><<<grid, DAG_TMA_NT, smem, s>>>(
+                args + (size_t)parity * nvol, maps + (size_t)parity * nvol, shapes, items, nitems, bar_off, counter);
+        return cudaGetLastError();
+    }
+
+    int n_items() const override { return nitems; }
+    int ctas_per_sm() const override { return 1; }
+};
+
 // Factories, one per translation unit (storage x model).
 SolverBase* make_potts_f32(int maxl, int dim, const ProblemView& v);
 SolverBase* make_potts_bf16(int maxl, int dim, const ProblemView& v);
+SolverBase* make_potts_f16(int maxl, int dim, const ProblemView& v);
 SolverBase* make_dag_f32(int maxl, int maxn, int dim, const ProblemView& v);
 SolverBase* make_dag_bf16(int maxl, int maxn, int dim, const ProblemView& v);
+SolverBase* make_dag_f16(int maxl, int maxn, int dim, const ProblemView& v);
 BatchBase* make_batch_potts_f32(int maxl, int dim);
 BatchBase* make_batch_potts_bf16(int maxl, int dim);
+BatchBase* make_batch_potts_f16(int maxl, int dim);
 BatchBase* make_batch_dag_f32(int maxl, int maxn, int dim);
 BatchBase* make_batch_dag_bf16(int maxl, int maxn, int dim);
+BatchBase* make_batch_dag_f16(int maxl, int maxn, int dim);
 // The TMA DAG batch, or nullptr if some member cannot run the TMA DAG kernel.
 BatchBase* make_batch_dag_tma_f32(const BatchMember* m, int n, int dim);
 BatchBase* make_batch_dag_tma_bf16(const BatchMember* m, int n, int dim);
+BatchBase* make_batch_dag_tma_f16(const BatchMember* m, int n, int dim);
+// The four-inner-node batch, or nullptr if some member cannot run that kernel.
+BatchBase* make_batch_dag4_tma_f32(const BatchMember* m, int n, int dim);
+BatchBase* make_batch_dag4_tma_bf16(const BatchMember* m, int n, int dim);
+BatchBase* make_batch_dag4_tma_f16(const BatchMember* m, int n, int dim);
 
 // Adjoint of one Potts iteration (pfm_adjoint.cu).
 struct AdjLaunch {

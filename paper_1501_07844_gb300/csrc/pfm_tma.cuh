@@ -113,9 +113,11 @@ __device__ __forceinline__ void tma_load_3d(unsigned dst, const CUtensorMap* map
 template <typename T> __device__ __forceinline__ float lds(const T* p);
 template <> __device__ __forceinline__ float lds<float>(const float* p) { return *p; }
 template <> __device__ __forceinline__ float lds<__nv_bfloat16>(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+template <> __device__ __forceinline__ float lds<__half>(const __half* p) { return __half2float(*p); }
 template <typename T> __device__ __forceinline__ void sts(T* p, float v);
 template <> __device__ __forceinline__ void sts<float>(float* p, float v) { *p = v; }
 template <> __device__ __forceinline__ void sts<__nv_bfloat16>(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+template <> __device__ __forceinline__ void sts<__half>(__half* p, float v) { stv<__half>(p, v); }
 
 // Two threads per voxel: thread pair (2v, 2v+1) shares voxel v, each owning
 // half of the labels, J(h, i) = 4*(i/2) + 2*h + i%2 (halves {0,1,4,5} and
@@ -403,7 +405,7 @@ fused_tma_kernel(const StepArgs<MAXL, MAXL> a, const __grid_constant__ TmaMaps m
                         const float un = u[i] * inv;
                         gcur[i] = a.literal ? u[i] : un;
                         gC[j * ustride + ui] = gcur[i];
-                        if (ownerE && p < z1) stv<T>(slot_ptr<IDX32>(uout, j, p, n, plane, vox), un);
+                        if (ownerE && p < z1) stu<T>(slot_ptr<IDX32>(uout, j, p, n, plane, vox), un);
                     }
                 }
             }

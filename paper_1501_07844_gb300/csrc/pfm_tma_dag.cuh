@@ -54,11 +54,23 @@ struct DagLists {
 // Shared-memory layout, sized by the runtime end-label count nl and the
 // count nf of flow-carrying nodes: per stage u, D, the nf nodes' flows and S;
 // two planes of g_A (nf nodes); one row of max(nl, nf) floats per voxel.
+// The four lanes of a voxel read four consecutive nodes' flows at the same
+// position, so the flow box is widened on the right when three stages still
+// fit (qbx 44 for FP32, 56 for 16-bit types: a node stride of 24 banks mod
+// 32, no two lanes on one bank), else it keeps the 32 + 2 * 16 bytes the
+// halo needs (qbx 40 / 48).
 struct DagTmaLayout {
-    int u_off, d_off, q_off, s_off, stage_bytes, g_off, e_off, row, bar_off, total;
+    int qbx, u_off, d_off, q_off, s_off, stage_bytes, g_off, e_off, row, bar_off, total;
     __host__ __device__ static int a128(int b) { return (b + 127) / 128 * 128; }
     __host__ __device__ DagTmaLayout(int nl, int nf, int dim, int es) {
-        const int qbx = FTX + 2 * (16 / es);
+        qbx = es == 4 ? 44 : 56;
+        set(nl, nf, dim, es);
+        if (total + (int)sizeof(DagLists) + 64 > 227 * 1024) {
+            qbx = FTX + 2 * (16 / es);
+            set(nl, nf, dim, es);
+        }
+    }
+    __host__ __device__ void set(int nl, int nf, int dim, int es) {
         u_off = 0;
         d_off = a128(nl * DAG_UY * TMA_BX * es);
         q_off = d_off + a128(nl * DAG_UY * TMA_BX * 4);
@@ -90,8 +102,6 @@ __device__ __forceinline__ bool dag_tma_tile(const StepArgs<DMAX, DMAX>& a, cons
                                              int bx, int by, int bz, unsigned char* smem, unsigned bar0,
                                              DagRing& ring) {
     constexpr int QOFF = 16 / (int)sizeof(T);
-    constexpr int QBX = FTX + 2 * QOFF;
-    constexpr int qstride = DAG_QY * QBX;
     constexpr int ustride = DAG_UY * TMA_BX;
     constexpr int PER = DMAX / 4;  // labels / nodes per thread at most
     // scalars read once (the batched kernel's arguments live in global memory)
@@ -99,6 +109,8 @@ __device__ __forceinline__ bool dag_tma_tile(const StepArgs<DMAX, DMAX>& a, cons
     const int nx = a.nx, ny = a.ny, nz = a.nz, px = a.px, literal = a.literal, aniso = a.aniso;
     const float ctau = a.ctau;
     const DagTmaLayout lay(nl, nf, DIM, (int)sizeof(T));
+    const int QBX = lay.qbx;             // flow box width (elements)
+    const int qstride = DAG_QY * QBX;    // one flow component of one node
     const int t = threadIdx.x;
     const int h = t & 3;
     const int v = t >> 2;
@@ -290,7 +302,7 @@ __device__ __forceinline__ bool dag_tma_tile(const StepArgs<DMAX, DMAX>& a, cons
                     if (j < nl) {
                         const float un = u[i] * inv;
                         ecol[(j) * DAG_NV] = literal ? u[i] : un;
-                        if (ownerE && p < z1) stv<T>(slot_ptr<IDX32>(uout, j, p, n, plane, vox), un);
+                        if (ownerE && p < z1) stu<T>(slot_ptr<IDX32>(uout, j, p, n, plane, vox), un);
                     }
                 }
             }

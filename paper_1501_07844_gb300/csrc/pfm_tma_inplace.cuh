@@ -162,7 +162,7 @@ prox_inplace_tma_kernel(const StepArgs<MAXL, MAXL> a, const __grid_constant__ In
 #pragma unroll
             for (int i = 0; i < HL; ++i) {
                 const int j = half_label(h, i);
-                if (EXACT || j < nl) stv<T>(slot_ptr<IDX32>(u_out, j, p, n, plane, vox), u[i] * inv);
+                if (EXACT || j < nl) stu<T>(slot_ptr<IDX32>(u_out, j, p, n, plane, vox), u[i] * inv);
             }
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");

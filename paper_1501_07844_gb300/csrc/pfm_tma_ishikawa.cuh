@@ -271,7 +271,7 @@ ishikawa_tma_kernel(const StepArgs<MAXL, MAXN> a, const __grid_constant__ TmaMap
                 for (int i = 0; i < HL; ++i) {
                     const int j = HL * h + i;
                     if (j < nl) {
-                        if (ownerE && p < z1) stv<T>(slot_ptr<IDX32>(uout, j, p, n, plane, vox), u[i] * inv);
+                        if (ownerE && p < z1) stu<T>(slot_ptr<IDX32>(uout, j, p, n, plane, vox), u[i] * inv);
                         if (j >= 1) {
                             gcur[i] = suf[i] + gcarry;  // g of level j: labels j..N
                             gC[j * ustride + ui] = gcur[i];

@@ -8,14 +8,15 @@
 // lane h of the pair's four threads takes labels h, h+4, ...  Every load,
 // every add / multiply / fused multiply-add and every store of the
 // iteration then serves two voxels (64-bit shared loads and global stores of
-// FP32 pairs, 32-bit ones of BF16 pairs; packed f32x2 add / multiply / fma),
+// FP32 pairs, 32-bit ones of BF16 / F16 pairs; packed f32x2 add / multiply /
+// fma),
 // so the kernel issues fewer instructions per voxel-label update than the
 // one-voxel-per-thread form (about a fifth fewer with BF16 storage: widening
 // BF16 pairs, the per-voxel work below and the operands assembled from
 // neighbours stay).  Only the hardware approximations (ex2, rsqrt, rcp),
 // the minimum and the projection's scale stay per voxel.  The per-voxel
 // minimum and normaliser of the prox are combined over the four lanes with
-// two shuffle rounds.  Used for BF16 storage: with FP32 storage the
+// two shuffle rounds.  Used for 16-bit storage: with FP32 storage the
 // one-voxel kernel already runs at the bandwidth roof and this one measured
 // slower.
 //
@@ -57,10 +58,17 @@ template <> __device__ __forceinline__ float2 lds2<__nv_bfloat16>(const __nv_bfl
     const unsigned w = *reinterpret_cast<const unsigned*>(p);
     return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
 }
+template <> __device__ __forceinline__ float2 lds2<__half>(const __half* p) {
+    return __half22float2(*reinterpret_cast<const __half2*>(p));
+}
 template <typename T> __device__ __forceinline__ void stv2(T* p, float2 v);
 template <> __device__ __forceinline__ void stv2<float>(float* p, float2 v) { *reinterpret_cast<float2*>(p) = v; }
 template <> __device__ __forceinline__ void stv2<__nv_bfloat16>(__nv_bfloat16* p, float2 v) {
     *reinterpret_cast<__nv_bfloat162*>(p) = __floats2bfloat162_rn(v.x, v.y);
+}
+template <> __device__ __forceinline__ void stv2<__half>(__half* p, float2 v) {
+    *reinterpret_cast<__half2*>(p) = __floats2half2_rn(fminf(fmaxf(v.x, -F16_MAX), F16_MAX),
+                                                       fminf(fmaxf(v.y, -F16_MAX), F16_MAX));
 }
 // the pair, or its first voxel alone when the second is beyond the grid
 template <typename T> __device__ __forceinline__ void st_pair(T* p, float2 v, bool both) {
@@ -68,6 +76,11 @@ template <typename T> __device__ __forceinline__ void st_pair(T* p, float2 v, bo
         stv2<T>(p, v);
     else
         stv<T>(p, v.x);
+}
+// a labelling pair (the F16 floor of stu applies)
+template <typename T> __device__ __forceinline__ void st_pair_u(T* p, float2 v, bool both) {
+    if constexpr (std::is_same<T, __half>::value) v = make_float2(fmaxf(v.x, F16_U_FLOOR), fmaxf(v.y, F16_U_FLOOR));
+    st_pair<T>(p, v, both);
 }
 
 // EXACT: the problem has exactly MAXL labels (no per-label guards).
@@ -291,7 +304,7 @@ fused_tma_x2_kernel(const StepArgs<MAXL, MAXL> a, const __grid_constant__ TmaMap
                         const float2 un = f2mul(u[i], inv);
                         gcur[i] = a.literal ? make_float2(u[i].x, both ? u[i].y : 0.f) : un;
                         *reinterpret_cast<float2*>(gC + j * ustride + ui) = gcur[i];
-                        if (ownerE && p < z1) st_pair<T>(slot_ptr<IDX32>(uout, j, p, n, plane, vox), un, both);
+                        if (ownerE && p < z1) st_pair_u<T>(slot_ptr<IDX32>(uout, j, p, n, plane, vox), un, both);
                     }
                 }
             }

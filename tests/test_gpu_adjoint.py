@@ -100,8 +100,14 @@ def test_adjoint_matches_fp64_autograd(shape, aniso):
     gD_ref, gS_ref, L_ref = reference_grads(prob, iters, s_label, aniso, target)
     gD, gS, L = gpu_grads(prob, iters, s_label, aniso, target, ce=5)
     assert abs(L - L_ref) <= 1e-5 * abs(L_ref)
-    assert relerr(gD, gD_ref) <= 1e-3, relerr(gD, gD_ref)
-    assert relerr(gS, gS_ref) <= 1e-3, relerr(gS, gS_ref)
+    # element by element: 1e-3 of the entry itself, with a floor of 1e-6 of
+    # the largest entry (entries far below it carry FP32 rounding only)
+    for g, g_ref in ((gD, gD_ref), (gS, gS_ref)):
+        floor = 1e-3 * np.abs(g_ref).max()
+        worst = float((np.abs(g - g_ref) / np.maximum(np.abs(g_ref), floor)).max())
+        print("ADJOINT %s %s worst element rel err %.3e, norm rel err %.3e" % (shape, "aniso" if aniso else "iso",
+                                                                              worst, relerr(g, g_ref)))
+        assert np.all(np.abs(g - g_ref) <= 1e-3 * np.maximum(np.abs(g_ref), floor)), worst
 
 
 def test_checkpoint_interval_does_not_change_gradients():

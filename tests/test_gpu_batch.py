@@ -32,13 +32,15 @@ def test_batch_members_equal_single_problems(iters, sched):
     import paper_1501_07844_gb300 as pfm
     vols = dag_volumes()
     with pfm.Batch([as_dict(p) for p in vols], schedule=sched) as b:
-        assert b.variant == ("batched_tma_dag" if sched == pfm.FUSED else "batched")
+        assert b.variant == ("batched_tma_dag4" if sched == pfm.FUSED else "batched")
         b.iterate(iters)
         E_b, P_b = b.energy()
         for k, p in enumerate(vols):
             # the same tile body as the batched kernel
             with gpu_problem(p, schedule=sched) as single:
-                assert single.variant == ("fused_tma_dag" if sched == pfm.FUSED else "fused")
+                if sched == pfm.FUSED:
+                    single.select_kernel("fused_tma_dag4")
+                assert single.variant == ("fused_tma_dag4" if sched == pfm.FUSED else "fused")
                 single.iterate(iters)
                 m = b.members[k]
                 assert np.array_equal(m.labels().cpu().numpy(), single.labels().cpu().numpy())
@@ -100,20 +102,22 @@ def test_batch_rejects_bad_members():
         pfm.Batch([as_dict(good), as_dict(flat2d)])
 
 
-@pytest.mark.parametrize("storage", [0, 1], ids=["f32", "bf16"])
+@pytest.mark.parametrize("storage", [0, 1, 2], ids=["f32", "bf16", "f16"])
 def test_tma_dag_batch_2d_bf16_and_hmf(storage):
-    """The TMA DAG batch on 2-D members and HMF trees, both storages: bit for
-    bit the single-problem TMA DAG kernel."""
+    """The TMA batch on 2-D DAGMF members and on HMF trees (both have at most
+    four inner nodes: the four-inner-node kernel), every storage: bit for bit
+    the single-problem kernel with the same tile body."""
     import paper_1501_07844_gb300 as pfm
     vols = [synth.hmf_problem(seed=4950 + k, shape=(19 + 5 * k, 37 - 3 * k, 45 + 2 * k), iters=20) for k in range(2)]
     vols += [synth.dagmf_problem(4960 + k, (53 + 9 * k, 70 - 11 * k), iters=20) for k in range(2)]
     for group in (vols[:2], vols[2:]):
         with pfm.Batch([as_dict(p) for p in group], storage=storage) as b:
-            assert b.variant == "batched_tma_dag"
+            assert b.variant == "batched_tma_dag4"
             b.iterate(23)
             for k, p in enumerate(group):
                 with gpu_problem(p, storage=storage) as single:
-                    assert single.variant == "fused_tma_dag"
+                    single.select_kernel("fused_tma_dag4")   # the batch's tile body
+                    assert single.variant == "fused_tma_dag4"
                     single.iterate(23)
                     assert np.array_equal(b.members[k].labels().cpu().numpy(), single.labels().cpu().numpy())
                     assert np.array_equal(b.members[k].flows().cpu().numpy(), single.flows().cpu().numpy())
@@ -135,6 +139,8 @@ def test_tma_dag_batch_mixed_layouts_and_ishikawa():
         b.iterate(26)
         for k, p in enumerate(vols):
             with gpu_problem(p) as single:
+                if k < 2:
+                    single.select_kernel("fused_tma_dag")   # the batch's tile body
                 single.iterate(26)
                 ub, us = b.members[k].labels().cpu().numpy(), single.labels().cpu().numpy()
                 qb, qs = b.members[k].flows().cpu().numpy(), single.flows().cpu().numpy()

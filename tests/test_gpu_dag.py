@@ -80,11 +80,12 @@ def test_ishikawa_chain_matches_algorithm3(nlev, spatial):
 
 
 @pytest.mark.parametrize("kind", ["hmf", "dagmf", "ishikawa8"])
-@pytest.mark.parametrize("storage", [0, 1], ids=["f32", "bf16"])
+@pytest.mark.parametrize("storage", [0, 1, 2], ids=["f32", "bf16", "f16"])
 def test_tma_dag_kernel_parity(kind, storage):
-    """A 16-byte row pitch selects the TMA-staged DAG kernel (32 x 4 tiles,
-    four threads per voxel, sparse path-weight lists); it matches the oracle
-    (FP32) and the register-staged kernel (both storages)."""
+    """A 16-byte row pitch selects a TMA-staged DAG kernel (32 x 4 tiles, four
+    threads per voxel: the tree-specialised one for HMF, the general one with
+    sparse path-weight lists for DAGMF); it matches the oracle (FP32) and the
+    register-staged kernel (every storage)."""
     import paper_1501_07844_gb300 as pfm
     shape = (23, 19, 48)
     if kind == "hmf":
@@ -94,7 +95,7 @@ def test_tma_dag_kernel_parity(kind, storage):
     else:
         prob = synth.ishikawa_problem(5650, shape, nlev=7)
     with gpu_problem(prob, storage=storage) as gp:
-        assert gp.variant == ("fused_tma_ishikawa" if kind == "ishikawa8" else "fused_tma_dag")
+        assert gp.variant == {"ishikawa8": "fused_tma_ishikawa", "hmf": "fused_tma_tree"}.get(kind, "fused_tma_dag4")
         if storage == 0:
             compare(prob, gp, 40)
         else:
@@ -192,7 +193,7 @@ def test_ishikawa_kernel_bf16_and_energy(norm):
 
 
 @pytest.mark.parametrize("kind", ["hmf", "dagmf"])
-@pytest.mark.parametrize("storage", [0, 1], ids=["f32", "bf16"])
+@pytest.mark.parametrize("storage", [0, 1, 2], ids=["f32", "bf16", "f16"])
 @pytest.mark.parametrize("norm", [0, 1], ids=["iso", "aniso"])
 def test_dag_iterate_energy(kind, storage, norm):
     """pfm_iterate_energy on the TMA DAG path (the per-voxel reduction of the
@@ -203,7 +204,7 @@ def test_dag_iterate_energy(kind, storage, norm):
     prob = synth.hmf_problem(seed=3500, shape=(21, 26, 47), iters=12) if kind == "hmf" else \
         synth.dagmf_problem(4500, (19, 30, 41), iters=12)
     with gpu_problem(prob, storage=storage, norm=norm) as a, gpu_problem(prob, storage=storage, norm=norm) as b:
-        assert a.variant == "fused_tma_dag"
+        assert a.variant == ("fused_tma_tree" if kind == "hmf" else "fused_tma_dag4")
         a.chunk_length = 8
         b.chunk_length = 8
         a.iterate(11)
@@ -216,3 +217,128 @@ def test_dag_iterate_energy(kind, storage, norm):
     if storage == 0:
         _, _, E_o, P_o = oracle_run(prob, 11, norm=norm)
         assert abs(E - E_o) <= TOL_E * abs(E_o) and abs(P - P_o) <= TOL_E * abs(P_o) + 1e-6
+
+
+def tree_cases():
+    """Two-level label trees the tree-specialised kernel takes: the HMF
+    shapes, a mixed tree (an inner node with two end-labels, a single-child
+    chain, two end-labels under the source) and a weighted tree (w_(S,A) = 1/2,
+    w_(A,L) = 2, so W_(S,L) = 1)."""
+    rng = np.random.default_rng(3700)
+    mixed = (7, [(-1, 0, 1.0), (0, 3, 1.0), (0, 4, 1.0), (-1, 1, 1.0), (1, 5, 1.0), (-1, 2, 1.0), (-1, 6, 1.0)])
+    weighted = (3, [(-1, 0, 0.5), (0, 1, 2.0), (0, 2, 2.0)])
+    out = [("hmf3x4", synth.hmf_problem(seed=3701, shape=(19, 26, 45), iters=40))]
+    nn, edges = synth.hmf_tree(2, 3)
+    out.append(("hmf2x3_2d", synth.random_problem(3702, (45, 70), nl=6, s_kind="both", n_nodes=nn, edges=edges)))
+    out.append(("mixed", synth.random_problem(3703, (13, 22, 37), nl=5, s_kind="both", n_nodes=mixed[0],
+                                              edges=mixed[1])))
+    out.append(("weighted", synth.random_problem(3704, (9, 17, 70), nl=2, s_kind="node", n_nodes=weighted[0],
+                                                 edges=weighted[1])))
+    return out
+
+
+TREE_NAMES = ["hmf3x4", "hmf2x3_2d", "mixed", "weighted"]
+TREE_MODES = {"normalised": (0, 0), "literal": (1, 0), "aniso": (0, 1)}
+TREE_PARAMS = [(c, m) for c in range(4) for m in TREE_MODES if not (TREE_NAMES[c] == "weighted" and m == "literal")]
+
+
+@pytest.mark.parametrize("case,mname", TREE_PARAMS, ids=["%s-%s" % (TREE_NAMES[c], m) for c, m in TREE_PARAMS])
+def test_tree_kernel_parity(case, mname):
+    """The tree-specialised kernel against the oracle's Algorithm 2 (every
+    voxel, 40 iterations, z-chunks of 8 planes) and against the general TMA
+    DAG kernel (path-weight lists) on the same problem.  Not among the cases:
+    the PAPER_LITERAL iteration on the weighted tree, which is chaotic in FP64
+    itself (a 2^-24 relative perturbation of D moves u by 0.33 within the 40
+    iterations), so no FP32 result can be compared with it voxel by voxel."""
+    name, prob = tree_cases()[case]
+    mode, norm = TREE_MODES[mname]
+    with gpu_problem(prob, grad_source=mode, norm=norm) as gp:
+        assert gp.variant == "fused_tma_tree", name
+        gp.chunk_length = 8
+        res = compare(prob, gp, 40, grad_source=mode, norm=norm)
+        print("tree", name, {k: "%.2e" % v for k, v in res.items()})
+        u_t, q_t = gp.labels().cpu().numpy(), gp.flows().cpu().numpy()
+    with gpu_problem(prob, grad_source=mode, norm=norm) as gp:
+        gp.select_kernel("fused_tma_dag")
+        assert gp.variant == "fused_tma_dag"
+        gp.iterate(40)
+        assert np.abs(gp.labels().cpu().numpy() - u_t).max() <= 5e-6
+        assert np.abs(gp.flows().cpu().numpy() - q_t).max() <= 5e-6
+
+
+@pytest.mark.parametrize("storage", [1, 2], ids=["bf16", "f16"])
+def test_tree_kernel_16bit_storage(storage):
+    """16-bit storage on the tree kernel: within the storage's rounding of
+    the general DAG kernel with the same storage."""
+    prob = synth.hmf_problem(seed=3705, shape=(21, 18, 50), iters=30)
+    with gpu_problem(prob, storage=storage) as a, gpu_problem(prob, storage=storage) as b:
+        b.select_kernel("fused_tma_dag")
+        assert a.variant == "fused_tma_tree" and b.variant == "fused_tma_dag"
+        a.iterate(30)
+        b.iterate(30)
+        assert np.abs(a.labels().cpu().numpy() - b.labels().cpu().numpy()).max() <= 2e-2
+        assert np.abs(a.flows().cpu().numpy() - b.flows().cpu().numpy()).max() <= 2e-2
+
+
+def test_select_kernel_rejects_what_a_problem_cannot_run():
+    import paper_1501_07844_gb300 as pfm
+    dag = synth.dagmf_problem(3706, (9, 10, 33), iters=5)
+    with gpu_problem(dag) as gp:
+        assert gp.variant == "fused_tma_dag4"
+        gp.select_kernel("fused_tma_dag")
+        assert gp.variant == "fused_tma_dag"
+        with pytest.raises(pfm.PfmError):
+            gp.select_kernel("fused_tma_tree")
+        gp.select_kernel("fused")
+        assert gp.variant == "fused"
+    with gpu_problem(dag, schedule=pfm.INPLACE) as gp:
+        with pytest.raises(pfm.PfmError):
+            gp.select_kernel("fused_tma_dag")
+
+
+DAG4_CASES = ["dagmf", "dagmf_2d", "hmf", "ishikawa3_2d", "five_inner"]
+
+
+def dag4_case(name):
+    """Problems with at most four non-end-label nodes (the DAGMF workload's
+    shape: four inner nodes, end-labels with one or two parents; a 2-D one;
+    the HMF tree; a three-level Ishikawa chain, whose end-labels carry no
+    flow) and one with five, which the four-inner-node kernel must refuse."""
+    if name == "dagmf":
+        return synth.dagmf_problem(3801, (17, 22, 45), iters=40)
+    if name == "dagmf_2d":
+        return synth.dagmf_problem(3802, (61, 77), iters=40)
+    if name == "hmf":
+        return synth.hmf_problem(seed=3803, shape=(13, 20, 41), iters=40)
+    if name == "ishikawa3_2d":
+        return synth.ishikawa_problem(3804, (40, 66), nlev=3)
+    rng = np.random.default_rng(3805)
+    nn, edges = synth.random_dag(rng, 5, 9, 2)
+    return synth.random_problem(3806, (9, 14, 37), nl=9, s_kind="both", n_nodes=nn, edges=edges)
+
+
+@pytest.mark.parametrize("name", DAG4_CASES)
+@pytest.mark.parametrize("mode,norm", [(0, 0), (1, 0), (0, 1)], ids=["normalised", "literal", "aniso"])
+def test_dag4_kernel_parity(name, mode, norm):
+    """The four-inner-node kernel against the oracle's Algorithm 2 (every
+    voxel, z-chunks of 8 planes) and against the general TMA DAG kernel
+    (path-weight lists) on the same problem."""
+    import paper_1501_07844_gb300 as pfm
+    prob = dag4_case(name)
+    iters = 40 if mode == 0 else 12
+    with gpu_problem(prob, grad_source=mode, norm=norm) as gp:
+        if name == "five_inner":
+            with pytest.raises(pfm.PfmError):
+                gp.select_kernel("fused_tma_dag4")
+            return
+        gp.select_kernel("fused_tma_dag4")
+        assert gp.variant == "fused_tma_dag4"
+        gp.chunk_length = 8
+        res = compare(prob, gp, iters, grad_source=mode, norm=norm)
+        print("dag4", name, {k: "%.2e" % v for k, v in res.items()})
+        u_t, q_t = gp.labels().cpu().numpy(), gp.flows().cpu().numpy()
+    with gpu_problem(prob, grad_source=mode, norm=norm) as gp:
+        gp.select_kernel("fused_tma_dag")
+        gp.iterate(iters)
+        assert np.abs(gp.labels().cpu().numpy() - u_t).max() <= 5e-6
+        assert np.abs(gp.flows().cpu().numpy() - q_t).max() <= 5e-6

@@ -219,7 +219,7 @@ def test_kernel_variant_selection():
 
 
 @pytest.mark.parametrize("nx", [1, 5, 37, 65])
-@pytest.mark.parametrize("storage", [0, 1], ids=["f32", "bf16"])
+@pytest.mark.parametrize("storage", [0, 1, 2], ids=["f32", "bf16", "f16"])
 def test_padded_rows_every_schedule(nx, storage):
     """Widths that are not a multiple of 8: the device rows are padded; every
     schedule matches the oracle (FP32) or the other schedules (BF16), the
@@ -256,7 +256,7 @@ def torch_equal(a, b):
 
 
 @pytest.mark.parametrize("sched", [0, 1, 2], ids=["fused_tma", "inplace", "fused_plain"])
-@pytest.mark.parametrize("storage", [0, 1], ids=["f32", "bf16"])
+@pytest.mark.parametrize("storage", [0, 1, 2], ids=["f32", "bf16", "f16"])
 def test_iterate_energy_reports_input_of_last_iteration(sched, storage):
     """pfm_iterate_energy(n) returns E and P of the state after n-1 iterations
     (reduced inside the last iteration on the TMA path) and leaves the state
@@ -297,7 +297,7 @@ def test_continuation_schedule_matches_oracle(sched):
 
 
 @pytest.mark.parametrize("shape", [(37, 19, 70), (53, 66), (1, 9, 33)], ids=["3d_chunks", "2d", "one_plane"])
-@pytest.mark.parametrize("storage", [0, 1], ids=["f32", "bf16"])
+@pytest.mark.parametrize("storage", [0, 1, 2], ids=["f32", "bf16", "f16"])
 def test_inplace_tma_sweeps(shape, storage):
     """The TMA-staged in-place sweeps (z-chunks of 4 planes here, ragged
     tiles) match the oracle (FP32) and the fused TMA schedule; PAPER_LITERAL
@@ -347,7 +347,7 @@ def test_prefetch_commit_equals_set_data():
         assert torch.equal(a.labels(), b.labels()) and torch.equal(a.flows(), b.flows())
 
 
-@pytest.mark.parametrize("storage", [0, 1], ids=["f32", "bf16"])
+@pytest.mark.parametrize("storage", [0, 1, 2], ids=["f32", "bf16", "f16"])
 def test_state_async_equals_readback(storage):
     """pfm_get_state_async (device destinations, stream-ordered, no wait)
     gives the same dense arrays as pfm_get_labels / pfm_get_flows, padded

@@ -63,6 +63,57 @@ def test_noalloc_energy_matches_pfm_energy(case):
         assert abs(P - P_ref) <= 1e-6 * abs(P_ref) + 1e-6, (P, P_ref)
 
 
+@pytest.mark.gpu
+def test_noalloc_energy_matches_the_oracle():
+    """E and P of a GPU state through the allocation-free entry point against
+    the FP64 oracle's E(u) (Eq. potts_original) and P(q) (Eq. potts_pseudo)
+    of the same state."""
+    import torch
+    import oracle
+    prob = synth.potts3d_problem(seed=2203, nl=8, shape=(21, 30, 44))
+    L = _lib()
+    stream = torch.cuda.current_stream().cuda_stream
+    with gpu_problem(prob, stream=stream) as gp:
+        gp.iterate(25)
+        u, q = gp.labels(), gp.flows()
+    D = torch.from_numpy(prob.D).cuda()
+    S = torch.from_numpy(prob.S_field).cuda()
+    out = torch.empty(2, dtype=torch.float64, device="cuda")
+    assert _call(L, prob, u, q, D, S, 0, out, stream) == 0, L.pfm_last_error()
+    torch.cuda.synchronize()
+    E, P = out.tolist()
+    E_o, P_o = oracle.potts_energy(prob.D.astype(np.float64), u.cpu().numpy().astype(np.float64),
+                                   q.cpu().numpy().astype(np.float64), S_field=prob.S_field.astype(np.float64))
+    assert abs(E - E_o) <= 1e-6 * abs(E_o) and abs(P - P_o) <= 1e-6 * abs(P_o) + 1e-6, (E, E_o, P, P_o)
+
+
+@pytest.mark.gpu
+def test_noalloc_energy_at_the_largest_accepted_grid():
+    """A grid of exactly PFM_NOALLOC_MAX_VOXELS voxels (256^3, two labels):
+    every block of the fixed scratch is used, the last partial sits just
+    before the flag word; twice in a row, against pfm_energy."""
+    import torch
+    prob = synth.potts3d_problem(seed=2204, nl=2, shape=(256, 256, 256))
+    assert int(np.prod(prob.spatial)) == 16777216
+    L = _lib()
+    stream = torch.cuda.current_stream().cuda_stream
+    with gpu_problem(prob, stream=stream) as gp:
+        gp.iterate(5)
+        E_ref, P_ref = gp.energy()
+        u, q = gp.labels(), gp.flows()
+    D = torch.from_numpy(prob.D).cuda()
+    S = torch.from_numpy(prob.S_field).cuda()
+    out = torch.empty(2, dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        out.fill_(float("nan"))
+        assert _call(L, prob, u, q, D, S, 0, out, stream) == 0, L.pfm_last_error()
+        torch.cuda.synchronize()
+        E, P = out.tolist()
+        assert abs(E - E_ref) <= 1e-6 * abs(E_ref) and abs(P - P_ref) <= 1e-6 * abs(P_ref) + 1e-6
+    del u, q, D, S
+    torch.cuda.empty_cache()
+
+
 def test_noalloc_rejects_grid_beyond_scratch():
     """A grid larger than the fixed scratch allows is refused on the host,
     before any device work (the pointers are never dereferenced)."""
