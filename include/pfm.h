@@ -299,9 +299,10 @@ PFM_API const char* pfm_kernel_variant(const pfm_problem* pb);
  * has launched since creation (for launch accounting). */
 PFM_API int64_t pfm_iterations_done(const pfm_problem* pb);
 /* Failure-detection self-test: runs, on the problem's stream, one bounded
- * mbarrier wait of the kind every TMA pipeline uses, on a barrier nothing
- * arrives on.  The wait gives up after its cycle budget (about 2 s), raises
- * the timeout flag and the kernel returns; the call then restores the
+ * mbarrier wait of the kind every TMA pipeline uses (the same primitive with
+ * a twentieth of the pipelines' cycle budget of about 2 s), on a barrier
+ * nothing arrives on.  The wait gives up after its budget (about 0.1 s),
+ * raises the timeout flag and the kernel returns; the call then restores the
  * problem's flags and returns PFM_ETIMEOUT (PFM_ECUDA if the wait did not
  * report).  The problem and the CUDA context stay usable.  Not part of the
  * paper's method. */

@@ -136,7 +136,9 @@ __global__ void wait_selftest_kernel(unsigned* flags) {
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    const bool ok = mbar_wait_bounded(b, 0u);
+    // the pipelines' wait with a twentieth of their budget (about 0.1 s):
+    // the same give-up path, without holding the GPU for the full budget
+    const bool ok = mbar_wait_bounded(b, 0u, TMA_WAIT_CYCLES / 20);
     if (__syncthreads_or(!ok) && threadIdx.x == 0) atomicOr(flags, FLAG_TIMEOUT);
 }
 

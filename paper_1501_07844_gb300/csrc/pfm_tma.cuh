@@ -84,11 +84,13 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity) {
     return ok != 0;
 }
 
-// Bounded wait: false if the budget ran out before the phase completed.
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity) {
+// Bounded wait: false if the budget (in clock cycles; every pipeline uses
+// TMA_WAIT_CYCLES) ran out before the phase completed.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity,
+                                                  long long budget = TMA_WAIT_CYCLES) {
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity))
-        if (clock64() - t0 > TMA_WAIT_CYCLES) return false;
+        if (clock64() - t0 > budget) return false;
     return true;
 }
 

@@ -1,14 +1,14 @@
 """Parity at the full sizes of the other benchmark workloads, in the launch
 configurations bench.py times, after each workload's own iteration count:
-HMF 192^3 (400 iterations, FP32 and BF16 storage, TMA DAG kernel), Ishikawa
-256^3 with 8 labels (200 iterations, chain-specialised kernel at the tuned
-chunk length), the 32-volume DAGMF batch (300 iterations, the batched
-four-inner-node kernel; every member bit for bit against its single-problem run, three
-members against the oracle at every voxel) and the differentiable Potts
-128^3 x 6 (100 unrolled iterations, checkpoint every 10; the adjoint at 64
-uniformly drawn entries against central differences of the oracle's
-forward run).  BF16 thresholded labels are compared where the oracle's two
-largest labels are further apart than BF16 resolves."""
+HMF 192^3 (tree kernel; FP32 voxel by voxel after 100 iterations, every
+storage after the workload's 400 within the bounds FP32 storage itself
+costs there), Ishikawa 256^3 with 8 labels (200 iterations, chain-specialised
+kernel at the tuned chunk length), the 32-volume DAGMF batch (300
+iterations, the batched four-inner-node kernel; every member bit for bit
+against its single-problem run, three members against the oracle at every
+voxel) and the differentiable Potts 128^3 x 6 (100 unrolled iterations,
+checkpoint every 10; the adjoint at 64 uniformly drawn entries against
+central differences of the oracle's forward run)."""
 import numpy as np
 import pytest
 
@@ -16,6 +16,7 @@ import synth
 from helpers import TOL_ARGMAX, TOL_E, TOL_U, gpu_problem, oracle_run
 
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
 
 def compare_state(name, u, q, E, P, o, tol_u, tol_e, margin=0.0):
     u_o, q_o, E_o, P_o = o
