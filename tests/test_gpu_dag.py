@@ -342,3 +342,19 @@ def test_dag4_kernel_parity(name, mode, norm):
         gp.iterate(iters)
         assert np.abs(gp.labels().cpu().numpy() - u_t).max() <= 5e-6
         assert np.abs(gp.flows().cpu().numpy() - q_t).max() <= 5e-6
+
+
+@pytest.mark.parametrize("spatial", [(1, 1, 1), (1, 1, 40), (5, 1, 1), (1, 37), (29, 1), (2, 2), (3, 65, 2),
+                                     (33, 4, 1)])
+@pytest.mark.parametrize("family", ["fused_tma_tree", "fused_tma_dag4"])
+def test_specialised_dag_kernels_on_degenerate_shapes(spatial, family):
+    """The tree and four-inner-node kernels on grids with extent-1 axes,
+    single voxels, one-plane volumes and tiles that are mostly halo, against
+    the oracle at every voxel."""
+    nn, edges = synth.hmf_tree(2, 3)
+    prob = synth.random_problem(3900 + len(spatial) + sum(spatial), spatial, nl=6, s_kind="both", n_nodes=nn,
+                                edges=edges)
+    with gpu_problem(prob) as gp:
+        gp.select_kernel(family)
+        assert gp.variant == family
+        compare(prob, gp, 25)
