@@ -474,11 +474,14 @@ struct Solver final : SolverBase {
         if constexpr (DIM == 3 && sizeof(T) == 2) {
             // 3-D, 16-bit storage: voxel pairs with packed FP32 arithmetic (the
             // one-voxel kernel is issue-bound there; with FP32 storage it is
-            // at the bandwidth roof and the pair kernel measured slower)
+            // at the bandwidth roof and the pair kernel measured slower); its
+            // pair stores need an even row pitch
+            if (a.px & 1) return cudaErrorInvalidValue;
+            using XLay = X2Layout<MAXL, T>;
             cudaError_t e = cudaFuncSetAttribute(fused_tma_x2_kernel<MAXL, T, EXACT, WITH_E, IDX32>,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, Lay::total_bytes);
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, XLay::total_bytes);
             if (e != cudaSuccess) return e;
-            fused_tma_x2_kernel<MAXL, T, EXACT, WITH_E, IDX32><<<grid, X2_NT, Lay::total_bytes, s>>>(a, m, partial);
+            fused_tma_x2_kernel<MAXL, T, EXACT, WITH_E, IDX32><<<grid, X2_NT, XLay::total_bytes, s>>>(a, m, partial);
             return cudaGetLastError();
         } else {
             // the one-voxel kernel (not instantiated for 3-D 16-bit storage, which never runs it)

@@ -72,22 +72,35 @@ __device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
 
+// One arrival on a barrier (release: the thread's earlier shared-memory
+// writes are visible to a thread whose wait on the phase succeeds).
+__device__ __forceinline__ void mbar_arrive(unsigned bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// Suspend limit of one try_wait (ns): a waiting thread sleeps until the phase
+// completes or this much time has passed, instead of re-polling; each poll
+// would take issue slots from the warps that have work.
+constexpr unsigned TMA_SUSPEND_NS = 100000u;
+
 __device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity) {
     unsigned ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
-        : "r"(bar), "r"(parity)
+        : "r"(bar), "r"(parity), "r"(TMA_SUSPEND_NS)
         : "memory");
     return ok != 0;
 }
 
 // Bounded wait: false if the budget (in clock cycles; every pipeline uses
-// TMA_WAIT_CYCLES) ran out before the phase completed.
+// TMA_WAIT_CYCLES) ran out before the phase completed.  The clock is read
+// only once the first try has failed.
 __device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity,
                                                   long long budget = TMA_WAIT_CYCLES) {
+    if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity))
         if (clock64() - t0 > budget) return false;

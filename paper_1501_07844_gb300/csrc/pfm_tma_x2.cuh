@@ -24,7 +24,8 @@
 // 16 pairs of the y-halo row and 9 pairs (x0+32, x0+33) of the x-halo column,
 // whose second voxel only pads the pair (it is computed from the staged box,
 // never stored, never read).  A pair whose second voxel lies beyond the
-// grid's last index computes it as zero and stores only the first.
+// grid's last index computes it as zero and stores the pair into the row
+// padding (the launch requires an even row pitch).
 #pragma once
 
 #include "pfm_tma.cuh"
@@ -33,6 +34,23 @@ namespace pfm {
 
 constexpr int X2_PAIRS = (FTX / 2) * FTY + FTX / 2 + FEY;  // 128 + 16 + 9 = 153
 constexpr int X2_NT = ((4 * X2_PAIRS + 31) / 32) * 32;      // 640 threads
+
+// Shared memory of the pair kernel: the staging boxes of TmaLayout in a ring
+// of four stages, four FP32 g planes, and one barrier per stage and per g
+// plane (211.6 KB for 8 labels in 16-bit storage).
+template <int MAXL, typename T>
+struct X2Layout {
+    using B = TmaLayout<MAXL, 3, T>;
+    static constexpr int STAGES = 4;
+    static constexpr int GBUF = 4;
+    static constexpr int QBX = B::QBX, QOFF = B::QOFF;
+    static constexpr int u_off = B::u_off, d_off = B::d_off, q_off = B::q_off, s_off = B::s_off;
+    static constexpr int stage_bytes = B::stage_bytes;
+    static constexpr int g_elems = B::g_elems;
+    static constexpr int g_off = STAGES * stage_bytes;
+    static constexpr int bar_off = B::align128(g_off + GBUF * g_elems * 4);
+    static constexpr int total_bytes = bar_off + 8 * (STAGES + GBUF) + 128;
+};
 
 __device__ __forceinline__ float2 f2add(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 f2mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
@@ -70,19 +88,37 @@ template <> __device__ __forceinline__ void stv2<__half>(__half* p, float2 v) {
     *reinterpret_cast<__half2*>(p) = __floats2half2_rn(fminf(fmaxf(v.x, -F16_MAX), F16_MAX),
                                                        fminf(fmaxf(v.y, -F16_MAX), F16_MAX));
 }
-// the pair, or its first voxel alone when the second is beyond the grid
-template <typename T> __device__ __forceinline__ void st_pair(T* p, float2 v, bool both) {
-    if (both)
-        stv2<T>(p, v);
-    else
-        stv<T>(p, v.x);
-}
-// a labelling pair (the F16 floor of stu applies)
-template <typename T> __device__ __forceinline__ void st_pair_u(T* p, float2 v, bool both) {
+// A labelling pair (the F16 floor of stu applies), stored as a pair even
+// when its second voxel is beyond the grid: with an even row pitch the second slot
+// of a pair that starts inside a row is inside the row too (in the padding
+// when the second voxel is beyond the grid, where the kernel computes zero
+// labels and flows; the tensor maps end at the grid, so nothing reads it).
+template <typename T> __device__ __forceinline__ void st_pair_u_padded(T* p, float2 v) {
     if constexpr (std::is_same<T, __half>::value) v = make_float2(fmaxf(v.x, F16_U_FLOOR), fmaxf(v.y, F16_U_FLOOR));
-    st_pair<T>(p, v, both);
+    stv2<T>(p, v);
 }
 
+// Synchronisation.  No block barrier holds the warps in step.  Staged plane
+// s of the chunk (plane z0-1 + s; s = 0 holds only the flows of plane z0-1)
+// sits in stage s % 4 and is handed over by that stage's TMA barrier; its
+// prox writes g plane (s-1) % 4, and every thread then arrives on that g
+// plane's barrier (its g values are written, its reads of stage s are done)
+// and waits on the barrier of plane s-1 just before the flow step that reads
+// g of plane s-1 at the neighbours.  A warp may therefore run up to one plane
+// ahead of the slowest one, and the warps' phases interleave.  The rings are
+// deep enough: the TMA load of plane s+3, issued in plane s right after the
+// wait on plane s-1's g barrier, refills the stage of plane s-1, whose readers
+// have all arrived on that barrier (planes s+1 and s+2 are in flight, so a
+// load is requested two and a half planes ahead of its use; planes 0-2 are
+// requested before the loop, 3-4 at the start of plane 1); the prox of plane s overwrites the g plane of plane
+// s-4, whose last readers (the flow steps in plane s-3) arrived on the
+// barrier of plane s-2 after them, which the writing thread has passed.  A
+// barrier's k-th use (k = 0, 1, ...) is waited on with parity k & 1: stage b
+// is used at s = b + 4k, g plane b by the prox of s = b + 1 + 4k.  The plane
+// loop is unrolled twice, so that the values carried from one plane to the
+// next (g, flows, field) alternate between two register sets instead of
+// being copied.
+//
 // EXACT: the problem has exactly MAXL labels (no per-label guards).
 // WITH_E: also reduce E(u) and P(q) of the input state into one (E, P)
 // partial per CTA, as fused_tma_kernel does (P of plane p from the prox's
@@ -94,7 +130,9 @@ fused_tma_x2_kernel(const StepArgs<MAXL, MAXL> a, const __grid_constant__ TmaMap
     static_assert(MAXL % 4 == 0, "labels are split in four");
     constexpr int DIM = 3;
     constexpr int QL = MAXL / 4;
-    using Lay = TmaLayout<MAXL, DIM, T>;
+    using Lay = X2Layout<MAXL, T>;
+    constexpr int NS = Lay::STAGES;
+    constexpr int NG = Lay::GBUF;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ int s_abort;
     __shared__ double sE[X2_NT / 32], sP[X2_NT / 32];
@@ -115,7 +153,8 @@ fused_tma_x2_kernel(const StepArgs<MAXL, MAXL> a, const __grid_constant__ TmaMap
     const unsigned bytes_d = (unsigned)(nl * TMA_UY * TMA_BX * 4);
     const unsigned bytes_q = (unsigned)(DIM * nl * TMA_QY * Lay::QBX * sizeof(T));
     const unsigned bytes_s = has_S ? (unsigned)(FTX * FTY * 4) : 0u;
-    const unsigned bar0 = smem_addr(smem + Lay::bar_off);
+    const unsigned bar0 = smem_addr(smem + Lay::bar_off);  // stage barriers
+    const unsigned gbar0 = bar0 + 8 * NS;                   // g plane barriers
     const float kexp = -a.inv_c * 1.4426950408889634f;  // exp(-(d-m)/c) = 2^((d-m) kexp)
     constexpr int qstride = TMA_QY * Lay::QBX;
     constexpr int ustride = TMA_UY * TMA_BX;
@@ -136,7 +175,8 @@ fused_tma_x2_kernel(const StepArgs<MAXL, MAXL> a, const __grid_constant__ TmaMap
 
     int inflight_hi = z0;
     if (t == 0) {
-        for (int k = 0; k < TMA_STAGES; ++k) mbar_init(bar0 + 8 * k, 1);
+        for (int k = 0; k < NS; ++k) mbar_init(bar0 + 8 * k, 1);
+        for (int k = 0; k < NG; ++k) mbar_init(gbar0 + 8 * k, X2_NT);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         s_abort = 0;
         issue(z0 - 1, 0, true);
@@ -166,7 +206,7 @@ fused_tma_x2_kernel(const StepArgs<MAXL, MAXL> a, const __grid_constant__ TmaMap
     const float cyv = ye < a.ny - 1 ? -a.ctau : 0.f;
     const float2 ncy = make_float2(cyv, cyv);
 
-    for (int k = t; k < 2 * Lay::g_elems; k += X2_NT) gbuf[k] = 0.f;
+    for (int k = t; k < NG * Lay::g_elems; k += X2_NT) gbuf[k] = 0.f;
     float cap[QL];
 #pragma unroll
     for (int i = 0; i < QL; ++i) cap[i] = (EXACT || h + 4 * i < nl) ? a.s_node[h + 4 * i] : 0.f;
@@ -185,6 +225,7 @@ fused_tma_x2_kernel(const StepArgs<MAXL, MAXL> a, const __grid_constant__ TmaMap
         }
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    // the zeroed g planes and the reads of stage 0 are complete everywhere
     if (__syncthreads_or(!ok)) {
         if (t == 0) atomicOr(a.flags, FLAG_TIMEOUT);
         s_abort = 1;
@@ -197,19 +238,25 @@ fused_tma_x2_kernel(const StepArgs<MAXL, MAXL> a, const __grid_constant__ TmaMap
     SumF sumE, sumP;
     bool bad = false;
     int p_stop = z0 - 1;
+#pragma unroll 2
     for (int p = z0; p <= z1 && !s_abort; ++p) {
         const int s = p - z0 + 1;
-        const int cs = s % 3, ps = (s + 2) % 3;
-        if (t == 0 && p + 2 <= z1 && p + 2 < a.nz) {
-            issue(p + 2, ps, false);
-            inflight_hi = p + 2;
+        const int cs = s % NS;
+        if (s == 1 && t == 0) {
+            for (int k = 2; k <= 3; ++k)
+                if (p + k <= z1 && p + k < a.nz) {
+                    issue(p + k, (s + k) % NS, false);
+                    inflight_hi = p + k;
+                }
         }
         unsigned char* cst = stage_ptr(cs);
-        float* gC = gbuf + (p & 1) * Lay::g_elems;
-        const float* gP = gbuf + ((p + 1) & 1) * Lay::g_elems;
-        ok = true;
-        if (p < a.nz) ok = mbar_wait_bounded(bar0 + 8 * cs, (unsigned)((s / 3) & 1));
-        if (!ok) atomicOr(a.flags, FLAG_TIMEOUT);
+        float* gC = gbuf + ((s + NG - 1) % NG) * Lay::g_elems;        // plane s
+        const float* gP = gbuf + ((s + NG - 2) % NG) * Lay::g_elems;  // plane s-1
+        if (p < a.nz && !mbar_wait_bounded(bar0 + 8 * cs, (unsigned)((s / NS) & 1))) {
+            atomicOr(a.flags, FLAG_TIMEOUT);
+            s_abort = 1;
+            break;
+        }
         float2 qxc[QL], qyc[QL], qzc[QL], uin[QL], txy[QL];
 #pragma unroll
         for (int i = 0; i < QL; ++i) qxc[i] = qyc[i] = qzc[i] = uin[i] = txy[i] = zero2;
@@ -304,16 +351,30 @@ fused_tma_x2_kernel(const StepArgs<MAXL, MAXL> a, const __grid_constant__ TmaMap
                         const float2 un = f2mul(u[i], inv);
                         gcur[i] = a.literal ? make_float2(u[i].x, both ? u[i].y : 0.f) : un;
                         *reinterpret_cast<float2*>(gC + j * ustride + ui) = gcur[i];
-                        if (ownerE && p < z1) st_pair_u<T>(slot_ptr<IDX32>(uout, j, p, n, plane, vox), un, both);
+                        if (ownerE && p < z1) st_pair_u_padded<T>(slot_ptr<IDX32>(uout, j, p, n, plane, vox), un);
                     }
                 }
             }
         }
 
+        // g of plane p written, stage of plane p read (before a later TMA
+        // load refills it)
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive(gbar0 + 8 * ((s + NG - 1) % NG));
+
         // ---- flow step of plane p-1 at the owned pair: g of plane p-1 at
-        // x+2 and y+1 from shared memory, own g of planes p-1 and p from
-        // registers
+        // x+2 and y+1 from shared memory (once every thread has written it),
+        // own g of planes p-1 and p from registers
         const int pm = p - 1;
+        if (pm >= z0 && !mbar_wait_bounded(gbar0 + 8 * ((s + NG - 2) % NG), (unsigned)(((s - 2) / NG) & 1))) {
+            atomicOr(a.flags, FLAG_TIMEOUT);
+            s_abort = 1;
+            break;
+        }
+        if (pm >= z0 && t == 0 && p + 3 <= z1 && p + 3 < a.nz) {
+            issue(p + 3, (s + 3) % NS, false);
+            inflight_hi = p + 3;
+        }
         if (pm >= z0 && ownerE) {
             const float czv = pm < a.nz - 1 ? -a.ctau : 0.f;
             const float2 ncz = make_float2(czv, czv);
@@ -353,9 +414,9 @@ fused_tma_x2_kernel(const StepArgs<MAXL, MAXL> a, const __grid_constant__ TmaMap
                         yy = f2mul(yy, f);
                         yz = f2mul(yz, f);
                     }
-                    st_pair<T>(slot_ptr<IDX32>(qout, j * DIM + 0, pm, n, plane, vox), yx, both);
-                    st_pair<T>(slot_ptr<IDX32>(qout, j * DIM + 1, pm, n, plane, vox), yy, both);
-                    st_pair<T>(slot_ptr<IDX32>(qout, j * DIM + 2, pm, n, plane, vox), yz, both);
+                    stv2<T>(slot_ptr<IDX32>(qout, j * DIM + 0, pm, n, plane, vox), yx);
+                    stv2<T>(slot_ptr<IDX32>(qout, j * DIM + 1, pm, n, plane, vox), yy);
+                    stv2<T>(slot_ptr<IDX32>(qout, j * DIM + 2, pm, n, plane, vox), yz);
                 }
             }
             if constexpr (WITH_E) sumE.add(eloc);
@@ -371,18 +432,14 @@ fused_tma_x2_kernel(const StepArgs<MAXL, MAXL> a, const __grid_constant__ TmaMap
             txy_prev[i] = txy[i];
         }
         sprev = scur;
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         p_stop = p;
-        if (__syncthreads_or(!ok)) {
-            if (t == 0) s_abort = 1;
-            break;
-        }
     }
     if (bad) atomicOr(a.flags, FLAG_NONFINITE);
-    if (s_abort && t == 0) {
-        for (int p = p_stop; p <= inflight_hi; ++p) {
+    // after an abort, the copies still in flight land before the block exits
+    if (t == 0) {
+        for (int p = p_stop + 1; p <= inflight_hi; ++p) {
             const int s = p - z0 + 1;
-            mbar_wait_bounded(bar0 + 8 * (s % 3), (unsigned)((s / 3) & 1));
+            mbar_wait_bounded(bar0 + 8 * (s % NS), (unsigned)((s / NS) & 1));
         }
     }
     if constexpr (WITH_E) {
