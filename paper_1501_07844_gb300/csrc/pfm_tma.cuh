@@ -78,19 +78,14 @@ __device__ __forceinline__ void mbar_arrive(unsigned bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
-// Suspend limit of one try_wait (ns): a waiting thread sleeps until the phase
-// completes or this much time has passed, instead of re-polling; each poll
-// would take issue slots from the warps that have work.
-constexpr unsigned TMA_SUSPEND_NS = 100000u;
-
 __device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity) {
     unsigned ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
-        : "r"(bar), "r"(parity), "r"(TMA_SUSPEND_NS)
+        : "r"(bar), "r"(parity)
         : "memory");
     return ok != 0;
 }
