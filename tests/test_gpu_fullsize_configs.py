@@ -18,9 +18,13 @@ from helpers import TOL_ARGMAX, TOL_E, TOL_U, gpu_problem, oracle_run
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 
 
-def compare_state(name, u, q, E, P, o, tol_u, tol_e, margin=0.0):
+def compare_state(name, u, q, E, P, o, tol_u, tol_e, margin=0.0, tol_p9999=None):
     u_o, q_o, E_o, P_o = o
     du = float(np.abs(u - u_o).max())
+    if tol_p9999 is not None:
+        p9999 = float(np.quantile(np.abs(u - u_o), 0.9999))
+        print("PARITY %s p99.99 |du| %.3e" % (name, p9999))
+        assert p9999 <= tol_p9999
     dq = float(np.abs(q - q_o).max())
     dE, dP = abs(E - E_o) / abs(E_o), abs(P - P_o) / max(abs(P_o), 1e-30)
     same = np.argmax(u, 0) == np.argmax(u_o, 0)
@@ -87,11 +91,27 @@ def test_hmf_192_every_voxel(hmf_case, storage):
     assert r["agree"] >= b["agree"] and r["dE"] <= b["dE"] and r["dP"] <= b["dP"] and r["p999"] <= b["p999"], r
 
 
+# The DAGMF volumes after 300 iterations have a few voxels (label
+# boundaries where two end-labels share the voxel, e.g. 0.175 / 0.825) that
+# amplify rounding: in the FP64 iteration, a 2^-24 relative perturbation of
+# D alone moves u there by 1.1e-4 after 300 iterations, and perturbing the
+# stored state by up to 4 FP32 ulps (uniform, independent) after every
+# iteration moves it by 7.7e-4 (99.99th percentile 3.0e-5, flows 9.9e-5).
+# The FP32 kernels, whose approximate exponential, reciprocal and summation
+# orders err by a few ulps per step, land there: max |du| 8.0e-4 (general
+# DAG kernel), 9.5e-4 (register-staged), 2.0e-3 (four-inner-node kernel),
+# 99.99th percentile 2.5-2.8e-5.  Max |du| is bounded a little above that,
+# the 99.99th percentile and the energies as everywhere else.
+DAGMF300_TOL_U = 5e-3
+DAGMF300_TOL_P9999 = 1e-4
+
+
 def test_dagmf_batch_32_volumes_300_iterations():
     """The bench's 32 volumes (46.8 M voxels) after 300 batched iterations
     (graph-replayed, tuned z-chunk and grid): every member equals its
     single-problem TMA run bit for bit; three members (the smallest, the
-    largest and one in between) match the oracle at every voxel."""
+    largest and one in between) match the oracle at every voxel within the
+    bounds above."""
     import torch
     import paper_1501_07844_gb300 as pfm
     iters = 300
@@ -117,7 +137,7 @@ def test_dagmf_batch_32_volumes_300_iterations():
                 E, P = single.energy()
             if k in sampled:
                 compare_state("dagmf member %d %s %d it" % (k, p.spatial, iters), u_b, q_b, E, P,
-                              oracle_run(p, iters), TOL_U, TOL_E)
+                              oracle_run(p, iters), DAGMF300_TOL_U, TOL_E, tol_p9999=DAGMF300_TOL_P9999)
             del u_b, q_b
     del probs
     torch.cuda.empty_cache()
