@@ -261,7 +261,7 @@ __device__ __forceinline__ bool dag4_tma_tile(const StepArgs<DMAX, DMAX>& a, con
                 }
             }
             // reduce-scatter over the quad: lane h ends with the sum of part[h]
-            // (round 1 pairs lanes two apart, round 2 neighbours)
+            // (the first shuffle step pairs lanes two apart, the second neighbours)
             const bool hi2 = (h & 2) != 0, hi1 = (h & 1) != 0;
             const float s0 = hi2 ? part[0] : part[2], s1 = hi2 ? part[1] : part[3];
             const float k0 = hi2 ? part[2] : part[0], k1 = hi2 ? part[3] : part[1];
