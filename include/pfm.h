@@ -169,12 +169,17 @@ PFM_API pfm_status pfm_set_data(pfm_problem* pb, const float* D, const float* S_
  * buffer on a copy stream of its own and returns at once, so the copy
  * overlaps the iterations already queued; the caller keeps the source
  * buffers unchanged (pinned host memory for a truly asynchronous copy) until
- * pfm_commit_data, which makes the problem's stream wait for the copy, moves
- * the staged data into place (a device-to-device copy) and validates it like
- * pfm_set_data.  A second prefetch before the commit replaces the first;
- * pfm_commit_data without a prefetch returns PFM_EINVAL.  The staging buffer
- * (D and S sized) is allocated on the first prefetch and freed with the
- * problem. */
+ * pfm_commit_data.  The staged data is validated like pfm_set_data's, on the
+ * copy stream.  pfm_commit_data makes the problem's stream wait for the copy
+ * and puts the staged data in place: the staging buffers and the problem's
+ * D / S trade places (no device work; the next prefetch waits for the work
+ * queued before the commit, which still reads the old buffers), except for a
+ * member of a batch, whose buffers the batch's kernel arguments hold, where
+ * the staged data is copied into place on the problem's stream.  A failed
+ * validation shows at the next call that checks the problem's flags.  A
+ * second prefetch before the commit replaces the first; pfm_commit_data
+ * without a prefetch returns PFM_EINVAL.  The staging buffers (D and S
+ * sized) are allocated on the first prefetch and freed with the problem. */
 PFM_API pfm_status pfm_prefetch_data(pfm_problem* pb, const float* D, const float* S_field);
 PFM_API pfm_status pfm_commit_data(pfm_problem* pb);
 

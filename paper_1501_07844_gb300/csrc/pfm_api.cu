@@ -10,6 +10,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <utility>
 #include <string>
 #include <vector>
 
@@ -269,13 +270,17 @@ struct pfm_problem {
     std::vector<float> W;  // [nn][nl]
     int64_t iters = 0, launches = 0;
     pfm::SolverBase* solver = nullptr;
-    // double-buffered upload (pfm_prefetch_data / pfm_commit_data)
+    // double-buffered upload (pfm_prefetch_data / pfm_commit_data): the
+    // staging buffers and D / S trade places at a commit (batch members, whose
+    // buffers the batch's kernel arguments hold, copy instead)
     float* D_stage = nullptr;
     float* S_stage = nullptr;
+    unsigned* stage_flags = nullptr;  // validation of the staged data
     cudaStream_t copy_stream = nullptr;
     cudaEvent_t staged = nullptr;    // the prefetch copy is complete
-    cudaEvent_t consumed = nullptr;  // the last commit has moved the staged data
+    cudaEvent_t consumed = nullptr;  // work enqueued before the last commit (readers of the staging buffers) is done
     bool stage_pending = false;
+    bool in_batch = false;
     // asynchronous argmax read-back (pfm_get_argmax_async)
     int* am_buf = nullptr;
     cudaEvent_t am_ready = nullptr;   // the argmax kernel has written am_buf
@@ -346,7 +351,7 @@ void free_all(pfm_problem* pb) {
     if (pb->copy_stream) cudaStreamSynchronize(pb->copy_stream);
     void* ptrs[] = {pb->u[0], pb->u[1] != pb->u[0] ? pb->u[1] : nullptr, pb->q[0],
                     pb->q[1] != pb->q[0] ? pb->q[1] : nullptr, pb->D, pb->S, pb->abuf, pb->snode_dev,
-                    pb->flags, pb->partial, pb->result, pb->D_stage, pb->S_stage};
+                    pb->flags, pb->partial, pb->result, pb->D_stage, pb->S_stage, pb->stage_flags};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (pb->am_done) cudaEventSynchronize(pb->am_done);
@@ -594,13 +599,20 @@ pfm_status pfm_prefetch_data(pfm_problem* pb, const float* D, const float* S_fie
             PFM_CUDA(cudaMalloc(&pb->S_stage, (size_t)pb->n * 4), "alloc staging S");
             PFM_CUDA(cudaMemset(pb->S_stage, 0, (size_t)pb->n * 4), "memset");
         }
+        PFM_CUDA(cudaMalloc(&pb->stage_flags, sizeof(unsigned)), "alloc staging flags");
     }
-    // the staging buffer is free once the last commit has moved it (a
-    // prefetch not yet committed is simply overwritten, in copy-stream order)
+    // the staging buffers are free once the work enqueued before the last
+    // commit (which may read them: they were D and S then) is done; a
+    // prefetch not yet committed is simply overwritten, in copy-stream order
     PFM_CUDA(cudaStreamWaitEvent(pb->copy_stream, pb->consumed, 0), "wait");
     const long long rows = (long long)pb->ny * pb->nz;
     PFM_CUDA(copy_rows(pb->D_stage, pb->px, D, pb->nx, pb->nx, pb->nl * rows, pb->copy_stream), "copy D");
     if (S_field) PFM_CUDA(copy_rows(pb->S_stage, pb->px, S_field, pb->nx, pb->nx, rows, pb->copy_stream), "copy S");
+    // validated here, off the compute stream; the commit carries the result over
+    PFM_CUDA(cudaMemsetAsync(pb->stage_flags, 0, sizeof(unsigned), pb->copy_stream), "memset");
+    PFM_CUDA(pfm::launch_validate(pb->D_stage, (long long)pb->nl * pb->n, pb->S_stage, pb->n, pb->stage_flags,
+                                  pb->copy_stream),
+             "validate");
     PFM_CUDA(cudaEventRecord(pb->staged, pb->copy_stream), "event");
     pb->stage_pending = true;
     return PFM_OK;
@@ -610,12 +622,22 @@ pfm_status pfm_commit_data(pfm_problem* pb) {
     if (!pb) return fail(PFM_EINVAL, "NULL problem");
     if (!pb->stage_pending) return fail(PFM_EINVAL, "no data prefetched since the last commit");
     PFM_CUDA(cudaStreamWaitEvent(pb->stream, pb->staged, 0), "wait");
-    PFM_CUDA(cudaMemcpyAsync(pb->D, pb->D_stage, (size_t)pb->nl * pb->n * 4, cudaMemcpyDeviceToDevice, pb->stream),
-             "move D");
-    if (pb->S)
-        PFM_CUDA(cudaMemcpyAsync(pb->S, pb->S_stage, (size_t)pb->n * 4, cudaMemcpyDeviceToDevice, pb->stream), "move S");
+    if (pb->in_batch) {
+        PFM_CUDA(cudaMemcpyAsync(pb->D, pb->D_stage, (size_t)pb->nl * pb->n * 4, cudaMemcpyDeviceToDevice, pb->stream),
+                 "move D");
+        if (pb->S)
+            PFM_CUDA(cudaMemcpyAsync(pb->S, pb->S_stage, (size_t)pb->n * 4, cudaMemcpyDeviceToDevice, pb->stream),
+                     "move S");
+    } else {
+        // the kernels enqueued before this commit still read the old D and S,
+        // which become the staging buffers: the next prefetch waits for them
+        std::swap(pb->D, pb->D_stage);
+        std::swap(pb->S, pb->S_stage);
+        pb->solver->set_data(pb->D, pb->S);
+        pb->solver->prepare_tma(pb->u, pb->q, pb->D, pb->S);
+    }
+    PFM_CUDA(pfm::launch_merge_flags(pb->stage_flags, pb->flags, pb->stream), "flags");
     PFM_CUDA(cudaEventRecord(pb->consumed, pb->stream), "event");
-    PFM_CUDA(pfm::launch_validate(pb->D, (long long)pb->nl * pb->n, pb->S, pb->n, pb->flags, pb->stream), "validate");
     pb->launches++;
     pb->stage_pending = false;
     return PFM_OK;
@@ -1231,6 +1253,7 @@ pfm_status pfm_batch_create(int n, const pfm_desc* descs, const pfm_params* para
             batch_free(b);
             return fail(st, "%s", msg.c_str());
         }
+        pb->in_batch = true;
         b->probs.push_back(pb);
         maxl = std::max(maxl, pb->nl);
         maxn = std::max(maxn, pb->nn);

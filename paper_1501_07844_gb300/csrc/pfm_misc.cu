@@ -247,6 +247,16 @@ cudaError_t launch_wait_selftest(unsigned* flags, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+__global__ void merge_flags_kernel(const unsigned* src, unsigned* dst) {
+    const unsigned f = *src;
+    if (f) atomicOr(dst, f);
+}
+
+cudaError_t launch_merge_flags(const unsigned* src, unsigned* dst, cudaStream_t s) {
+    merge_flags_kernel<<<1, 1, 0, s>>>(src, dst);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_validate(const float* D, long long nD, const float* S, long long nS, unsigned* flags,
                             cudaStream_t s) {
     validate_kernel<<<1216, NT, 0, s>>>(D, nD, S, nS, flags);

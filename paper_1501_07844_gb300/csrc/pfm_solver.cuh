@@ -337,6 +337,9 @@ struct SolverBase {
     // Builds TMA descriptors for the double-buffered state; true if the
     // TMA-pipelined fused kernel can run on this problem.
     virtual bool prepare_tma(void* const* u, void* const* q, const float* D, const float* S) { return false; }
+    // New data buffers (D, S) for later launches; the caller then prepares
+    // the tensor maps over them again (prepare_tma).
+    virtual void set_data(const float* D, const float* S) = 0;
     bool use_tma = true;  // cleared to force the register-staged fused kernel
     bool use_tree = true;  // cleared to run a two-level tree on the general TMA DAG kernel
     bool use_ishi = true;  // cleared to run an Ishikawa chain on the general TMA DAG kernel
@@ -375,6 +378,11 @@ struct Solver final : SolverBase {
     Dag4Shape dag4{};
     bool inplace_ready = false;
     InplaceMaps inplace_maps{};
+
+    void set_data(const float* D, const float* S) override {
+        base.D = D;
+        base.S = S;
+    }
 
     explicit Solver(const ProblemView& v) {
         base = make_step_args<MAXL, MAXN, IS_DAG>(v, 0);
@@ -1176,6 +1184,8 @@ cudaError_t launch_set_labels(const float* src, int storage, int nl, long long n
                               void* dst, unsigned* flags, cudaStream_t s);
 cudaError_t launch_set_flows(const float* src, int storage, int nn, int ndim, int nx, int ny, int nz, int px,
                              const float* s_node_dev, const float* S, int aniso, void* dst, cudaStream_t s);
+// ORs *src into *dst (one thread).
+cudaError_t launch_merge_flags(const unsigned* src, unsigned* dst, cudaStream_t s);
 cudaError_t launch_validate(const float* D, long long nD, const float* S, long long nS, unsigned* flags,
                             cudaStream_t s);
 cudaError_t launch_energy_final(const double* partial, int blocks, double* out, unsigned* flags, cudaStream_t s);

@@ -347,6 +347,90 @@ def test_prefetch_commit_equals_set_data():
         assert torch.equal(a.labels(), b.labels()) and torch.equal(a.flows(), b.flows())
 
 
+def _prefetch_kinds(kind):
+    if kind == "hmf":
+        return synth.hmf_problem(seed=3310, shape=(11, 19, 40), iters=30), {}
+    if kind == "ishikawa":
+        return synth.ishikawa_problem(3311, (10, 17, 38), nlev=4), {}
+    if kind == "dagmf":
+        return synth.dagmf_problem(3312, (9, 18, 37), iters=30), {}
+    prob = synth.random_problem(3313, (10, 17, 39), nl=5, s_kind="both")
+    if kind == "potts_inplace":
+        import paper_1501_07844_gb300 as pfm
+        return prob, {"schedule": pfm.INPLACE}
+    if kind == "potts_bf16":
+        return prob, {"storage": 1}
+    return prob, {}
+
+
+@pytest.mark.parametrize("kind", ["potts", "potts_inplace", "potts_bf16", "hmf", "ishikawa", "dagmf"])
+def test_prefetch_commit_rounds_equal_set_data(kind):
+    """Several prefetch / commit rounds, in which the data buffers and the
+    staging buffers trade places and the kernels' tensor maps follow them,
+    give bit for bit the state of the same sequence with pfm_set_data, on
+    every kernel family; a staged D with a NaN is reported by the next
+    call that checks the problem (the energy)."""
+    import torch
+    import paper_1501_07844_gb300 as pfm
+    prob, kw = _prefetch_kinds(kind)
+    rng = np.random.default_rng(77)
+    data = []
+    for k in range(3):
+        D = (prob.D * rng.uniform(0.7, 1.3, size=prob.D.shape)).astype(np.float32)
+        S = None if prob.S_field is None else (prob.S_field * rng.uniform(0.5, 1.5, size=prob.S_field.shape)).astype(
+            np.float32)
+        data.append((torch.from_numpy(D).pin_memory(), None if S is None else torch.from_numpy(S).pin_memory()))
+    with gpu_problem(prob, **kw) as a, gpu_problem(prob, **kw) as b:
+        a.iterate(5)
+        b.iterate(5)
+        for k, (iters_before, iters_after) in enumerate([(3, 4), (0, 6), (2, 5)]):
+            D, S = data[k % 3] if k < 2 else data[0]
+            a.prefetch_data(D, S)
+            a.iterate(iters_before)      # still on the previous data
+            a.commit_data()
+            a.iterate(iters_after)
+            b.iterate(iters_before)
+            b.set_data(D, S)
+            b.iterate(iters_after)
+        assert torch.equal(a.labels(), b.labels()) and torch.equal(a.flows(), b.flows())
+        assert a.energy() == b.energy()
+        bad = data[1][0].clone()
+        bad[0].view(-1)[7] = float("nan")
+        a.prefetch_data(bad, data[1][1])
+        a.commit_data()
+        a.iterate(1)
+        with pytest.raises(pfm.PfmError) as ei:
+            a.energy()
+        assert ei.value.name == "PFM_ENONFINITE"
+
+
+def test_prefetch_commit_on_batch_member():
+    """A batch member's prefetch / commit copies the staged data into the
+    buffers the batch's kernels read: the batch then iterates on the new data
+    exactly as after pfm_set_data on the member."""
+    import torch
+    import paper_1501_07844_gb300 as pfm
+    vols = [synth.dagmf_problem(3320 + k, (8, 13, 35 + 3 * k), iters=30) for k in range(3)]
+    new = torch.from_numpy((vols[1].D * 1.25).astype(np.float32)).pin_memory()
+    newS = torch.from_numpy(vols[1].S_field).pin_memory()
+    states = []
+    for mode in ("prefetch", "set"):
+        probs = [dict(D=torch.from_numpy(p.D).cuda(), S_field=torch.from_numpy(p.S_field).cuda(), s_node=p.s_node,
+                      n_nodes=p.n_nodes, edges=p.edges) for p in vols]
+        with pfm.Batch(probs, c=0.5, tau=0.11) as bt:
+            bt.iterate(4)
+            m = bt.members[1]
+            if mode == "prefetch":
+                m.prefetch_data(new, newS)
+                m.commit_data()
+            else:
+                m.set_data(new, newS)
+            bt.iterate(6)
+            states.append([(bm.labels().cpu(), bm.flows().cpu()) for bm in bt.members])
+    for (ua, qa), (ub, qb) in zip(*states):
+        assert torch.equal(ua, ub) and torch.equal(qa, qb)
+
+
 @pytest.mark.parametrize("storage", [0, 1, 2], ids=["f32", "bf16", "f16"])
 def test_state_async_equals_readback(storage):
     """pfm_get_state_async (device destinations, stream-ordered, no wait)
