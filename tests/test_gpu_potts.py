@@ -471,7 +471,7 @@ def test_argmax_async_equals_argmax():
         assert torch.equal(h1, ref1) and torch.equal(h2, gp.argmax().cpu())
 
 
-@pytest.mark.parametrize("kind", ["fused_f32", "fused_bf16", "inplace", "hmf"])
+@pytest.mark.parametrize("kind", ["fused_f32", "fused_bf16", "fused_f16", "inplace", "hmf"])
 def test_chunk_length_leaves_iterates_unchanged(kind):
     """The z-chunk length (planes per CTA) changes only which CTA runs a
     plane: the iterates are bit-identical for every length, the energy
@@ -482,7 +482,7 @@ def test_chunk_length_leaves_iterates_unchanged(kind):
     else:
         prob = synth.potts3d_problem(seed=2600, nl=8, shape=(23, 18, 45))
     sched = pfm.INPLACE if kind == "inplace" else pfm.FUSED
-    storage = pfm.BF16 if kind == "fused_bf16" else pfm.F32
+    storage = {"fused_bf16": pfm.BF16, "fused_f16": pfm.F16}.get(kind, pfm.F32)
     res = []
     for zc in (1, 4, 7, 64):
         with gpu_problem(prob, schedule=sched, storage=storage) as gp:
