@@ -91,11 +91,9 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity) {
 }
 
 // Bounded wait: false if the budget (in clock cycles; every pipeline uses
-// TMA_WAIT_CYCLES) ran out before the phase completed.  The clock is read
-// only once the first try has failed.
+// TMA_WAIT_CYCLES) ran out before the phase completed.
 __device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity,
                                                   long long budget = TMA_WAIT_CYCLES) {
-    if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity))
         if (clock64() - t0 > budget) return false;
