@@ -34,6 +34,15 @@ namespace pfm {
 // Tile of the fused z-marching kernel: each CTA owns FTX x FTY voxels of
 // every plane of a z-chunk and recomputes the labelling on a one-voxel
 // halo at +x and +y (the gradient's forward neighbours).
+// sqrt(x) by the hardware approximation (relative error about 2^-23; a
+// subnormal x counts as 0), for the TV norms of the energy that the last
+// iteration of a step reduces alongside its update.
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 constexpr int FTX = 32;
 constexpr int FTY = 8;
 constexpr int FEX = FTX + 1;

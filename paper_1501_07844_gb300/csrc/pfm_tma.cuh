@@ -445,7 +445,7 @@ fused_tma_kernel(const StepArgs<MAXL, MAXL> a, const __grid_constant__ TmaMaps m
                         // staged u
                         float gz = 0.f;
                         if constexpr (DIM == 3) gz = cz != 0.f ? uin[i] - uin_prev[i] : 0.f;
-                        const float nv = a.aniso ? txy_prev[i] + fabsf(gz) : sqrtf(fmaf(gz, gz, txy_prev[i]));
+                        const float nv = a.aniso ? txy_prev[i] + fabsf(gz) : sqrt_approx(fmaf(gz, gz, txy_prev[i]));
                         eloc = fmaf(sj, nv, eloc);
                     }
                     project_nb<DIM>(yv, sj, a.aniso);

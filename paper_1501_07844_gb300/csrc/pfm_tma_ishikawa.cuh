@@ -294,7 +294,7 @@ ishikawa_tma_kernel(const StepArgs<MAXL, MAXN> a, const __grid_constant__ TmaMap
                     if constexpr (WITH_E) {
                         // TV of level j on the input labelling, plane p-1
                         const float gz = cz != 0.f ? gin[i] - ginp[i] : 0.f;
-                        const float nv = a.aniso ? txy_prev[i] + fabsf(gz) : sqrtf(fmaf(gz, gz, txy_prev[i]));
+                        const float nv = a.aniso ? txy_prev[i] + fabsf(gz) : sqrt_approx(fmaf(gz, gz, txy_prev[i]));
                         eloc = fmaf(cap[i] * sf, nv, eloc);
                     }
                     const float* gj = gP + j * ustride;

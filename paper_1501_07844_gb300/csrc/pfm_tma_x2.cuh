@@ -396,8 +396,8 @@ fused_tma_x2_kernel(const StepArgs<MAXL, MAXL> a, const __grid_constant__ TmaMap
                         // TV term of plane p-1 on the input labelling
                         const float2 gz = czv != 0.f ? f2sub(uin[i], uin_prev[i]) : zero2;
                         const float2 tp = txy_prev[i];
-                        const float na = a.aniso ? tp.x + fabsf(gz.x) : sqrtf(fmaf(gz.x, gz.x, tp.x));
-                        const float nb = a.aniso ? tp.y + fabsf(gz.y) : sqrtf(fmaf(gz.y, gz.y, tp.y));
+                        const float na = a.aniso ? tp.x + fabsf(gz.x) : sqrt_approx(fmaf(gz.x, gz.x, tp.x));
+                        const float nb = a.aniso ? tp.y + fabsf(gz.y) : sqrt_approx(fmaf(gz.y, gz.y, tp.y));
                         eloc = fmaf(sj.x, na, eloc);
                         if (both) eloc = fmaf(sj.y, nb, eloc);
                     }
