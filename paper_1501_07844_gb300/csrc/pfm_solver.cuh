@@ -18,6 +18,7 @@
 #include "pfm_tma_inplace.cuh"
 #include "pfm_tma_ishikawa.cuh"
 #include "pfm_tma_dag4.cuh"
+#include "pfm_tma_energy4.cuh"
 #include "pfm_tma_tree.cuh"
 #include "pfm_tma_x2.cuh"
 
@@ -754,11 +755,15 @@ struct Solver final : SolverBase {
     }
 
     long long tma_energy_blocks(int zc) const override {
-        // one partial per CTA of the TMA energy kernel or of an iteration
-        // that reduces its input (Potts and Ishikawa kernels: 32 x 8 tiles)
-        if (!((kTmaCapable && tma_ready) || (IS_DAG && ishi_ready))) return 0;
+        // one partial per CTA of a TMA energy kernel or of an iteration that
+        // reduces its input (Potts and Ishikawa kernels: 32 x 8 tiles; the
+        // four-inner-node energy kernel: 32 x 4)
         zc = zc < 1 ? 1 : zc;
-        return (long long)((base.nx + FTX - 1) / FTX) * ((base.ny + FTY - 1) / FTY) * ((base.nz + zc - 1) / zc);
+        const long long chunks = (base.nz + zc - 1) / zc, tx = (base.nx + FTX - 1) / FTX;
+        long long nb = 0;
+        if ((kTmaCapable && tma_ready) || (IS_DAG && ishi_ready)) nb = tx * ((base.ny + FTY - 1) / FTY) * chunks;
+        if (IS_DAG && dag4_ready) nb = std::max(nb, tx * ((base.ny + DTY - 1) / DTY) * chunks);
+        return nb;
     }
 
     cudaError_t energy(const void* u, const void* q, double* partial, int max_blocks, int zc, cudaStream_t s,
@@ -777,6 +782,27 @@ struct Solver final : SolverBase {
                 a.zc = zc < 1 ? 1 : zc;
                 dim3 grid((a.nx + FTX - 1) / FTX, (a.ny + FTY - 1) / FTY, (a.nz + a.zc - 1) / a.zc);
                 energy_tma_kernel<MAXL, DIM, T><<<grid, ENERGY_TMA_NT, Lay::total_bytes, s>>>(a, tma_maps[k], partial);
+                *nblocks = (int)nb;
+                return cudaGetLastError();
+            }
+        }
+        if constexpr (kDagTmaCapable) {
+            // DAGs with at most four inner nodes (HMF, DAGMF): the TMA energy
+            // kernel in the four-inner-node layout, over the iteration's maps
+            const int zcl = zc < 1 ? 1 : zc;
+            const long long nb = (long long)((a.nx + FTX - 1) / FTX) * ((a.ny + DTY - 1) / DTY) *
+                                 ((a.nz + zcl - 1) / zcl);
+            if (dag4_ready && nb <= max_blocks) {
+                StepArgs<DMAX, DMAX> w = widen_args(a);
+                w.zc = zcl;
+                const TreeTmaLayout lay(w.nl, w.nn, DIM, (int)sizeof(T));
+                const int smem = lay.g_off + 64 + 128;  // the stages and their barriers
+                const int k = (u == tma_u[0]) ? 0 : 1;
+                cudaError_t e = cudaFuncSetAttribute(energy_dag4_tma_kernel<DIM, T>,
+                                                     cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+                if (e != cudaSuccess) return e;
+                dim3 grid((a.nx + FTX - 1) / FTX, (a.ny + DTY - 1) / DTY, (a.nz + zcl - 1) / zcl);
+                energy_dag4_tma_kernel<DIM, T><<<grid, ENERGY4_NT, smem, s>>>(w, tree_maps[k], dag4, partial);
                 *nblocks = (int)nb;
                 return cudaGetLastError();
             }
