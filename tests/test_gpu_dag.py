@@ -3,7 +3,7 @@ import numpy as np
 import pytest
 
 import synth
-from helpers import TOL_E, compare, gpu_problem, oracle_run
+from helpers import TOL_E, compare, gpu_problem, oracle_energy, oracle_run
 
 pytestmark = pytest.mark.gpu
 
@@ -358,3 +358,35 @@ def test_specialised_dag_kernels_on_degenerate_shapes(spatial, family):
         gp.select_kernel(family)
         assert gp.variant == family
         compare(prob, gp, 25)
+
+
+@pytest.mark.parametrize("name", ["dagmf", "dagmf_2d", "hmf", "ishikawa3_2d"])
+@pytest.mark.parametrize("norm", [0, 1], ids=["iso", "aniso"])
+@pytest.mark.parametrize("storage", [0, 1], ids=["f32", "bf16"])
+def test_four_inner_node_energy_kernel(name, norm, storage):
+    """E(u) and P(q) from the four-inner-node energy kernel (the TMA path of
+    pfm_energy on these DAGs) against the oracle's energy of the same state,
+    at z-chunk lengths that put chunk boundaries everywhere, for an iterated
+    state and for an imported random one (labels of unit sum, flows as
+    pfm_set_flows stores them: projected, zero normal flow at the far
+    boundary)."""
+    import torch
+    prob = dag4_case(name)
+    rng = np.random.default_rng(3900 + len(name) + norm)
+    with gpu_problem(prob, norm=norm, storage=storage) as gp:
+        gp.iterate(15)
+        states = [(gp.labels().cpu().numpy(), gp.flows().cpu().numpy())]
+        u = rng.uniform(0.01, 1.0, size=states[0][0].shape).astype(np.float32)
+        u /= u.sum(axis=0, keepdims=True)
+        q = rng.uniform(-0.2, 0.2, size=states[0][1].shape).astype(np.float32)
+        states.append((u, q))
+        for u, q in states:
+            gp.set_labels(torch.from_numpy(u).cuda())
+            gp.set_flows(torch.from_numpy(q).cuda())
+            u_s, q_s = gp.labels().cpu().numpy(), gp.flows().cpu().numpy()   # as stored (16-bit rounding)
+            E_o, P_o = oracle_energy(prob, u_s, q_s, norm=norm)
+            for zc in (1, 3, 64):
+                gp.chunk_length = zc
+                E, P = gp.energy()
+                assert abs(E - E_o) <= 1e-5 * abs(E_o), (zc, E, E_o)
+                assert abs(P - P_o) <= 1e-5 * abs(P_o) + 1e-5, (zc, P, P_o)
