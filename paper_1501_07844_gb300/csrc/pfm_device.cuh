@@ -35,8 +35,8 @@ namespace pfm {
 // every plane of a z-chunk and recomputes the labelling on a one-voxel
 // halo at +x and +y (the gradient's forward neighbours).
 // sqrt(x) by the hardware approximation (relative error about 2^-23; a
-// subnormal x counts as 0), for the TV norms of the energy that the last
-// iteration of a step reduces alongside its update.
+// subnormal x counts as 0), for the TV norms of the energy E (the TMA energy
+// kernels and the iterations that reduce their input).
 __device__ __forceinline__ float sqrt_approx(float x) {
     float y;
     asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));

@@ -638,7 +638,7 @@ energy_tma_kernel(const StepArgs<MAXL, MAXL> a, const __grid_constant__ TmaMaps 
                         float r2 = 0.f;
 #pragma unroll
                         for (int k = 0; k < DIM; ++k) r2 = fmaf(gr[k], gr[k], r2);
-                        nv = sqrtf(r2);
+                        nv = sqrt_approx(r2);
                     }
                     tv = fmaf(a.s_node[j] * sf, nv, tv);
                     const T* qx = qS + (j * DIM + 0) * qstride;
