@@ -1366,6 +1366,29 @@ pfm_status pfm_batch_iterate(pfm_batch* b, int n_iters) {
 pfm_status pfm_batch_energy(pfm_batch* b, double* primal, double* dual) {
     if (!b || !primal || !dual) return fail(PFM_EINVAL, "NULL argument");
     pfm_status first = PFM_OK;
+    if (b->runner && b->runner->has_energy()) {
+        // one launch over every member's tiles, one reduction per member, one
+        // synchronisation for the results and every member's flags
+        const size_t n = b->probs.size();
+        PFM_CUDA(b->runner->energy(b->probs[0]->cur, b->stream), "batch energy");
+        b->launches += 2;
+        std::vector<double> h(2 * n);
+        std::vector<unsigned> f(n, 0u);
+        PFM_CUDA(cudaMemcpyAsync(h.data(), b->runner->energy_out(), sizeof(double) * 2 * n, cudaMemcpyDeviceToHost,
+                                 b->stream),
+                 "read energy");
+        for (size_t k = 0; k < n; ++k)
+            PFM_CUDA(cudaMemcpyAsync(&f[k], b->probs[k]->flags, sizeof(unsigned), cudaMemcpyDeviceToHost, b->stream),
+                     "read flags");
+        PFM_CUDA(cudaStreamSynchronize(b->stream), "stream sync");
+        for (size_t k = 0; k < n; ++k) {
+            primal[k] = h[2 * k];
+            dual[k] = h[2 * k + 1];
+            const pfm_status st = flags_status(f[k]);
+            if (st != PFM_OK && first == PFM_OK) first = st;
+        }
+        return first;
+    }
     for (size_t k = 0; k < b->probs.size(); ++k) {
         pfm_status st = pfm_energy(b->probs[k], &primal[k], &dual[k]);
         if (st != PFM_OK && first == PFM_OK) first = st;

@@ -832,6 +832,13 @@ struct BatchBase {
     virtual int n_items() const = 0;
     // Resident CTAs per SM of the batched kernel (occupancy).
     virtual int ctas_per_sm() const = 0;
+    // E and P of every member's state `parity` into energy_out()[2 k],
+    // [2 k + 1] on the device: one launch over the batch's tiles and one
+    // fixed-order reduction per member.  Runners without it return false
+    // from has_energy (the members are then reduced one by one).
+    virtual bool has_energy() const { return false; }
+    virtual cudaError_t energy(int parity, cudaStream_t s) { return cudaErrorNotSupported; }
+    virtual const double* energy_out() const { return nullptr; }
 };
 
 template <int MAXL, int MAXN, int DIM, bool IS_DAG, typename T>
@@ -1032,13 +1039,16 @@ struct BatchDag4Tma final : BatchBase {
     Dag4Shape* shapes = nullptr;
     int4* items = nullptr;
     int* counter = nullptr;     // next work item of the running launch
-    int nvol = 0, nitems = 0, smem = 0, bar_off = 0;
+    int* ebegin = nullptr;      // [nvol + 1]: each member's first work item
+    double* epartial = nullptr; // [nitems][2]: (E, P) of every work item
+    double* eout = nullptr;     // [nvol][2]
+    int nvol = 0, nitems = 0, smem = 0, bar_off = 0, esmem = 0;
     bool idx32 = true;
 
     ~BatchDag4Tma() override { release(); }
 
     void release() {
-        void* ptrs[] = {args, maps, shapes, items, counter};
+        void* ptrs[] = {args, maps, shapes, items, counter, ebegin, epartial, eout};
         for (void* p : ptrs)
             if (p) cudaFree(p);
         args = nullptr;
@@ -1046,6 +1056,21 @@ struct BatchDag4Tma final : BatchBase {
         shapes = nullptr;
         items = nullptr;
         counter = nullptr;
+        ebegin = nullptr;
+        epartial = nullptr;
+        eout = nullptr;
+    }
+
+    bool has_energy() const override { return true; }
+    const double* energy_out() const override { return eout; }
+    cudaError_t energy(int parity, cudaStream_t s) override {
+        batched_energy_dag4_tma_kernel<DIM, T><<<nitems, ENERGY4_NT, esmem, s>>>(
+            args + (size_t)parity * nvol, maps + (size_t)parity * nvol, shapes, items, epartial);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        energy_final_ranges_kernel<<<nvol, ENERGY_RANGES_NT, 0, s>>>(epartial, ebegin, args + (size_t)parity * nvol,
+                                                                       eout);
+        return cudaGetLastError();
     }
 
     // True if every member can run the four-inner-node kernel.
@@ -1069,7 +1094,9 @@ struct BatchDag4Tma final : BatchBase {
         std::vector<int4> work;
         smem = 0;
         bar_off = 0;
+        esmem = 0;
         idx32 = true;
+        std::vector<int> begin((size_t)n + 1, 0);
         for (int k = 0; k < n; ++k) {
             const ProblemView& v = m[k].view;
             idx32 = idx32 && (long long)DIM * v.nn * v.n <= 0xFFFFFFFFll;
@@ -1078,6 +1105,8 @@ struct BatchDag4Tma final : BatchBase {
             const TreeTmaLayout lay(v.nl, v.nn, DIM, es);
             smem = std::max(smem, lay.total);
             bar_off = std::max(bar_off, lay.bar_off);
+            esmem = std::max(esmem, lay.g_off + 64 + 128);  // the energy kernel: stages and barriers
+            begin[k] = (int)work.size();
             for (int p = 0; p < 2; ++p) {
                 Args a = base;
                 a.u_in = m[k].u[p];
@@ -1097,7 +1126,16 @@ struct BatchDag4Tma final : BatchBase {
         // the barriers sit past every member's buffers
         smem = std::max(smem, bar_off + 64 + 128);
         nitems = (int)work.size();
+        begin[n] = nitems;
         cudaError_t e;
+        if ((e = cudaMalloc(&ebegin, sizeof(int) * begin.size())) != cudaSuccess) return e;
+        if ((e = cudaMalloc(&epartial, sizeof(double) * 2 * (size_t)nitems)) != cudaSuccess) return e;
+        if ((e = cudaMalloc(&eout, sizeof(double) * 2 * (size_t)n)) != cudaSuccess) return e;
+        if ((e = cudaMemcpy(ebegin, begin.data(), sizeof(int) * begin.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
+            return e;
+        if ((e = cudaFuncSetAttribute(batched_energy_dag4_tma_kernel<DIM, T>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, esmem)) != cudaSuccess)
+            return e;
         if ((e = cudaMalloc(&args, sizeof(Args) * ha.size())) != cudaSuccess) return e;
         if ((e = cudaMalloc(&maps, sizeof(TmaMaps) * hm.size())) != cudaSuccess) return e;
         if ((e = cudaMalloc(&shapes, sizeof(Dag4Shape) * hs.size())) != cudaSuccess) return e;

@@ -17,7 +17,8 @@
 // The planes of a tile arrive through the same boxes and tensor maps as the
 // iteration's (three-stage ring, plane r and r+1 staged together, one block
 // barrier per plane); each CTA leaves one (E, P) partial in FP64, summed in
-// a fixed order by energy_final_kernel.
+// a fixed order by energy_final_kernel (per problem; for a batch, one launch
+// over every member's tiles and energy_final_ranges_kernel).
 #pragma once
 
 #include "pfm_tma_dag4.cuh"
@@ -39,29 +40,32 @@ __device__ __forceinline__ float quad_reduce_scatter(const float (&part)[DAG4_IN
     return (hi1 ? r1 : r0) + __shfl_xor_sync(0xffffffffu, hi1 ? r0 : r1, 1);
 }
 
+// One tile (bx, by) of z-chunk bz of one problem: E and P of its owned
+// voxels into out[0], out[1].  smem: the aligned dynamic shared memory (the
+// stages of the problem's layout, then three barriers).  Every thread of the
+// CTA calls it.
 template <int DIM, typename T>
-__global__ void __launch_bounds__(ENERGY4_NT, 1)
-energy_dag4_tma_kernel(const StepArgs<DMAX, DMAX> a, const __grid_constant__ TmaMaps maps,
-                       const __grid_constant__ Dag4Shape sh, double* partial) {
+__device__ __forceinline__ void energy_dag4_tile(const StepArgs<DMAX, DMAX>& a, const TmaMaps& maps,
+                                                 const Dag4Shape& sh, int bx, int by, int bz, unsigned char* smem,
+                                                 double* out) {
     constexpr int QOFF = 16 / (int)sizeof(T);
     constexpr int ustride = DAG_UY * TMA_BX;
     constexpr int NS = DAG4_SLOTS;
     constexpr int NI = DAG4_INNER;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ int s_abort;
     __shared__ double sE[ENERGY4_NT / 32], sP[ENERGY4_NT / 32];
-    unsigned char* smem = dag_smem_base(smem_raw);
+    // scalars read once (the batched kernel's arguments live in global memory)
     const int nl = a.nl, nn = a.nn;
-    const int nx = a.nx, ny = a.ny, nz = a.nz, aniso = a.aniso;
+    const int nx = a.nx, ny = a.ny, nz = a.nz, aniso = a.aniso, zc = a.zc;
     const TreeTmaLayout lay(nl, nn, DIM, (int)sizeof(T));
     const int QBX = lay.qbx;
     const int qstride = DAG_QY * QBX;
     const int t = threadIdx.x;
     const int h = t & 3;
     const int v = t >> 2;
-    const int x0 = blockIdx.x * FTX, y0 = blockIdx.y * DTY;
-    const int z0 = blockIdx.z * a.zc;
-    const int z1 = min(z0 + a.zc, nz);
+    const int x0 = bx * FTX, y0 = by * DTY;
+    const int z0 = bz * zc;
+    const int z1 = min(z0 + zc, nz);
     const long long n = a.n;
     const long long plane = (long long)a.px * ny;
     const int has_S = a.S != nullptr;
@@ -253,9 +257,65 @@ energy_dag4_tma_kernel(const StepArgs<DMAX, DMAX> a, const __grid_constant__ Tma
             E += sE[k];
             P += sP[k];
         }
-        const long long b = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-        partial[2 * b] = E;
-        partial[2 * b + 1] = P;
+        out[0] = E;
+        out[1] = P;
+    }
+}
+
+// One problem: CTA = (x tile, y tile, z chunk), one partial per CTA.
+template <int DIM, typename T>
+__global__ void __launch_bounds__(ENERGY4_NT, 1)
+energy_dag4_tma_kernel(const StepArgs<DMAX, DMAX> a, const __grid_constant__ TmaMaps maps,
+                       const __grid_constant__ Dag4Shape sh, double* partial) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const long long b = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    energy_dag4_tile<DIM, T>(a, maps, sh, blockIdx.x, blockIdx.y, blockIdx.z, dag_smem_base(smem_raw),
+                             partial + 2 * b);
+}
+
+// The members of a batch: CTA k takes work item k (member, x tile, y tile,
+// z chunk) of the batch's list (the items of one member are contiguous), one
+// partial per item; args, maps and shapes are per member (one parity).
+template <int DIM, typename T>
+__global__ void __launch_bounds__(ENERGY4_NT, 1)
+batched_energy_dag4_tma_kernel(const StepArgs<DMAX, DMAX>* __restrict__ args, const TmaMaps* __restrict__ maps,
+                               const Dag4Shape* __restrict__ shapes, const int4* __restrict__ items,
+                               double* partial) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int4 w = items[blockIdx.x];
+    energy_dag4_tile<DIM, T>(args[w.x], maps[w.x], shapes[w.x], w.y, w.z, w.w, dag_smem_base(smem_raw),
+                             partial + 2 * (long long)blockIdx.x);
+}
+
+// Per member k of a batch (block k): the fixed-order sum of its items'
+// partials [begin[k], begin[k+1]) into out[2 k], out[2 k + 1]; a non-finite
+// result raises FLAG_NONFINITE in the member's flags (args: one parity).
+constexpr int ENERGY_RANGES_NT = 256;
+static __global__ void __launch_bounds__(ENERGY_RANGES_NT)
+energy_final_ranges_kernel(const double* __restrict__ partial, const int* __restrict__ begin,
+                           const StepArgs<DMAX, DMAX>* __restrict__ args, double* out) {
+    __shared__ double sE[ENERGY_RANGES_NT], sP[ENERGY_RANGES_NT];
+    const int k = blockIdx.x;
+    const int b0 = begin[k], b1 = begin[k + 1];
+    double E = 0.0, P = 0.0;
+    for (int b = b0 + (int)threadIdx.x; b < b1; b += ENERGY_RANGES_NT) {
+        E += partial[2 * (long long)b];
+        P += partial[2 * (long long)b + 1];
+    }
+    sE[threadIdx.x] = E;
+    sP[threadIdx.x] = P;
+    __syncthreads();
+    for (int w = ENERGY_RANGES_NT / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) {
+            sE[threadIdx.x] += sE[threadIdx.x + w];
+            sP[threadIdx.x] += sP[threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out[2 * k] = sE[0];
+        out[2 * k + 1] = sP[0];
+        if (!isfinite(sE[0]) || !isfinite(sP[0])) atomicOr(args[k].flags, FLAG_NONFINITE);
     }
 }
 

@@ -46,7 +46,9 @@ def test_batch_members_equal_single_problems(iters, sched):
                 assert np.array_equal(m.labels().cpu().numpy(), single.labels().cpu().numpy())
                 assert np.array_equal(m.flows().cpu().numpy(), single.flows().cpu().numpy())
                 E, P = single.energy()
-                assert E_b[k] == E and P_b[k] == P
+                # the batch reduces every member in one launch at its own
+                # chunk length: the same terms, summed in another order
+                assert abs(E_b[k] - E) <= 1e-6 * abs(E) and abs(P_b[k] - P) <= 1e-6 * abs(P) + 1e-6
                 assert m.iterations == iters
 
 
