@@ -592,12 +592,15 @@ pfm_status pfm_prefetch_data(pfm_problem* pb, const float* D, const float* S_fie
         PFM_CUDA(cudaEventCreateWithFlags(&pb->staged, cudaEventDisableTiming), "event");
         PFM_CUDA(cudaEventCreateWithFlags(&pb->consumed, cudaEventDisableTiming), "event");
         PFM_CUDA(cudaEventRecord(pb->consumed, pb->stream), "event");
-        // the staging buffers mirror the pitched D and S, padding zeroed once
+        // the staging buffers mirror the pitched D and S, padding zeroed once,
+        // in copy-stream order ahead of the first copy (a memset on the
+        // legacy stream would not be ordered with the non-blocking copy
+        // stream, and could land after the copy)
         PFM_CUDA(cudaMalloc(&pb->D_stage, (size_t)pb->nl * pb->n * 4), "alloc staging D");
-        PFM_CUDA(cudaMemset(pb->D_stage, 0, (size_t)pb->nl * pb->n * 4), "memset");
+        PFM_CUDA(cudaMemsetAsync(pb->D_stage, 0, (size_t)pb->nl * pb->n * 4, pb->copy_stream), "memset");
         if (pb->S) {
             PFM_CUDA(cudaMalloc(&pb->S_stage, (size_t)pb->n * 4), "alloc staging S");
-            PFM_CUDA(cudaMemset(pb->S_stage, 0, (size_t)pb->n * 4), "memset");
+            PFM_CUDA(cudaMemsetAsync(pb->S_stage, 0, (size_t)pb->n * 4, pb->copy_stream), "memset");
         }
         PFM_CUDA(cudaMalloc(&pb->stage_flags, sizeof(unsigned)), "alloc staging flags");
     }
