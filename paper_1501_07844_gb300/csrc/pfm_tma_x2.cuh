@@ -84,9 +84,12 @@ template <> __device__ __forceinline__ void stv2<float>(float* p, float2 v) { *r
 template <> __device__ __forceinline__ void stv2<__nv_bfloat16>(__nv_bfloat16* p, float2 v) {
     *reinterpret_cast<__nv_bfloat162*>(p) = __floats2bfloat162_rn(v.x, v.y);
 }
+// F16 pairs: one conversion that rounds to nearest and saturates to
+// +-65504 (a NaN stays NaN)
 template <> __device__ __forceinline__ void stv2<__half>(__half* p, float2 v) {
-    *reinterpret_cast<__half2*>(p) = __floats2half2_rn(fminf(fmaxf(v.x, -F16_MAX), F16_MAX),
-                                                       fminf(fmaxf(v.y, -F16_MAX), F16_MAX));
+    unsigned w;
+    asm("cvt.rn.satfinite.f16x2.f32 %0, %1, %2;" : "=r"(w) : "f"(v.y), "f"(v.x));
+    *reinterpret_cast<unsigned*>(p) = w;
 }
 // A labelling pair (the F16 floor of stu applies), stored as a pair even
 // when its second voxel is beyond the grid: with an even row pitch the second slot
