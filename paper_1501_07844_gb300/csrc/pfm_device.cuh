@@ -108,10 +108,12 @@ template <> __device__ __forceinline__ void stv<__nv_bfloat16>(__nv_bfloat16* p,
     *p = __float2bfloat16_rn(v);
 }
 // F16 storage: values beyond the largest finite F16 (65504) are stored as
-// +-65504 (a capacity that large bounds no flow of a labelling in [0, 1]).
-constexpr float F16_MAX = 65504.0f;
+// +-65504 (a capacity that large bounds no flow of a labelling in [0, 1]):
+// one conversion that rounds to nearest and saturates (a NaN stays NaN).
 template <> __device__ __forceinline__ void stv<__half>(__half* p, float v) {
-    *p = __float2half_rn(fminf(fmaxf(v, -F16_MAX), F16_MAX));
+    unsigned short h;
+    asm("cvt.rn.satfinite.f16.f32 %0, %1;" : "=h"(h) : "f"(v));
+    *reinterpret_cast<unsigned short*>(p) = h;
 }
 
 // Store of a labelling value.  With F16 storage a value below the smallest
