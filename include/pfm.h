@@ -398,12 +398,16 @@ PFM_API pfm_status pfm_batch_create(int n, const pfm_desc* descs, const pfm_para
                                     pfm_batch** out);
 PFM_API void pfm_batch_destroy(pfm_batch* b);
 PFM_API int pfm_batch_size(const pfm_batch* b);
-/* "batched_tma_dag" or "batched": the kernel family of pfm_batch_iterate. */
+/* "batched_tma_dag4", "batched_tma_dag" or "batched": the kernel family of
+ * pfm_batch_iterate. */
 PFM_API const char* pfm_batch_kernel_variant(const pfm_batch* b);
 PFM_API pfm_status pfm_batch_member(pfm_batch* b, int index, pfm_problem** out);
 /* n_iters >= 0 iterations of every member (asynchronous). */
 PFM_API pfm_status pfm_batch_iterate(pfm_batch* b, int n_iters);
-/* E and P of every member (arrays of pfm_batch_size entries).  (sync) */
+/* E and P of every member (arrays of pfm_batch_size entries), as
+ * pfm_energy gives them; the four-inner-node batch reduces every member in
+ * one launch over its work items (the members' sums agree with pfm_energy's
+ * up to their order).  Returns the first member error.  (sync) */
 PFM_API pfm_status pfm_batch_energy(pfm_batch* b, double* primal, double* dual);
 /* Autotuner: times trial_iters iterations for each z-chunk length in
  * {8, 16, 32, 64} and persistent grid sizes (resident CTAs, twice that, one
