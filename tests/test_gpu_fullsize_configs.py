@@ -6,7 +6,8 @@ costs there), Ishikawa 256^3 with 8 labels (200 iterations, chain-specialised
 kernel at the tuned chunk length), the 32-volume DAGMF batch (300
 iterations, the batched four-inner-node kernel; every member bit for bit
 against its single-problem run, three members against the oracle at every
-voxel) and the differentiable Potts 128^3 x 6 (100 unrolled iterations,
+voxel within bounds set by the rounding amplification measured there) and
+the differentiable Potts 128^3 x 6 (100 unrolled iterations,
 checkpoint every 10; the adjoint at 64 uniformly drawn entries against
 central differences of the oracle's forward run)."""
 import numpy as np
